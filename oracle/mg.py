@@ -1,0 +1,225 @@
+"""Multigrid pieces of the domain-wall method, FP64, following Sec. 2.3 and Sec. 3.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Readings of points the paper leaves open:
+  * chiral doubling ("1/2(1+P_pm)" in Sec. 3 is garbled): every relaxed vector
+    v is split into P_+ v and P_- v, giving 2*Nvec coarse dof per aggregate,
+    ordered [chirality (+, -)][vector]; sigma_3 = diag(+1 x Nvec, -1 x Nvec).
+  * block orthonormalisation = Gram-Schmidt of each aggregate's vectors of one
+    chirality, in vector order; written here as the Q factor of a QR
+    factorisation with a positive real diagonal of R (the same result).
+  * "r_1" of Eq. TruncProjectInterpolate is the wall field of the permuted
+    basis: (P^dag r)_1 = P_- r_1 + P_+ r_Ls.  Restriction puts
+    Phat_- P^dag P_- r_1 on coarse slice 1 and Phat_+ P^dag P_+ r_Ls on slice
+    Lhat_s; prolongation is the mirror image onto fine slices 1 and Ls.
+  * the setup operator is D_W(m_setup) D_W(m_setup)^dag (Table kcycle) at a
+    caller-chosen Wilson mass m_setup; relaxation is CG on the homogeneous
+    system from a Gaussian start, at most 250 iterations or a residual
+    reduction of 1e-4.
+  * the coarse kernel is always P^dag D_W(-M5) P, so the coarse D_DW / D_PV
+    of Eq. coarsenDW follow by linearity.
+  * post-smoothing: 8 GCR iterations on A z = r starting from the prolonged
+    coarse correction (0 pre-smoothing), A = D_PV^dag D_DW (Table kcycle).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import dirac
+from .solvers import cgnr_fixed, gcr, norm
+
+
+def relax_null_vector(Dw, v0, maxiter=250, tol=1e-4):
+    """CG on the homogeneous system (D_W D_W^dag) v = 0 from the start v0.
+
+    Returns (v, iterations).  The iterate's residual is -(D_W D_W^dag) v;
+    CG stops once it has fallen by `tol` relative to the start or after
+    `maxiter` steps (Table kcycle).
+    """
+    Dd = Dw.conj().T.tocsr()
+
+    def A(v):
+        return Dw @ (Dd @ v)
+
+    x = np.array(v0, dtype=complex).ravel()
+    r = -A(x)
+    r0 = norm(r)
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    it = 0
+    while it < maxiter and np.sqrt(rr) > tol * r0:
+        Ap = A(p)
+        alpha = rr / np.vdot(p, Ap).real
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+def aggregate_map(dims, block):
+    """Coarse site of every fine site, and the coarse lattice dims."""
+    cdims = tuple(L // b for L, b in zip(dims, block))
+    for L, b in zip(dims, block):
+        if L % b:
+            raise ValueError("block must divide the lattice")
+    c = dirac.site_coords(dims)
+    cc = c // np.asarray(block)[None, :]
+    return dirac.site_index(cc, cdims), cdims
+
+
+def build_prolongator(vecs, dims, block, nd, nc):
+    """Block-orthonormal, chirality-preserving prolongator P (Sec. 2.3).
+
+    vecs: list of Nvec d-dim vectors ([site][spin][color]).  Returns
+    (P sparse of shape (V*ns*nc, Vc*2*Nvec), coarse dims).  Columns are
+    ordered [coarse site][chirality +,-][vector].
+    """
+    ns = dirac.n_spin(nd)
+    dof = ns * nc
+    V = int(np.prod(dims))
+    nvec = len(vecs)
+    agg, cdims = aggregate_map(dims, block)
+    Vc = int(np.prod(cdims))
+    _, g5 = dirac.gammas(nd)
+    chir = np.kron(np.diag(g5).real, np.ones(nc))          # +1 / -1 per site dof
+    Vm = np.stack([np.asarray(v).reshape(V, dof) for v in vecs], axis=-1)   # (V, dof, nvec)
+    rows, cols, vals = [], [], []
+    for a in range(Vc):
+        sites = np.nonzero(agg == a)[0]
+        for ci, sign in enumerate((+1.0, -1.0)):
+            d_idx = np.nonzero(chir == sign)[0]
+            M = Vm[np.ix_(sites, d_idx)].reshape(len(sites) * len(d_idx), nvec)
+            Q, R = np.linalg.qr(M)
+            ph = np.diag(R) / np.abs(np.diag(R))
+            Q = Q * ph[None, :]
+            fine = (sites[:, None] * dof + d_idx[None, :]).reshape(-1)
+            for k in range(nvec):
+                rows.append(fine)
+                cols.append(np.full(fine.shape, (a * 2 + ci) * nvec + k))
+                vals.append(Q[:, k])
+    P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(V * dof, Vc * 2 * nvec))
+    return P, cdims
+
+
+def coarse_projectors(Vc, nvec):
+    """(Phat_+, Phat_-) = (1 pm sigma_3)/2 on the coarse d-dim space."""
+    plus = np.concatenate([np.ones(nvec), np.zeros(nvec)])
+    Pp = sp.kron(sp.identity(Vc), sp.diags(plus))
+    Pm = sp.kron(sp.identity(Vc), sp.diags(1.0 - plus))
+    return Pp.tocsr(), Pm.tocsr()
+
+
+def galerkin_kernel(P, Dw):
+    """Dhat_W = P^dag D_W P, the explicit sparse triple product (Sec. 2.3)."""
+    return (P.conj().T @ Dw @ P).tocsr()
+
+
+def coarse_dwf(Dhat_w, Ls_c, mf, nvec):
+    """Coarse Dhat_DW(m) of Eq. coarsenDW: Eq. DWoperator around Dhat_W with Phat_pm."""
+    Vc = Dhat_w.shape[0] // (2 * nvec)
+    Pp, Pm = coarse_projectors(Vc, nvec)
+    return dirac.dwf_from_kernel(Dhat_w, Ls_c, mf, Pp, Pm)
+
+
+def restrict(r, P, Ls, Ls_c, nd, nc, nvec):
+    """Truncated restriction onto the coarse walls (Eq. TruncProjectInterpolate)."""
+    nf = P.shape[0]
+    V = nf // (dirac.n_spin(nd) * nc)
+    Pp, Pm = dirac.site_projectors(V, nd, nc)
+    r = np.asarray(r).reshape(Ls, nf)
+    Vc = P.shape[1] // (2 * nvec)
+    Cp, Cm = coarse_projectors(Vc, nvec)
+    rho = P.conj().T @ (Pm @ r[0] + Pp @ r[Ls - 1])
+    out = np.zeros((Ls_c, P.shape[1]), dtype=complex)
+    out[0] = Cm @ rho
+    out[Ls_c - 1] += Cp @ rho
+    return out.reshape(-1)
+
+
+def prolong(e_c, P, Ls, Ls_c, nd, nc, nvec):
+    """Truncated prolongation from the coarse walls (Eq. TruncProjectInterpolate)."""
+    nf = P.shape[0]
+    V = nf // (dirac.n_spin(nd) * nc)
+    Pp, Pm = dirac.site_projectors(V, nd, nc)
+    Vc = P.shape[1] // (2 * nvec)
+    Cp, Cm = coarse_projectors(Vc, nvec)
+    e_c = np.asarray(e_c).reshape(Ls_c, P.shape[1])
+    eta = P @ (Cm @ e_c[0] + Cp @ e_c[Ls_c - 1])
+    out = np.zeros((Ls, nf), dtype=complex)
+    out[0] = Pm @ eta
+    out[Ls - 1] += Pp @ eta
+    return out.reshape(-1)
+
+
+class TwoLevel:
+    """Two-level PV-preconditioned K-cycle of Sec. 2.3 with the Table kcycle parameters."""
+
+    def __init__(self, U, dims, Ls, M5, mf, P, nvec, Ls_c=4, group="u1", antiperiodic=None,
+                 coarse_tol=0.05, coarse_maxiter=1024, post_smooth=8, restart=16):
+        nd = len(dims)
+        self.nd, self.nc = nd, (1 if group == "u1" else 3)
+        self.Ls, self.Ls_c, self.nvec, self.P = Ls, Ls_c, nvec, P
+        self.Ddw = dirac.dwf_matrix(U, dims, Ls, M5, mf, group, antiperiodic)
+        Dpv = dirac.pv_matrix(U, dims, Ls, M5, group, antiperiodic)
+        self.Dpv_dag = dirac.dagger(Dpv)
+        self.A = (self.Dpv_dag @ self.Ddw).tocsr()
+        Dw = dirac.wilson_matrix(U, dims, -M5, group, antiperiodic)
+        self.Dhat_w = galerkin_kernel(P, Dw)
+        Ddw_c = coarse_dwf(self.Dhat_w, Ls_c, mf, nvec)
+        Dpv_c = coarse_dwf(self.Dhat_w, Ls_c, 1.0, nvec)
+        self.Ac = (dirac.dagger(Dpv_c) @ Ddw_c).tocsr()
+        self.coarse_tol, self.coarse_maxiter = coarse_tol, coarse_maxiter
+        self.post_smooth, self.restart = post_smooth, restart
+        self.coarse_iters = []
+
+    def precondition(self, r):
+        """One K-cycle preconditioner application z = M(r)."""
+        rc = restrict(r, self.P, self.Ls, self.Ls_c, self.nd, self.nc, self.nvec)
+        ec, it = cgnr_fixed(self.Ac, rc, self.coarse_tol, self.coarse_maxiter)
+        self.coarse_iters.append(it)
+        e0 = prolong(ec, self.P, self.Ls, self.Ls_c, self.nd, self.nc, self.nvec)
+        z, _, _ = gcr(lambda v: self.A @ v, r, x0=e0, maxiter=self.post_smooth)
+        return z
+
+    def solve(self, b, tol=1e-10, max_restarts=200):
+        """Outer flexible GCR(restart) on D_PV^dag D_DW x = D_PV^dag b.
+
+        Stops on the true residual ||b - D_DW x|| / ||b|| <= tol.
+        Returns (x, outer iterations, true relative residual).
+        """
+        b = np.asarray(b, dtype=complex).ravel()
+        bn = norm(b)
+        x = np.zeros_like(b)
+        outer = 0
+        for _ in range(max_restarts):
+            rt = b - self.Ddw @ x
+            if norm(rt) <= tol * bn:
+                break
+            rA = self.Dpv_dag @ rt
+            # one restart cycle; stop early once the true residual is met
+            Z, AZ = [], []
+            r = rA.copy()
+            for _k in range(self.restart):
+                z = self.precondition(r)
+                w = self.A @ z
+                for zj, wj in zip(Z, AZ):
+                    beta = np.vdot(wj, w)
+                    w = w - beta * wj
+                    z = z - beta * zj
+                wn = norm(w)
+                w, z = w / wn, z / wn
+                alpha = np.vdot(w, r)
+                x = x + alpha * z
+                r = r - alpha * w
+                Z.append(z)
+                AZ.append(w)
+                outer += 1
+                if norm(b - self.Ddw @ x) <= tol * bn:
+                    break
+        return x, outer, norm(b - self.Ddw @ x) / bn

@@ -1,0 +1,211 @@
+"""Pins of the oracle's solvers, multigrid transfer, Galerkin operator and gradient."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac, mg, solvers, force
+
+
+def _u1(dims, sigma, seed):
+    return synth.u1_links(synth.u1_angles(np.random.default_rng(seed), dims, sigma))
+
+
+def _null_vectors(U, dims, nvec, seed, m_setup=-0.6, iters=30):
+    rng = np.random.default_rng(seed)
+    Dw = dirac.wilson_matrix(U, dims, m_setup)
+    out = []
+    for _ in range(nvec):
+        v0 = synth.gaussian_complex(rng, (Dw.shape[0],))
+        v, _ = mg.relax_null_vector(Dw, v0, maxiter=iters, tol=1e-4)
+        out.append(v)
+    return out
+
+
+def test_cgnr_matches_dense_solve():
+    dims, Ls = (4, 4), 4
+    U = _u1(dims, 0.5, 1)
+    D = dirac.dwf_matrix(U, dims, Ls, 1.0, 0.01)
+    b = synth.gaussian_complex(np.random.default_rng(2), (D.shape[0],))
+    x, it, res = solvers.cgnr(D, b, tol=1e-10)
+    xd = np.linalg.solve(D.toarray(), b)
+    assert res <= 1e-10
+    cond = np.linalg.cond(D.toarray())
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10 * cond
+    assert it > 0
+
+
+def test_gcr_exact_in_n_steps_and_monotone():
+    rng = np.random.default_rng(3)
+    n = 12
+    A = np.eye(n) * 3 + synth.gaussian_complex(rng, (n, n)) * 0.3
+    b = synth.gaussian_complex(rng, (n,))
+    x, r, k = solvers.gcr(lambda v: A @ v, b, maxiter=n)
+    assert np.linalg.norm(b - A @ x) < 1e-10 * np.linalg.norm(b)
+    # residual norms never increase step to step
+    prev = np.linalg.norm(b)
+    for m in range(1, n):
+        _, r, _ = solvers.gcr(lambda v: A @ v, b, maxiter=m)
+        assert np.linalg.norm(r) <= prev * (1 + 1e-12)
+        prev = np.linalg.norm(r)
+
+
+def test_relax_reduces_rayleigh_quotient():
+    dims = (8, 8)
+    U = _u1(dims, 0.5, 4)
+    Dw = dirac.wilson_matrix(U, dims, -0.5)
+    rng = np.random.default_rng(5)
+    v0 = synth.gaussian_complex(rng, (Dw.shape[0],))
+    v, it = mg.relax_null_vector(Dw, v0, maxiter=40)
+    q0 = np.linalg.norm(Dw.conj().T @ v0) / np.linalg.norm(v0)
+    q1 = np.linalg.norm(Dw.conj().T @ v) / np.linalg.norm(v)
+    assert 0 < it <= 40 and q1 < 0.5 * q0
+
+
+def test_prolongator_orthonormal_and_chiral():
+    """P^dag P = 1 and gamma_5 P = P sigma_3 (Sec. 2.3, Eq. gamma5)."""
+    dims, block, nvec = (8, 8), (4, 4), 4
+    U = _u1(dims, 0.5, 6)
+    vecs = _null_vectors(U, dims, nvec, 7)
+    P, cdims = mg.build_prolongator(vecs, dims, block, 2, 1)
+    assert cdims == (2, 2)
+    PdP = (P.conj().T @ P).toarray()
+    assert np.abs(PdP - np.eye(P.shape[1])).max() < 1e-13
+    V = 64
+    G5 = np.kron(np.eye(V), np.diag([1.0, -1.0]))
+    s3 = np.kron(np.eye(4), np.diag([1.0] * nvec + [-1.0] * nvec))
+    assert np.abs(G5 @ P.toarray() - P.toarray() @ s3).max() < 1e-14
+    # P^dag (1 pm gamma_5) P = 1 pm sigma_3
+    for sgn in (1, -1):
+        lhs = P.conj().T.toarray() @ (np.eye(2 * V) + sgn * G5) @ P.toarray()
+        assert np.abs(lhs - (np.eye(8 * nvec // nvec * nvec) + sgn * s3)).max() < 1e-13
+    # the span holds every chiral half of every relaxed vector: P P^dag v = v
+    Pp, Pm = dirac.site_projectors(V, 2, 1)
+    for v in vecs:
+        for proj in (Pp, Pm):
+            w = proj @ v
+            assert np.linalg.norm(P @ (P.conj().T @ w) - w) < 1e-12 * np.linalg.norm(w)
+
+
+def test_prolongator_first_column_is_normalised_vector():
+    """Gram-Schmidt order: column 0 of an aggregate is the normalised first vector there."""
+    dims, block, nvec = (4, 4), (2, 2), 2
+    U = _u1(dims, 0.5, 6)
+    vecs = _null_vectors(U, dims, nvec, 8, iters=5)
+    P, _ = mg.build_prolongator(vecs, dims, block, 2, 1)
+    agg, _ = mg.aggregate_map(dims, block)
+    sites = np.nonzero(agg == 1)[0]
+    v = vecs[0].reshape(16, 2)[sites, 0]             # chirality + = spin 0
+    col = P.toarray()[:, (1 * 2 + 0) * nvec + 0].reshape(16, 2)[sites, 0]
+    assert np.abs(col - v / np.linalg.norm(v)).max() < 1e-13
+
+
+def test_galerkin_commutes_with_dw_structure():
+    """P^dag D_DW(m) P (P diagonal in s) equals Eq. coarsenDW built from P^dag D_W P (Sec. 2.3)."""
+    dims, block, nvec, Ls, M5, m = (8, 8), (4, 4), 3, 4, 1.0, 0.03
+    U = _u1(dims, 0.5, 9)
+    vecs = _null_vectors(U, dims, nvec, 10)
+    P, _ = mg.build_prolongator(vecs, dims, block, 2, 1)
+    Dw = dirac.wilson_matrix(U, dims, -M5)
+    Dhat = mg.galerkin_kernel(P, Dw)
+    Ps = np.kron(np.eye(Ls), P.toarray())
+    lhs = Ps.conj().T @ dirac.dwf_matrix(U, dims, Ls, M5, m).toarray() @ Ps
+    rhs = mg.coarse_dwf(Dhat, Ls, m, nvec).toarray()
+    assert np.abs(lhs - rhs).max() < 1e-12
+
+
+def test_galerkin_identity_prolongator_reduces_to_wilson():
+    """Single-site aggregates with constant vectors: P = 1, so P^dag D_W P = D_W."""
+    dims = (4, 6)
+    U = _u1(dims, 0.7, 11)
+    V = 24
+    vecs = [np.ones(2 * V, dtype=complex)]
+    P, cdims = mg.build_prolongator(vecs, dims, (1, 1), 2, 1)
+    assert cdims == dims
+    Dw = dirac.wilson_matrix(U, dims, -1.0)
+    assert np.abs(P.toarray() - np.eye(2 * V)).max() < 1e-15
+    assert np.abs(mg.galerkin_kernel(P, Dw).toarray() - Dw.toarray()).max() < 1e-15
+
+
+def test_galerkin_stencil_is_nearest_neighbour():
+    """The coarse kernel couples a coarse site only to itself and its 2d nearest neighbours."""
+    dims, block, nvec = (12, 8), (4, 4), 2
+    U = _u1(dims, 0.5, 12)
+    P, cdims = mg.build_prolongator(_null_vectors(U, dims, nvec, 13), dims, block, 2, 1)
+    Dhat = mg.galerkin_kernel(P, dirac.wilson_matrix(U, dims, -1.0)).toarray()
+    nc = 2 * nvec
+    c = dirac.site_coords(cdims)
+    for a in range(Dhat.shape[0] // nc):
+        for b in range(Dhat.shape[0] // nc):
+            blk = Dhat[a * nc:(a + 1) * nc, b * nc:(b + 1) * nc]
+            d = np.abs(c[a] - c[b])
+            d = np.minimum(d, np.asarray(cdims) - d)
+            if d.sum() > 1:
+                assert np.abs(blk).max() < 1e-14
+
+
+def test_restrict_prolong_adjoint_and_wall_only():
+    dims, block, nvec, Ls, Ls_c = (8, 8), (4, 4), 3, 6, 4
+    U = _u1(dims, 0.5, 14)
+    P, _ = mg.build_prolongator(_null_vectors(U, dims, nvec, 15), dims, block, 2, 1)
+    rng = np.random.default_rng(16)
+    r = synth.gaussian_complex(rng, (Ls * P.shape[0],))
+    ec = synth.gaussian_complex(rng, (Ls_c * P.shape[1],))
+    R = mg.restrict(r, P, Ls, Ls_c, 2, 1, nvec)
+    E = mg.prolong(ec, P, Ls, Ls_c, 2, 1, nvec)
+    # prolongation is the adjoint of restriction
+    assert abs(np.vdot(ec, R) - np.vdot(E, r)) < 1e-12 * np.linalg.norm(r) * np.linalg.norm(ec)
+    # only the wall field P_- r_1 + P_+ r_Ls is read; only coarse slices 1, Lhat_s written
+    r2 = r.reshape(Ls, -1).copy()
+    r2[1:Ls - 1] = 0
+    r2[0, 0::2] = 0        # P_+ part of slice 1 (spin 0)
+    r2[Ls - 1, 1::2] = 0   # P_- part of slice Ls (spin 1)
+    assert np.abs(mg.restrict(r2.reshape(-1), P, Ls, Ls_c, 2, 1, nvec) - R).max() < 1e-14
+    Rr = R.reshape(Ls_c, -1)
+    assert np.abs(Rr[1:Ls_c - 1]).max() == 0
+    Ee = E.reshape(Ls, -1)
+    assert np.abs(Ee[1:Ls - 1]).max() == 0
+
+
+def test_restrict_with_identity_prolongator_is_wall_projection():
+    dims, Ls = (4, 4), 5
+    V = 16
+    P, _ = mg.build_prolongator([np.ones(2 * V, dtype=complex)], dims, (1, 1), 2, 1)
+    r = synth.gaussian_complex(np.random.default_rng(1), (Ls, 2 * V))
+    R = mg.restrict(r.reshape(-1), P, Ls, Ls, 2, 1, 1).reshape(Ls, V, 2)
+    rr = r.reshape(Ls, V, 2)
+    assert np.abs(R[0, :, 1] - rr[0, :, 1]).max() == 0 and np.abs(R[0, :, 0]).max() == 0
+    assert np.abs(R[Ls - 1, :, 0] - rr[Ls - 1, :, 0]).max() == 0 and np.abs(R[Ls - 1, :, 1]).max() == 0
+
+
+def test_two_level_kcycle_solves_to_tolerance():
+    """The K-cycle reaches ||b - D_DW x|| / ||b|| <= 1e-10 and the dense solution."""
+    dims, block, nvec, Ls = (8, 8), (4, 4), 4, 6
+    U = _u1(dims, 0.3, 17)
+    P, _ = mg.build_prolongator(_null_vectors(U, dims, nvec, 18, m_setup=-0.3, iters=60), dims, block, 2, 1)
+    ml = mg.TwoLevel(U, dims, Ls, 1.0, 0.02, P, nvec, Ls_c=4)
+    b = synth.gaussian_complex(np.random.default_rng(19), (Ls * 128,))
+    x, outer, res = ml.solve(b, tol=1e-10)
+    assert res <= 1e-10
+    D = ml.Ddw.toarray()
+    xd = np.linalg.solve(D, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10 * np.linalg.cond(D)
+    # MG needs far fewer outer iterations than CGNR needs iterations
+    _, it_cg, _ = solvers.cgnr(ml.Ddw, b, tol=1e-10)
+    assert outer < it_cg / 4
+
+
+@pytest.mark.parametrize("anti", [None, [0, 1]])
+def test_adjoint_gradient_matches_central_differences(anti):
+    dims, Ls, M5, mf = (4, 4), 4, 1.0, 0.05
+    rng = np.random.default_rng(20)
+    theta = synth.u1_angles(rng, dims, 0.7)
+    b = synth.gaussian_spinor(rng, dims, Ls).reshape(-1)
+    l0, grad = force.loss_and_grad(theta, b, dims, Ls, M5, mf, anti)
+    h = 1e-6
+    for mu, site in [(0, 0), (1, 5), (0, 15), (1, 12)]:
+        tp = theta.copy(); tp[mu, site] += h
+        tm = theta.copy(); tm[mu, site] -= h
+        lp, _ = force.loss_and_grad(tp, b, dims, Ls, M5, mf, anti)
+        lm, _ = force.loss_and_grad(tm, b, dims, Ls, M5, mf, anti)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - grad[mu, site]) < 1e-6 * max(1.0, abs(fd))
