@@ -1,0 +1,139 @@
+/*
+ * dwf.h -- C ABI of the GB300 domain-wall multigrid library (libdwfmg.so).
+ *
+ * The operations follow Brower, Clark, Howarth, Weinberg, "Multigrid for
+ * chiral lattice fermions: domain wall" (arXiv:2004.07732).  Every pointer
+ * argument named U, psi, out, b, x is a DEVICE pointer owned by the caller;
+ * the library never frees caller memory.  All calls are ordered on the CUDA
+ * stream passed as `stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  Applies are asynchronous; solvers synchronise the stream only to
+ * read convergence scalars.  Nothing is thrown across the ABI: every call
+ * returns a dwf_status and leaves a thread-local message for dwf_last_error().
+ *
+ * Canonical layouts (complex numbers interleaved re, im; x0 fastest):
+ *   5-d spinor  psi[s][x_{nd-1}]...[x_0][spin][color], s = 0..Ls-1
+ *               (2 spins x 1 color for 2-d U(1); 4 spins x 3 colors for 4-d SU(3))
+ *   gauge links U[mu][x_{nd-1}]...[x_0]          (U(1): one complex number)
+ *               U[mu][x_{nd-1}]...[x_0][a][b]    (SU(3): 3x3 complex, row-major)
+ * gamma basis: d = 2: gamma_1 = sigma_1, gamma_2 = sigma_2, gamma_5 = sigma_3;
+ *              d = 4: chiral basis, gamma_5 = diag(1, 1, -1, -1).
+ * P_+ = (1 + gamma_5)/2 therefore selects spin 0 (d = 2) or spins 0, 1 (d = 4).
+ *
+ * Mass convention: M5 is the domain-wall height (> 0).  The Wilson kernel is
+ * the paper's D_W(M5_paper) with M5_paper = -M5, i.e. diagonal d - M5.
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define DWF_API __attribute__((visibility("default")))
+#else
+#define DWF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DWF_OK = 0,
+    DWF_ERR_ARG = 1,        /* invalid geometry, pointer, size or parameter     */
+    DWF_ERR_CUDA = 2,       /* a CUDA call failed (message has the CUDA error)  */
+    DWF_ERR_NOCONV = 3,     /* solver hit its iteration cap; x = last iterate   */
+    DWF_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up               */
+    DWF_ERR_OOM = 5,        /* a library-owned allocation failed                */
+    DWF_ERR_UNSUPPORTED = 6 /* valid request outside what this build implements */
+} dwf_status;
+
+/* Arithmetic / storage precision of an operator application.
+ * F64:      complex128 spinors and links, FP64 arithmetic.
+ * F32:      complex64 spinors and links, FP32 arithmetic.
+ * F32_L16:  complex64 spinors, links stored as IEEE half pairs (re, im), FP32 arithmetic.
+ * F32_LBF16: complex64 spinors, links stored as bfloat16 pairs, FP32 arithmetic. */
+typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F32_L16 = 2, DWF_F32_LBF16 = 3 } dwf_prec;
+
+typedef enum { DWF_U1 = 1, DWF_SU3 = 3 } dwf_group;
+
+/* Lattice geometry.  nd = 2 (group U(1)) or nd = 4 (group SU(3)); L[mu] >= 1
+ * for mu < nd; Ls >= 1.  antiperiodic[mu] != 0 puts a factor -1 on hops that
+ * cross the mu boundary (periodic otherwise). */
+typedef struct {
+    int nd;
+    int L[4];
+    int Ls;
+    int group;
+    int antiperiodic[4];
+} dwf_geom;
+
+/* Message of the last failed call on this thread ("" if none). */
+DWF_API const char* dwf_last_error(void);
+
+/* Number of complex values of a 5-d spinor / of the link field of geometry g. */
+DWF_API size_t dwf_spinor_size(const dwf_geom* g);
+DWF_API size_t dwf_link_size(const dwf_geom* g);
+
+/* Convert FP64 links (complex128, canonical layout) to the link storage of
+ * `prec` (complex128 copy, complex64, half pairs or bfloat16 pairs, rounded to
+ * nearest even).  U_out must hold dwf_link_size(g) values of that format. */
+DWF_API dwf_status dwf_convert_links(const dwf_geom* g, const void* U64, void* U_out, int prec, void* stream);
+
+/* out = D_DW(mf) psi, or D_DW(mf)^dag psi if dagger != 0.
+ * Shamir operator of Eq. DWoperator (Sec. 2): diagonal blocks D_W(-M5) + 1,
+ * block (s, s+1) = P_-, block (s+1, s) = P_+, block (1, Ls) = -mf P_+,
+ * block (Ls, 1) = -mf P_-, with the Wilson kernel
+ * D_W(U, m)_{x,y} = -1/2 (1-gamma_mu) U_mu(x) delta_{x+mu,y}
+ *                  -1/2 (1+gamma_mu) U_mu(x-mu)^dag delta_{x-mu,y} + (d+m) delta_{x,y}.
+ * psi and out hold dwf_spinor_size(g) complex values (complex128 for F64,
+ * complex64 otherwise); U is in the link storage of `prec`.  psi and out must
+ * not overlap.  Returns DWF_ERR_ARG on a bad geometry or NULL pointer with a
+ * non-empty lattice; an empty lattice is a no-op. */
+DWF_API dwf_status dwf_apply(const dwf_geom* g, const void* U, const void* psi, void* out,
+                     double M5, double mf, int dagger, int prec, void* stream);
+
+/* out = D_PV psi (or D_PV^dag psi): the Pauli-Villars operator D_PV = D_DW(1)
+ * (Sec. 2.2).  Same arguments and layouts as dwf_apply. */
+DWF_API dwf_status pv_apply(const dwf_geom* g, const void* U, const void* psi, void* out,
+                    double M5, int dagger, int prec, void* stream);
+
+/* out = D_PV^dag D_DW(mf) psi, the approximately PV-preconditioned operator of
+ * Eq. NormalExp (Sec. 2.3).  `tmp` is caller-owned device scratch of
+ * dwf_spinor_size(g) complex values in the precision of `prec`; it receives
+ * D_DW(mf) psi.  psi, tmp and out must be three distinct buffers. */
+DWF_API dwf_status dwf_pvdag_apply(const dwf_geom* g, const void* U, const void* psi, void* tmp, void* out,
+                           double M5, double mf, int prec, void* stream);
+
+/* Inner product <x, y> = sum conj(x_i) y_i over n complex values (complex128
+ * if prec == DWF_F64, complex64 otherwise), accumulated in FP64 by a
+ * warp-shuffle / block / grid reduction with a fixed summation order (the
+ * result is bitwise reproducible run to run).  result_host receives
+ * {re, im}; the call synchronises `stream`. */
+DWF_API dwf_status dwf_dot(const void* x, const void* y, size_t n, int prec, double* result_host, void* stream);
+
+/* Solver statistics (Sec. 3 counts D_DW, D_DW^dag and D_PV^dag as one fine
+ * application each). */
+typedef struct {
+    int iterations;            /* CGNR iterations, or outer GCR iterations of mg_solve */
+    int restarts;              /* reliable updates / restart cycles                    */
+    long long fine_applies;    /* fine-operator applications                           */
+    long long coarse_applies;  /* coarse-operator applications                         */
+    double coarse_avg_iters;   /* average coarsest-solver iterations per cycle          */
+    double true_residual;      /* final ||b - D_DW x|| / ||b||, recomputed in FP64     */
+    double seconds;            /* wall time of the call                                 */
+} dwf_solve_stats;
+
+/* Conjugate gradient on the normal equations D_DW^dag D_DW x = D_DW^dag b
+ * (CGNR, Sec. 2.1 and Fig. iterationscompare), entirely in FP64 on the GPU,
+ * from x = 0.  Stops when ||b - D_DW x|| / ||b|| <= tol, confirmed on the
+ * recomputed true residual.  U, b, x are complex128.  Returns DWF_ERR_NOCONV
+ * after maxiter iterations (x then holds the last iterate).  stats may be NULL. */
+DWF_API dwf_status cgne_solve(const dwf_geom* g, const void* U, const void* b, void* x,
+                      double M5, double mf, double tol, int maxiter,
+                      dwf_solve_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWF_H */

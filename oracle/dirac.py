@@ -276,3 +276,53 @@ def free_dwf_symbol(p, Ls, M5, mf, nd):
     B[0:ns, (Ls - 1) * ns:Ls * ns] += -mf * Pp
     B[(Ls - 1) * ns:Ls * ns, 0:ns] += -mf * Pm
     return B
+
+
+# ----------------------------------------------------------------------------
+# Point evaluation for lattices too large to assemble (2-d U(1))
+# ----------------------------------------------------------------------------
+
+def dwf_apply_points_2d(U, psi, dims, Ls, M5, mf, points, dagger_=False, antiperiodic=None):
+    """(D_DW psi)_{s, x} at selected (s, site) points, straight from Eq. DWoperator.
+
+    U: (2, V) complex; psi: (Ls, V, 2) complex; points: iterable of (s, site)
+    with 0-based s.  Returns an array (len(points), 2).  Pure-Python loop, for
+    spot checks of large lattices.
+    """
+    g, g5 = gammas(2)
+    I2 = np.eye(2)
+    Pp, Pm = 0.5 * (I2 + g5), 0.5 * (I2 - g5)
+    anti = antiperiodic or [0, 0]
+    L0, L1 = dims
+    psi = np.asarray(psi).reshape(Ls, L0 * L1, 2)
+    U = np.asarray(U).reshape(2, L0 * L1)
+    out = []
+    for s, site in points:
+        x, y = site % L0, site // L0
+        acc = (2 - M5 + 1) * psi[s, site]
+        for mu in range(2):
+            c = [x, y]
+            c[mu] += 1
+            cross_f = c[mu] == dims[mu]
+            c[mu] %= dims[mu]
+            fwd = c[0] + L0 * c[1]
+            c = [x, y]
+            c[mu] -= 1
+            cross_b = c[mu] < 0
+            c[mu] %= dims[mu]
+            bwd = c[0] + L0 * c[1]
+            uf = U[mu, site] * (-1 if (cross_f and anti[mu]) else 1)
+            ub = np.conj(U[mu, bwd]) * (-1 if (cross_b and anti[mu]) else 1)
+            sg = -1 if dagger_ else 1
+            acc = acc - 0.5 * (I2 - sg * g[mu]) @ (uf * psi[s, fwd]) - 0.5 * (I2 + sg * g[mu]) @ (ub * psi[s, bwd])
+        A, B = (Pp, Pm) if dagger_ else (Pm, Pp)   # block (s, s+1) and (s+1, s) of D or D^dag
+        if s + 1 < Ls:
+            acc = acc + A @ psi[s + 1, site]
+        else:
+            acc = acc - mf * A @ psi[0, site]
+        if s > 0:
+            acc = acc + B @ psi[s - 1, site]
+        else:
+            acc = acc - mf * B @ psi[Ls - 1, site]
+        out.append(acc)
+    return np.array(out)

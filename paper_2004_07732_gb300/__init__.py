@@ -1,0 +1,9 @@
+"""GB300-native domain-wall multigrid (arXiv:2004.07732) -- Python binding of libdwfmg.so.
+
+All arithmetic runs in the library's sm_103a CUDA kernels behind the C ABI of
+include/dwf.h; this package only marshals torch tensors to device pointers.
+"""
+from ._lib import (  # noqa: F401
+    DwfError, Geom, SolveStats, PREC, lib, make_geom, spinor_size, link_size, spinor_dtype,
+    links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_dot, cgne_solve,
+)

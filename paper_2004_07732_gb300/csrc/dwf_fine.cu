@@ -1,0 +1,192 @@
+// Fine-level Shamir domain-wall operator D_DW(m) (Eq. DWoperator, Sec. 2) and
+// its Pauli-Villars / dagger variants, 2-d U(1) and 4-d SU(3).
+//
+// One thread owns one d-dim site and walks a chunk of s slices with a sliding
+// window: psi_{s+1}(x) is loaded once and reused for slice s+1, so every
+// spinor is read from HBM once per apply; the Wilson neighbours psi_s(x +- mu)
+// of the same slice are shared between threads through L1/L2.  The links of
+// the site are loaded once per s-chunk and reused on every slice (they do not
+// depend on s).  The s-hops P_+ psi_{s-1} and P_- psi_{s+1} are a component
+// select in the chiral basis (gamma_5 diagonal), fused into the same pass.
+#include "common.cuh"
+#include "fine_kernels.cuh"
+
+namespace dwf {
+
+// ----------------------------------------------------------------------------
+// 2-d U(1): spinor = 2 complex components (chirality +, -)
+// ----------------------------------------------------------------------------
+template <class R> struct Sp2 { typename cplx<R>::T c0, c1; };
+
+__device__ __forceinline__ Sp2<float> ld_sp(const Sp2<float>* p, long long i) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+    Sp2<float> s; s.c0 = make_float2(v.x, v.y); s.c1 = make_float2(v.z, v.w); return s;
+}
+__device__ __forceinline__ Sp2<double> ld_sp(const Sp2<double>* p, long long i) {
+    const double2* q = reinterpret_cast<const double2*>(p) + 2 * i;
+    Sp2<double> s; s.c0 = __ldg(q); s.c1 = __ldg(q + 1); return s;
+}
+__device__ __forceinline__ void st_sp(Sp2<float>* p, long long i, const Sp2<float>& s) {
+    reinterpret_cast<float4*>(p)[i] = make_float4(s.c0.x, s.c0.y, s.c1.x, s.c1.y);
+}
+__device__ __forceinline__ void st_sp(Sp2<double>* p, long long i, const Sp2<double>& s) {
+    double2* q = reinterpret_cast<double2*>(p) + 2 * i;
+    q[0] = s.c0; q[1] = s.c1;
+}
+// one chirality component of a spinor: comp 0 = P_+, comp 1 = P_-
+template <class R>
+__device__ __forceinline__ typename cplx<R>::T ld_comp(const Sp2<R>* p, long long i, int comp) {
+    const typename cplx<R>::T* q = reinterpret_cast<const typename cplx<R>::T*>(p) + 2 * i + comp;
+    return __ldg(q);
+}
+
+// Wilson hopping term -1/2 sum_mu [ (1 -+ gamma_mu) U psi(x+mu) + (1 +- gamma_mu) U^dag psi(x-mu) ]
+// (upper signs: D_W; lower: D_W^dag = gamma_5 D_W gamma_5).
+template <class R, bool DAG>
+__device__ __forceinline__ Sp2<R> hop2d(const Sp2<R>& xf, const Sp2<R>& xb, const Sp2<R>& yf, const Sp2<R>& yb,
+                                        typename cplx<R>::T u0f, typename cplx<R>::T u0b,
+                                        typename cplx<R>::T u1f, typename cplx<R>::T u1b) {
+    using C = typename cplx<R>::T;
+    C s0, s1;
+    if (!DAG) {
+        C t0f = cmul(u0f, xf.c0 - xf.c1);               // (1 - g1): (h, -h)
+        C t0b = cmulc(u0b, xb.c0 + xb.c1);              // (1 + g1): (h,  h)
+        C t1f = cmul(u1f, yf.c0 + times_i(yf.c1));     // (1 - g2): (h, -i h)
+        C t1b = cmulc(u1b, yb.c0 - times_i(yb.c1));     // (1 + g2): (h,  i h)
+        s0 = t0f + t0b + t1f + t1b;
+        s1 = (t0b - t0f) + times_i(t1b - t1f);
+    } else {
+        C t0f = cmul(u0f, xf.c0 + xf.c1);               // (1 + g1): (h,  h)
+        C t0b = cmulc(u0b, xb.c0 - xb.c1);              // (1 - g1): (h, -h)
+        C t1f = cmul(u1f, yf.c0 - times_i(yf.c1));      // (1 + g2): (h,  i h)
+        C t1b = cmulc(u1b, yb.c0 + times_i(yb.c1));     // (1 - g2): (h, -i h)
+        s0 = t0f + t0b + t1f + t1b;
+        s1 = (t0f - t0b) + times_i(t1f - t1b);
+    }
+    Sp2<R> o;
+    o.c0 = scale(s0, R(-0.5));
+    o.c1 = scale(s1, R(-0.5));
+    return o;
+}
+
+template <class LT, class R, bool DAG>
+__global__ void __launch_bounds__(256)
+k_dwf2d(const typename LT::store* __restrict__ U, const Sp2<R>* __restrict__ psi, Sp2<R>* __restrict__ out,
+        Fine2dParams p) {
+    using C = typename cplx<R>::T;
+    const long long V = p.V;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= V) return;
+    const int Lx = p.L0;
+    const int x = (int)(site % Lx);
+    const long long yrow = site - x;  // y * Lx
+    const int Ls = p.Ls;
+    const int s0 = blockIdx.y * p.s_chunk;
+    if (s0 >= Ls) return;
+    const int s1 = min(s0 + p.s_chunk, Ls);
+
+    // neighbour sites with periodic wrap
+    const long long xf_site = (x == Lx - 1) ? yrow : site + 1;
+    const long long xb_site = (x == 0) ? yrow + Lx - 1 : site - 1;
+    const long long yf_site = (site + Lx >= V) ? site + Lx - V : site + Lx;
+    const long long yb_site = (site - Lx < 0) ? site - Lx + V : site - Lx;
+
+    // links, loaded once for all s (antiperiodic boundaries flip the hop sign)
+    C u0f = load_link(U, site);
+    C u1f = load_link(U, V + site);
+    C u0b = load_link(U, xb_site);
+    C u1b = load_link(U, V + yb_site);
+    if (p.anti0) {
+        if (x == Lx - 1) u0f = scale(u0f, R(-1));
+        if (x == 0) u0b = scale(u0b, R(-1));
+    }
+    if (p.anti1) {
+        if (site + Lx >= V) u1f = scale(u1f, R(-1));
+        if (site - Lx < 0) u1b = scale(u1b, R(-1));
+    }
+    const R diag = R(p.diag);
+    const R mf = R(p.mf);
+    // component fed from below (s-1) and from above (s+1):
+    //   D:     out.c0 += psi_{s-1}.c0, out.c1 += psi_{s+1}.c1
+    //   D^dag: out.c0 += psi_{s+1}.c0, out.c1 += psi_{s-1}.c1
+    const int cb = DAG ? 1 : 0;   // component taken from s-1
+    const int ca = DAG ? 0 : 1;   // component taken from s+1
+
+    Sp2<R> cur = ld_sp(psi, (long long)s0 * V + site);
+    C below = (s0 > 0) ? ld_comp(psi, (long long)(s0 - 1) * V + site, cb)
+                       : scale(ld_comp(psi, (long long)(Ls - 1) * V + site, cb), -mf);
+    C wall0 = (s0 == 0) ? (ca == 0 ? cur.c0 : cur.c1) : C();
+
+    for (int s = s0; s < s1; ++s) {
+        const long long base = (long long)s * V;
+        Sp2<R> nxt;
+        C above;
+        if (s + 1 < Ls) {
+            nxt = ld_sp(psi, base + V + site);
+            above = (ca == 0) ? nxt.c0 : nxt.c1;
+        } else {
+            C w = (s0 == 0) ? wall0 : ld_comp(psi, site, ca);
+            above = scale(w, -mf);
+        }
+        Sp2<R> nb_xf = ld_sp(psi, base + xf_site);
+        Sp2<R> nb_xb = ld_sp(psi, base + xb_site);
+        Sp2<R> nb_yf = ld_sp(psi, base + yf_site);
+        Sp2<R> nb_yb = ld_sp(psi, base + yb_site);
+        Sp2<R> o = hop2d<R, DAG>(nb_xf, nb_xb, nb_yf, nb_yb, u0f, u0b, u1f, u1b);
+        o.c0 = o.c0 + scale(cur.c0, diag);
+        o.c1 = o.c1 + scale(cur.c1, diag);
+        if (cb == 0) { o.c0 = o.c0 + below; o.c1 = o.c1 + above; }
+        else         { o.c1 = o.c1 + below; o.c0 = o.c0 + above; }
+        st_sp(out, base + site, o);
+        below = (cb == 0) ? cur.c0 : cur.c1;
+        if (s + 1 < Ls) cur = nxt;
+    }
+}
+
+template <class LT, class R>
+static void launch2d(const void* U, const void* psi, void* out, const Fine2dParams& p, bool dagger,
+                     cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid((unsigned)((p.V + threads - 1) / threads), (unsigned)((p.Ls + p.s_chunk - 1) / p.s_chunk));
+    auto Ut = reinterpret_cast<const typename LT::store*>(U);
+    auto pi = reinterpret_cast<const Sp2<R>*>(psi);
+    auto po = reinterpret_cast<Sp2<R>*>(out);
+    if (dagger) k_dwf2d<LT, R, true><<<grid, threads, 0, st>>>(Ut, pi, po, p);
+    else        k_dwf2d<LT, R, false><<<grid, threads, 0, st>>>(Ut, pi, po, p);
+}
+
+int choose_s_chunk(long long V, int Ls) {
+    // enough threads to fill 152 SMs x 2048 threads several times over; a
+    // longer chunk keeps more of the s-window reuse (fewer boundary re-reads)
+    const long long target = 152LL * 2048LL * 2LL;
+    long long nchunks = (target + V - 1) / V;
+    if (nchunks < 1) nchunks = 1;
+    if (nchunks > Ls) nchunks = Ls;
+    int chunk = (int)((Ls + nchunks - 1) / nchunks);
+    return chunk < 1 ? 1 : chunk;
+}
+
+dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                         bool dagger, int prec, int s_chunk, cudaStream_t st) {
+    Fine2dParams p;
+    p.V = g.V;
+    p.L0 = g.L[0];
+    p.L1 = g.L[1];
+    p.Ls = g.Ls;
+    p.anti0 = g.anti[0];
+    p.anti1 = g.anti[1];
+    p.diag = (double)g.nd - M5 + 1.0;
+    p.mf = mf;
+    p.s_chunk = s_chunk > 0 ? s_chunk : choose_s_chunk(g.V, g.Ls);
+    switch (prec) {
+        case DWF_F64:      launch2d<LinkF64, double>(U, psi, out, p, dagger, st); break;
+        case DWF_F32:      launch2d<LinkF32, float>(U, psi, out, p, dagger, st); break;
+        case DWF_F32_L16:  launch2d<LinkH16, float>(U, psi, out, p, dagger, st); break;
+        case DWF_F32_LBF16: launch2d<LinkBF16, float>(U, psi, out, p, dagger, st); break;
+        default: set_error("bad precision %d", prec); return DWF_ERR_ARG;
+    }
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+}  // namespace dwf

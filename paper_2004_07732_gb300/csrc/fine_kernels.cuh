@@ -1,0 +1,47 @@
+// Internal interfaces between the translation units of libdwfmg.
+#pragma once
+
+#include "common.cuh"
+
+namespace dwf {
+
+struct Fine2dParams {
+    long long V;
+    int L0, L1, Ls;
+    int anti0, anti1;
+    double diag;   // d - M5 + 1
+    double mf;
+    int s_chunk;
+};
+
+struct Fine4dParams {
+    long long V;
+    int L[4];
+    int Ls;
+    int anti[4];
+    double diag;
+    double mf;
+    int s_chunk;
+};
+
+int choose_s_chunk(long long V, int Ls);
+
+// out = D_DW(mf) psi or its adjoint, on the canonical layout; `prec` selects
+// spinor / link storage.  s_chunk <= 0 picks the default.
+dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                         bool dagger, int prec, int s_chunk, cudaStream_t st);
+dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                         bool dagger, int prec, int s_chunk, cudaStream_t st);
+
+inline dwf_status fine_apply(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                             bool dagger, int prec, cudaStream_t st, int s_chunk = 0) {
+    if (g.nd == 2) return fine_apply_2d(g, U, psi, out, M5, mf, dagger, prec, s_chunk, st);
+    return fine_apply_4d(g, U, psi, out, M5, mf, dagger, prec, s_chunk, st);
+}
+
+// number of complex values per 5-d / d-dim site
+inline long long site_dof(const Geom& g) { return (long long)g.nspin * g.ncol; }
+inline long long spinor_len(const Geom& g) { return g.V * g.Ls * site_dof(g); }
+inline long long link_len(const Geom& g) { return g.V * g.nd * (long long)(g.ncol * g.ncol); }
+
+}  // namespace dwf
