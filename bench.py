@@ -1,0 +1,363 @@
+"""Benchmark of the domain-wall multigrid hot path on one GB300 (or N replicas).
+
+Prints ONE JSON line (rank 0).  Metric: fine D_DW HBM bandwidth (algorithmic
+GB/s, % of the measured HBM peak), with the time to a 1e-10 true residual of
+the mixed-precision MG solve versus FP64 CGNE on the 256x256 x Ls=16 workload
+reported alongside.
+
+  value        fine D_DW apply (FP32 spinors, FP16 links) on the 1024x1024 x Ls=16
+               U(1) lattice (537 MB of algorithmic traffic per apply, larger than
+               L2), whole-job GB/s over N ranks; L2 flushed before every timed apply
+  e2e          the same apply through the C ABI from pinned host buffers: H2D of
+               psi and links, apply, D2H of the result, all inside the timed region
+  roofline     the apply kernel: algorithmic bytes / CUDA-event duration vs the
+               measured HBM copy bandwidth
+  solve        256x256 x Ls=16 (sigma 0.7, M5 1, m 0.005): FP64 CGNE and MG, each
+               to ||b - D x|| / ||b|| <= 1e-10, wall time on the same GPU
+  cpu_baseline the FP64 oracle's CSR apply on the host cores, bounded sample
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the same metric and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "D_dw HBM GB/s (% peak); MG vs CGNE time to 1e-10 residual, same GPU"
+APPLY_WL = synth.SCHWINGER_1024
+SOLVE_WL = synth.SCHWINGER_256
+# algorithmic bytes per 5-d site of the FP32-spinor / FP16-link 2-d apply:
+# read psi (2 complex64 = 16 B) + write out (16 B) + 2 links x 4 B shared by Ls slices
+def apply_bytes(V, Ls, spinor_b=16, link_b=4):
+    return V * Ls * 2 * spinor_b + 2 * V * link_b
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic():
+    """Per-launch DRAM traffic of the apply kernel from the committed ncu summary,
+    or None if the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "k_dwf2d_f32l16_1024x1024_Ls16.md")
+    src = os.path.join(ROOT, "paper_2004_07732_gb300", "csrc", "dwf_fine.cu")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+_ORACLE_CACHE = {}
+
+
+def cpu_oracle_apply(budget_s=12.0):
+    """Time the FP64 oracle's CSR apply of D_DW on the host (bounded sample)."""
+    from oracle import dirac
+    wl = SOLVE_WL
+    if "D" not in _ORACLE_CACHE:
+        U, srcs = wl.draw(1)
+        _ORACLE_CACHE["D"] = dirac.dwf_matrix(U, wl.dims, wl.Ls, wl.M5, wl.mf)
+        _ORACLE_CACHE["b"] = srcs[0].reshape(-1)
+    D, b = _ORACLE_CACHE["D"], _ORACLE_CACHE["b"]
+    D @ b
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        D @ b
+        reps += 1
+    t = (time.perf_counter() - t0) / reps
+    gbs = apply_bytes(wl.V, wl.Ls) / t / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"scipy CSR matvec of D_DW on {wl.dims[0]}x{wl.dims[1]}xLs{wl.Ls} (1/16 of the "
+                      f"bench lattice), {reps} reps in {budget_s:.0f} s, same algorithmic bytes per site",
+            "seconds_per_apply": t, "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return
+    per = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_apply(budget_s=4.0 if i >= args.warmup else 1.0)
+        if i >= args.warmup:
+            per.append(r["seconds_per_apply"])
+            base = r
+    t = float(np.mean(per))
+    v = apply_bytes(SOLVE_WL.V, SOLVE_WL.Ls) / t / 1e9
+    base["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{APPLY_WL.name} D_DW apply (oracle sample {SOLVE_WL.name})",
+                       "l2": "oracle runs on the host"},
+            "cpu_baseline": base,
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2004_07732_gb300 as dw
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    dw.lib()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- fine apply bandwidth (value) ----------------
+    wl = APPLY_WL
+    g = dw.make_geom(wl.dims, wl.Ls)
+    U, srcs = wl.draw(1)
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    Ud = dw.links_to(g, U64, "f32_l16")
+    psi_h = torch.from_numpy(srcs[0].reshape(-1).astype(np.complex64)).pin_memory()
+    psi = psi_h.to(dev)
+    out = torch.empty_like(psi)
+    del U64
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    nbytes = apply_bytes(wl.V, wl.Ls)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+            b.record(stream)
+        barrier()
+    times = [a.elapsed_time(b) * 1e-3 for a, b in evs]
+    t_apply = max_over_ranks(float(np.mean(times)))
+    value = world * nbytes / t_apply / 1e9
+    launches = args.steps
+
+    # ---------------- e2e through host buffers ----------------
+    out_h = torch.empty_like(psi_h).pin_memory()
+    Ud_h = Ud.cpu().pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        Ud.copy_(Ud_h, non_blocking=True)
+        psi.copy_(psi_h, non_blocking=True)
+        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+        out_h.copy_(out, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 4)
+    for _ in range(e2e_steps):
+        Ud.copy_(Ud_h, non_blocking=True)
+        psi.copy_(psi_h, non_blocking=True)
+        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+        out_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+    h2d = psi_h.numel() * psi_h.element_size() + Ud_h.numel() * Ud_h.element_size()
+    d2h = out_h.numel() * out_h.element_size()
+    del flush, out_h, Ud_h, psi, out, Ud, psi_h
+
+    # ---------------- time to solution on the 256^2 workload ----------------
+    solve = None
+    if not args.skip_solve:
+        solve = time_solves(dw, dev, args)
+
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    achieved = nbytes / float(np.mean(times)) / 1e9
+    traffic = kernel_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "kernel": "k_dwf2d<LinkH16,float> (fine D_DW apply)",
+                "algorithmic_bytes_per_launch": nbytes, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
+    cpu = cpu_oracle_apply() if (rank == 0 and world == 1 and not args.skip_cpu) else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_apply * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp16 links)", "data": "synthetic",
+                "config": {"workload": f"{wl.name}: fine D_DW(m) apply, U(1) 2-d, sigma {wl.sigma}, "
+                                       f"M5 {wl.M5}, m {wl.mf}",
+                           "solve_workload": SOLVE_WL.name, "parallelism": f"replicas x{world}",
+                           "l2": "flushed (512 MB write) before every timed apply; the apply moves 537 MB"},
+                "pct_of_hbm_peak": 100.0 * achieved / hbm_peak,
+                "e2e": {"value": world * nbytes / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": launches, "solve": solve}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def time_solves(dw, dev, args):
+    import torch
+    wl = SOLVE_WL
+    U, srcs = wl.draw(1)
+    g = dw.make_geom(wl.dims, wl.Ls)
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    b = torch.from_numpy(srcs[0].reshape(-1)).to(dev)
+    x = torch.empty_like(b)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st, status = dw.cgne_solve(g, U64, b, x, wl.M5, wl.mf, tol=1e-10, maxiter=200000, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    t_cg = time.perf_counter() - t0
+    res = {"workload": wl.name, "tol": 1e-10,
+           "cgne_fp64": {"seconds": t_cg, "iterations": st["iterations"], "fine_applies": st["fine_applies"],
+                         "true_residual": st["true_residual"], "status": status}}
+    if hasattr(dw, "mg_setup") and not args.skip_mg:
+        res.update(time_mg(dw, dev, wl, U, U64, b, g, t_cg))
+    return res
+
+
+def time_mg(dw, dev, wl, U, U64, b, g, t_cg):
+    import torch
+    params = dw.mg_default_params()
+    rng = synth.rng_for(wl.seed + 7000)
+    nvec = params["nvec"]
+    starts = np.stack([synth.gaussian_complex(rng, (wl.V * 2,)) for _ in range(nvec)])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    mg = dw.mg_setup(g, U64, wl.M5, wl.mf, params, torch.from_numpy(starts.reshape(-1)).to(dev))
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t0
+    x = torch.empty_like(b)
+    dw.mg_solve(mg, b, x, tol=1e-10)          # warm run (allocations, graphs)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st, status = dw.mg_solve(mg, b, x, tol=1e-10, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    t_mg = time.perf_counter() - t0
+    dw.mg_destroy(mg)
+    return {"mg": {"seconds": t_mg, "setup_seconds": t_setup, "outer_iterations": st["iterations"],
+                   "fine_applies": st["fine_applies"], "coarse_avg_iters": st["coarse_avg_iters"],
+                   "true_residual": st["true_residual"], "status": status},
+            "mg_speedup_vs_cgne": t_cg / t_mg if t_mg > 0 else None}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-solve", action="store_true")
+    ap.add_argument("--skip-mg", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
