@@ -104,6 +104,21 @@ DWF_API dwf_status pv_apply(const dwf_geom* g, const void* U, const void* psi, v
 DWF_API dwf_status dwf_pvdag_apply(const dwf_geom* g, const void* U, const void* psi, void* tmp, void* out,
                            double M5, double mf, int prec, void* stream);
 
+/* out = D_PV^dag D_DW(mf) psi, like dwf_pvdag_apply but without any allocation
+ * and without a caller scratch buffer.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory (a host code whose own
+ * allocator has reserved nearly all of HBM, or a latency-critical loop that
+ * cannot take cudaMalloc's implicit synchronisation).  The intermediate
+ * D_DW psi lives in a fixed 16 MiB device array inside the library, resident on
+ * every GPU that loads it until the process exits; lattices whose spinor needs
+ * more than 16 MiB (2^20 complex128 or 2^21 complex64 values) return
+ * DWF_ERR_ARG.  All calls on a device share that array: calls that overlap on
+ * the GPU race and must be ordered on one stream.  The first call on each device
+ * looks up the array's address (cudaGetSymbolAddress); make it before any
+ * stream capture.  Arguments as dwf_pvdag_apply without `tmp`. */
+DWF_API dwf_status dwf_pvdag_apply_noalloc(const dwf_geom* g, const void* U, const void* psi, void* out,
+                                   double M5, double mf, int prec, void* stream);
+
 /* Inner product <x, y> = sum conj(x_i) y_i over n complex values (complex128
  * if prec == DWF_F64, complex64 otherwise), accumulated in FP64 by a
  * warp-shuffle / block / grid reduction with a fixed summation order (the

@@ -5,5 +5,5 @@ include/dwf.h; this package only marshals torch tensors to device pointers.
 """
 from ._lib import (  # noqa: F401
     DwfError, Geom, SolveStats, PREC, lib, make_geom, spinor_size, link_size, spinor_dtype,
-    links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_dot, cgne_solve,
+    links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_pvdag_apply_noalloc, dwf_dot, cgne_solve,
 )

@@ -76,6 +76,7 @@ def _setup_signatures(L):
         "dwf_apply": [G, _VP, _VP, _VP, _D, _D, _I, _I, _VP],
         "pv_apply": [G, _VP, _VP, _VP, _D, _I, _I, _VP],
         "dwf_pvdag_apply": [G, _VP, _VP, _VP, _VP, _D, _D, _I, _VP],
+        "dwf_pvdag_apply_noalloc": [G, _VP, _VP, _VP, _D, _D, _I, _VP],
         "dwf_dot": [_VP, _VP, ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _VP],
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
     }
@@ -177,6 +178,16 @@ def dwf_pvdag_apply(geom, U, psi, tmp, out, M5, mf, prec="f64", stream=None):
         _check_spinor(t, geom, prec, nm)
     check(lib().dwf_pvdag_apply(ctypes.byref(geom), _ptr(U), _ptr(psi), _ptr(tmp), _ptr(out), float(M5),
                                 float(mf), PREC[prec], _stream(stream)))
+    return out
+
+
+def dwf_pvdag_apply_noalloc(geom, U, psi, out, M5, mf, prec="f64", stream=None):
+    """D_PV^dag D_DW psi with the intermediate in the library's fixed device scratch
+    (no allocation; for callers that cannot allocate device memory)."""
+    for t, nm in ((psi, "psi"), (out, "out")):
+        _check_spinor(t, geom, prec, nm)
+    check(lib().dwf_pvdag_apply_noalloc(ctypes.byref(geom), _ptr(U), _ptr(psi), _ptr(out), float(M5),
+                                        float(mf), PREC[prec], _stream(stream)))
     return out
 
 
