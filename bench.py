@@ -39,6 +39,10 @@ import synth  # noqa: E402
 METRIC = "D_dw HBM GB/s (% peak); MG vs CGNE time to 1e-10 residual, same GPU"
 APPLY_WL = synth.SCHWINGER_1024
 SOLVE_WL = synth.SCHWINGER_256
+# Wilson setup mass near the critical mass of the synthetic fields: minus the
+# smallest real part of spec D_W(U, 0), estimated once offline on 64^2 samples
+# of each link-angle width (0.31-0.39 for sigma 0.7, 0.19-0.20 for 0.5).
+SETUP_MASS = {0.7: -0.3, 0.5: -0.19, 0.214: -0.035}
 # algorithmic bytes per 5-d site of the FP32-spinor / FP16-link 2-d apply:
 # read psi (2 complex64 = 16 B) + write out (16 B) + 2 links x 4 B shared by Ls slices
 def apply_bytes(V, Ls, spinor_b=16, link_b=4):
@@ -319,6 +323,7 @@ def time_solves(dw, dev, args):
 def time_mg(dw, dev, wl, U, U64, b, g, t_cg):
     import torch
     params = dw.mg_default_params()
+    params["setup_mass"] = SETUP_MASS[wl.sigma]
     rng = synth.rng_for(wl.seed + 7000)
     nvec = params["nvec"]
     starts = np.stack([synth.gaussian_complex(rng, (wl.V * 2,)) for _ in range(nvec)])

@@ -147,6 +147,90 @@ DWF_API dwf_status cgne_solve(const dwf_geom* g, const void* U, const void* b, v
                       double M5, double mf, double tol, int maxiter,
                       dwf_solve_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Multigrid (Sec. 2.3, Sec. 3, Table kcycle)
+ * ------------------------------------------------------------------------ */
+
+/* Parameters of the two-level PV-preconditioned K-cycle.  Defaults
+ * (dwf_mg_default_params) follow Table kcycle of the paper. */
+typedef struct {
+    int nvec;             /* near-null vectors before chiral doubling (8); coarse dof = 2*nvec */
+    int block[4];         /* aggregate extent per direction (4, 4)                             */
+    int Ls_c;             /* coarse fifth-dimension extent Lhat_s (4)                          */
+    int setup_maxiter;    /* CG iterations per near-null vector (250); 0 = use the starts as is */
+    double setup_tol;     /* CG residual reduction per near-null vector (1e-4)                 */
+    double setup_mass;    /* Wilson mass m of the setup operator D_W(m) D_W(m)^dag             */
+    int gcr_restart;      /* outer flexible GCR restart length (16)                            */
+    int pre_smooth;       /* GCR pre-smoothing iterations (0)                                  */
+    int post_smooth;      /* GCR post-smoothing iterations on the accumulated error (8)        */
+    double coarse_tol;    /* coarsest CGNR relative residual tolerance (0.05)                  */
+    int coarse_maxiter;   /* coarsest CGNR iteration cap (1024)                                */
+    int fine_prec;        /* storage of the fine links in the inner solve (DWF_F32_L16)        */
+    double inner_tol;     /* floor of the residual reduction of one reliable-update cycle      */
+    int max_restarts;     /* reliable-update cycles before giving up                          */
+} dwf_mg_params;
+
+typedef struct dwf_mg dwf_mg;
+
+/* Fill p with the Table kcycle defaults (2-level: level-3 CGNR settings on the
+ * coarse level). */
+DWF_API void dwf_mg_default_params(dwf_mg_params* p);
+
+/* Set up the two-level hierarchy of Sec. 2.3 for D_DW(mf) with links U
+ * (complex128, canonical layout; copied, the caller may free U afterwards).
+ * null_starts: nvec Gaussian d-dim vectors (complex128, [vec][site][spin][color])
+ * -- the random starts of the near-null relaxation are an input.  Steps, all on
+ * the GPU in FP64: CG on D_W(m) D_W(m)^dag v = 0 from each start (Table kcycle),
+ * chiral doubling P_+ v, P_- v, Gram-Schmidt per aggregate and chirality (the
+ * gamma_5-preserving prolongator, Eq. gamma5), and the Galerkin kernel
+ * Dhat_W = P^dag D_W(-M5) P (Sec. 2.3), stored per coarse site as the self block
+ * and one block per hop direction.  Returns an owning handle in *out. */
+DWF_API dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,
+                            const void* null_starts, dwf_mg** out, void* stream);
+
+/* Solve D_DW(mf) x = b (complex128 b, x) with the K-cycle of Sec. 2.3:
+ * FP64 reliable updates of the true residual around restarted flexible GCR on
+ * D_PV^dag D_DW (FP32 spinors, fine_prec links), preconditioned by truncated
+ * wall restriction (Eq. TruncProjectInterpolate), coarsest CGNR on
+ * (Dhat_PV^dag Dhat_DW)^dag (Dhat_PV^dag Dhat_DW) to coarse_tol, prolongation and
+ * post_smooth GCR iterations.  Stops when ||b - D_DW x|| / ||b|| <= tol
+ * (recomputed in FP64); DWF_ERR_NOCONV after maxiter outer iterations. */
+DWF_API dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, int maxiter, dwf_solve_stats* stats,
+                            void* stream);
+
+/* Free the handle and everything it owns. */
+DWF_API void mg_destroy(dwf_mg* h);
+
+/* Coarse geometry (nd, coarse L, Ls = Ls_c) and coarse dof per site (2*nvec). */
+DWF_API dwf_status mg_coarse_geom(const dwf_mg* h, dwf_geom* coarse, int* ncdof);
+
+/* Copy the FP64 prolongator, complex128 [site][chirality +,-][chirality dof][vec],
+ * V * 2 * (nspin/2 * ncolor) * nvec values; or the relaxed near-null vectors
+ * (complex128 [vec][site][spin][color]).  Device pointers; async on stream. */
+DWF_API dwf_status mg_get_prolongator(const dwf_mg* h, void* P_out, void* stream);
+DWF_API dwf_status mg_get_null_vectors(const dwf_mg* h, void* v_out, void* stream);
+
+/* Copy the FP64 Galerkin blocks of Dhat_W = P^dag D_W(-M5) P:
+ * complex128 [coarse site][dir][row][col], dir 0 = self, then +mu, -mu for
+ * mu = 0..nd-1; each block is (2 nvec) x (2 nvec) over the coarse dof
+ * [chirality][vec].  Block (x, +mu) couples coarse site x to x + mu. */
+DWF_API dwf_status mg_get_coarse_links(const dwf_mg* h, void* Y_out, void* stream);
+
+/* Truncated restriction / prolongation of Eq. TruncProjectInterpolate on the
+ * handle's prolongator, complex64 vectors: r_fine has the fine 5-d layout,
+ * r_coarse the coarse layout [s][coarse site][chirality][vec] over Ls_c slices.
+ * Restriction writes Phat_- P^dag P_- r_1 on coarse slice 1 and
+ * Phat_+ P^dag P_+ r_Ls on slice Ls_c (zero elsewhere); prolongation writes
+ * P_- P e_1 on fine slice 1 and P_+ P e_{Ls_c} on slice Ls (zero elsewhere). */
+DWF_API dwf_status mg_restrict(const dwf_mg* h, const void* r_fine, void* r_coarse, void* stream);
+DWF_API dwf_status mg_prolong(const dwf_mg* h, const void* e_coarse, void* e_fine, void* stream);
+
+/* Coarse Dhat_DW(mf) (or its adjoint) of Eq. coarsenDW on complex64 coarse
+ * vectors; mf = 1 gives Dhat_PV.  FP32 arithmetic on the FP32 copy of the
+ * Galerkin blocks. */
+DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, double mf, int dagger,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

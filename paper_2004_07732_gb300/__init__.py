@@ -7,3 +7,7 @@ from ._lib import (  # noqa: F401
     DwfError, Geom, SolveStats, PREC, lib, make_geom, spinor_size, link_size, spinor_dtype,
     links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_pvdag_apply_noalloc, dwf_dot, cgne_solve,
 )
+from ._lib import (  # noqa: F401
+    MgParams, Multigrid, mg_default_params, mg_setup, mg_solve, mg_destroy, mg_get_prolongator,
+    mg_get_null_vectors, mg_get_coarse_links, mg_restrict, mg_prolong, mg_coarse_apply,
+)

@@ -44,6 +44,14 @@ class SolveStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class MgParams(ctypes.Structure):
+    _fields_ = [("nvec", ctypes.c_int), ("block", ctypes.c_int * 4), ("Ls_c", ctypes.c_int),
+                ("setup_maxiter", ctypes.c_int), ("setup_tol", ctypes.c_double), ("setup_mass", ctypes.c_double),
+                ("gcr_restart", ctypes.c_int), ("pre_smooth", ctypes.c_int), ("post_smooth", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double), ("coarse_maxiter", ctypes.c_int), ("fine_prec", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -79,12 +87,25 @@ def _setup_signatures(L):
         "dwf_pvdag_apply_noalloc": [G, _VP, _VP, _VP, _D, _D, _I, _VP],
         "dwf_dot": [_VP, _VP, ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _VP],
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "mg_setup": [G, _VP, _D, _D, ctypes.POINTER(MgParams), _VP, ctypes.POINTER(_VP), _VP],
+        "mg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "mg_coarse_geom": [_VP, G, ctypes.POINTER(ctypes.c_int)],
+        "mg_get_prolongator": [_VP, _VP, _VP],
+        "mg_get_null_vectors": [_VP, _VP, _VP],
+        "mg_get_coarse_links": [_VP, _VP, _VP],
+        "mg_restrict": [_VP, _VP, _VP, _VP],
+        "mg_prolong": [_VP, _VP, _VP, _VP],
+        "mg_coarse_apply": [_VP, _VP, _VP, _D, _I, _VP],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
         fn.argtypes = args
         if name not in ("dwf_spinor_size", "dwf_link_size"):
             fn.restype = ctypes.c_int
+    L.dwf_mg_default_params.argtypes = [ctypes.POINTER(MgParams)]
+    L.dwf_mg_default_params.restype = None
+    L.mg_destroy.argtypes = [_VP]
+    L.mg_destroy.restype = None
 
 
 def check(status: int):
@@ -209,3 +230,138 @@ def cgne_solve(geom, U, b, x, M5, mf, tol=1e-10, maxiter=100000, stream=None, ra
     if status != OK and (raise_noconv or status != ERR_NOCONV):
         check(status)
     return st.as_dict(), status
+
+
+# ---------------------------------------------------------------------------
+# multigrid
+# ---------------------------------------------------------------------------
+def mg_default_params() -> dict:
+    p = MgParams()
+    lib().dwf_mg_default_params(ctypes.byref(p))
+    d = {k: getattr(p, k) for k, _ in MgParams._fields_}
+    d["block"] = list(p.block)
+    return d
+
+
+def _params(d: dict) -> MgParams:
+    p = MgParams()
+    lib().dwf_mg_default_params(ctypes.byref(p))
+    for k, v in d.items():
+        if k == "block":
+            for i, b in enumerate(v):
+                p.block[i] = int(b)
+        elif k == "fine_prec" and isinstance(v, str):
+            p.fine_prec = PREC[v]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Multigrid:
+    """Owning handle of an mg_setup hierarchy (freed by close() or garbage collection)."""
+
+    def __init__(self, ptr, geom, params):
+        self.ptr = ptr
+        self.geom = geom
+        self.params = params
+        cg = Geom()
+        ncd = ctypes.c_int()
+        check(lib().mg_coarse_geom(self.ptr, ctypes.byref(cg), ctypes.byref(ncd)))
+        self.coarse_geom = cg
+        self.ncdof = ncd.value
+        self.Vc = 1
+        for i in range(cg.nd):
+            self.Vc *= cg.L[i]
+
+    def close(self):
+        if self.ptr:
+            lib().mg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def coarse_size(self):
+        return self.Vc * self.coarse_geom.Ls * self.ncdof
+
+
+def mg_setup(geom, U64, M5, mf, params=None, null_starts=None, stream=None) -> Multigrid:
+    """Build the two-level hierarchy; null_starts: nvec d-dim complex128 Gaussian vectors."""
+    prm = _params(params or {})
+    if null_starts is None:
+        raise ValueError("null_starts (the Gaussian starts of the near-null relaxation) are required")
+    h = ctypes.c_void_p()
+    check(lib().mg_setup(ctypes.byref(geom), _ptr(U64.contiguous()), float(M5), float(mf), ctypes.byref(prm),
+                         _ptr(null_starts.contiguous()), ctypes.byref(h), _stream(stream)))
+    return Multigrid(h, geom, prm)
+
+
+def mg_solve(mg: Multigrid, b, x, tol=1e-10, maxiter=100000, stream=None, raise_noconv=True):
+    _check_spinor(b, mg.geom, "f64", "b")
+    _check_spinor(x, mg.geom, "f64", "x")
+    st = SolveStats()
+    status = lib().mg_solve(mg.ptr, _ptr(b), _ptr(x), float(tol), int(maxiter), ctypes.byref(st), _stream(stream))
+    if status != OK and (raise_noconv or status != ERR_NOCONV):
+        check(status)
+    return st.as_dict(), status
+
+
+def mg_destroy(mg: Multigrid):
+    mg.close()
+
+
+def mg_get_prolongator(mg: Multigrid):
+    g = mg.geom
+    nchd = (2 if g.nd == 4 else 1) * (3 if g.group == 3 else 1)
+    V = 1
+    for i in range(g.nd):
+        V *= g.L[i]
+    out = torch.empty(V * 2 * nchd * mg.params.nvec, dtype=torch.complex128, device="cuda")
+    check(lib().mg_get_prolongator(mg.ptr, _ptr(out), _stream(None)))
+    return out
+
+
+def mg_get_null_vectors(mg: Multigrid):
+    g = mg.geom
+    V = 1
+    for i in range(g.nd):
+        V *= g.L[i]
+    dof = (2 if g.nd == 2 else 4) * (3 if g.group == 3 else 1)
+    out = torch.empty(mg.params.nvec * V * dof, dtype=torch.complex128, device="cuda")
+    check(lib().mg_get_null_vectors(mg.ptr, _ptr(out), _stream(None)))
+    return out
+
+
+def mg_get_coarse_links(mg: Multigrid):
+    ndir = 2 * mg.geom.nd + 1
+    out = torch.empty(mg.Vc * ndir * mg.ncdof * mg.ncdof, dtype=torch.complex128, device="cuda")
+    check(lib().mg_get_coarse_links(mg.ptr, _ptr(out), _stream(None)))
+    return out
+
+
+def mg_restrict(mg: Multigrid, r_fine, r_coarse, stream=None):
+    _check_spinor(r_fine, mg.geom, "f32", "r_fine")
+    if r_coarse.dtype != torch.complex64 or r_coarse.numel() != mg.coarse_size:
+        raise ValueError("r_coarse must be complex64 of the coarse size")
+    check(lib().mg_restrict(mg.ptr, _ptr(r_fine), _ptr(r_coarse), _stream(stream)))
+    return r_coarse
+
+
+def mg_prolong(mg: Multigrid, e_coarse, e_fine, stream=None):
+    _check_spinor(e_fine, mg.geom, "f32", "e_fine")
+    if e_coarse.dtype != torch.complex64 or e_coarse.numel() != mg.coarse_size:
+        raise ValueError("e_coarse must be complex64 of the coarse size")
+    check(lib().mg_prolong(mg.ptr, _ptr(e_coarse), _ptr(e_fine), _stream(stream)))
+    return e_fine
+
+
+def mg_coarse_apply(mg: Multigrid, vin, vout, mf, dagger=False, stream=None):
+    for t in (vin, vout):
+        if t.dtype != torch.complex64 or t.numel() != mg.coarse_size or not t.is_cuda:
+            raise ValueError("coarse vectors must be complex64 CUDA tensors of the coarse size")
+    check(lib().mg_coarse_apply(mg.ptr, _ptr(vin), _ptr(vout), float(mf), int(bool(dagger)), _stream(stream)))
+    return vout

@@ -1,0 +1,75 @@
+// Internal structures of the two-level domain-wall multigrid (Sec. 2.3).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "fine_kernels.cuh"
+#include "blas.cuh"
+
+namespace dwf {
+
+constexpr int MG_MAX_NVEC = 32;
+constexpr int MG_MAX_DIRS = 9;   // self + 2 * 4
+
+// Geometry of the coarse level and of the aggregation map.
+struct MgGeom {
+    int nd;
+    int L[4];        // fine lattice
+    int b[4];        // aggregate extent
+    int Lc[4];       // coarse lattice
+    long long V, Vc;
+    int nb;          // fine sites per aggregate
+    int nchd;        // fine dof per chirality per site (1 for 2-d U(1), 6 for 4-d SU(3))
+    int nvec;
+    int ncd;         // coarse dof per site = 2 * nvec
+    int ndir;        // 2 * nd + 1
+    int Ls, Ls_c;
+};
+
+// Device-owned buffers are released by a single cudaFree of `arena`.
+struct dwf_mg_impl;
+
+}  // namespace dwf
+
+struct dwf_mg {
+    dwf::Geom G;          // fine geometry
+    dwf::MgGeom mg;
+    double M5, mf;
+    dwf_mg_params prm;
+    cudaStream_t st;
+    // device buffers (owned)
+    void* U64;            // complex128 links
+    void* Ulo;            // fine links in prm.fine_prec storage
+    double2* nullv;       // relaxed near-null vectors [vec][site][spin][color]
+    double2* P64;         // prolongator [site][chir][l][k]
+    float2* P32;
+    double2* Y64;         // Galerkin blocks [xc][dir][row][col]
+    float2* Y32;          // FP32 copy, column-major per block: [xc][dir][col][row]
+    int* status;          // device status word of the setup kernels
+    std::vector<void*> allocs;
+    // solver workspace (allocated on first solve)
+    bool ws_ready;
+    dwf::Workspace ws;
+    double* hsc;          // pinned host mirror of solver scalars
+    std::vector<void*> fine_vecs;   // FP32 fine vectors
+    std::vector<void*> coarse_vecs; // FP32 coarse vectors
+    void* x64;            // FP64 solution accumulator
+    void* r64;            // FP64 residual
+};
+
+namespace dwf {
+
+dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes);
+
+// Coarse operator application (Eq. coarsenDW) on FP32 coarse vectors;
+// `skip` (device, may be null): the launch does nothing when *skip != 0.
+dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger,
+                            const int* skip, cudaStream_t st);
+dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st);
+dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st);
+
+inline long long fine_len(const dwf_mg* h) { return h->G.V * h->G.Ls * site_dof(h->G); }
+inline long long coarse_len(const dwf_mg* h) { return h->mg.Vc * h->mg.Ls_c * h->mg.ncd; }
+
+}  // namespace dwf

@@ -1,0 +1,524 @@
+// Multigrid setup (Sec. 2.3 and Sec. 3, Table kcycle), all on the GPU in FP64:
+//   1. near-null vectors: CG on the homogeneous system D_W(m) D_W(m)^dag v = 0
+//      from caller-supplied Gaussian starts (at most setup_maxiter steps or a
+//      residual reduction setup_tol);
+//   2. chiral doubling and block orthonormalisation: per aggregate and
+//      chirality, Gram-Schmidt of the vectors' P_+ / P_- halves (applied twice
+//      for stability), giving a prolongator with gamma_5 P = P sigma_3 and
+//      P^dag P = 1 (Eq. gamma5);
+//   3. the Galerkin kernel Dhat_W = P^dag D_W(-M5) P, one (2 nvec)^2 block per
+//      coarse site for the self term and each of the 2d hop directions.
+#include <chrono>
+#include <new>
+#include <string>
+#include <string.h>
+
+#include "mg.cuh"
+
+namespace dwf {
+
+// ---------------------------------------------------------------------------
+// 1. near-null relaxation: FP64 CG kernels with a device-side stop flag
+// ---------------------------------------------------------------------------
+struct NvState {
+    double rr, rr0, alpha, beta;
+    int done, iters;
+};
+
+__global__ void __launch_bounds__(RED_THREADS) k_nv_init(double2* __restrict__ r, const double2* __restrict__ Av, long long n,
+                                                         RedScratch rs, NvState* S, int maxiter) {
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 a = Av[i];
+        r[i] = make_double2(-a.x, -a.y);
+        v[0] += a.x * a.x + a.y * a.y;
+    }
+    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+        S->rr = t[0]; S->rr0 = t[0]; S->iters = 0;
+        S->done = (t[0] == 0.0 || maxiter <= 0) ? 1 : 0;
+    });
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_nv_alpha(const double2* __restrict__ t, long long n, RedScratch rs, NvState* S) {
+    if (S->done) return;
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 a = t[i];
+        v[0] += a.x * a.x + a.y * a.y;
+    }
+    grid_reduce<1>(v, rs, [=] __device__(double* tt) {
+        if (tt[0] > 0.0) S->alpha = S->rr / tt[0];
+        else { S->alpha = 0.0; S->done = 1; }
+    });
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_nv_update(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
+                                                           const double2* __restrict__ Ap, long long n, RedScratch rs, NvState* S,
+                                                           double tol2, int maxiter) {
+    if (S->done) return;
+    const double a = S->alpha;
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 pi = p[i], qi = Ap[i], xi = x[i], ri = r[i];
+        xi.x += a * pi.x; xi.y += a * pi.y;
+        ri.x -= a * qi.x; ri.y -= a * qi.y;
+        x[i] = xi; r[i] = ri;
+        v[0] += ri.x * ri.x + ri.y * ri.y;
+    }
+    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+        S->beta = S->rr > 0.0 ? t[0] / S->rr : 0.0;
+        S->rr = t[0];
+        S->iters += 1;
+        if (t[0] <= tol2 * S->rr0 || S->iters >= maxiter) S->done = 1;
+    });
+}
+
+__global__ void k_nv_p(double2* __restrict__ p, const double2* __restrict__ r, long long n, const NvState* S) {
+    if (S->done) return;
+    const double b = S->beta;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 pi = p[i], ri = r[i];
+        p[i] = make_double2(ri.x + b * pi.x, ri.y + b * pi.y);
+    }
+}
+
+static int ew_grid(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 152LL * 8 ? b : 152LL * 8);
+}
+
+// CG on D_W(m) D_W(m)^dag v = 0 in place on v (d-dim, FP64).  D_W(m) is the
+// Ls = 1 domain-wall apply with wall mass 1 and height -m (diagonal d + m).
+static dwf_status relax_null(dwf_mg* h, double2* v, double2* r, double2* p, double2* t, double2* Ap, NvState* S,
+                             int* iters_out) {
+    Geom W = h->G;
+    W.Ls = 1;
+    const long long n = W.V * site_dof(W);
+    const double M5w = -h->prm.setup_mass;
+    cudaStream_t st = h->st;
+    const int rg = red_grid(n), eg = ew_grid(n);
+    const double tol2 = h->prm.setup_tol * h->prm.setup_tol;
+    const int maxit = h->prm.setup_maxiter;
+    DWF_TRY(fine_apply(W, h->U64, v, t, M5w, 1.0, true, DWF_F64, st));
+    DWF_TRY(fine_apply(W, h->U64, t, Ap, M5w, 1.0, false, DWF_F64, st));
+    k_nv_init<<<rg, RED_THREADS, 0, st>>>(r, Ap, n, h->ws.red(), S, maxit);
+    DWF_CHECK_CUDA(cudaMemcpyAsync(p, r, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    int launched = 0;
+    NvState hs;
+    for (;;) {
+        DWF_CHECK_CUDA(cudaMemcpyAsync(&hs, S, sizeof(NvState), cudaMemcpyDeviceToHost, st));
+        DWF_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (hs.done || launched >= maxit) break;
+        const int batch = 16;
+        for (int k = 0; k < batch && launched < maxit; ++k, ++launched) {
+            DWF_TRY(fine_apply(W, h->U64, p, t, M5w, 1.0, true, DWF_F64, st));
+            k_nv_alpha<<<rg, RED_THREADS, 0, st>>>(t, n, h->ws.red(), S);
+            DWF_TRY(fine_apply(W, h->U64, t, Ap, M5w, 1.0, false, DWF_F64, st));
+            k_nv_update<<<rg, RED_THREADS, 0, st>>>(v, r, p, Ap, n, h->ws.red(), S, tol2, maxit);
+            k_nv_p<<<eg, 256, 0, st>>>(p, r, n, S);
+            DWF_CHECK_LAUNCH();
+        }
+    }
+    *iters_out = hs.iters;
+    return DWF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 2. chiral doubling + block Gram-Schmidt
+// ---------------------------------------------------------------------------
+struct AggIndex {
+    int nd, L[4], b[4], Lc[4];
+    // fine site of local index l in aggregate xc
+    __host__ __device__ long long fine_site(long long xc, int l) const {
+        long long site = 0, stride = 1;
+        long long rem = xc;
+        int lr = l;
+        for (int mu = 0; mu < nd; ++mu) {
+            int c = (int)(rem % Lc[mu]);
+            rem /= Lc[mu];
+            int lc = lr % b[mu];
+            lr /= b[mu];
+            site += (long long)(c * b[mu] + lc) * stride;
+            stride *= L[mu];
+        }
+        return site;
+    }
+};
+
+// fine dof index within a site of chirality c, chirality-local index l
+__host__ __device__ __forceinline__ int chiral_dof(int nd, int ncol, int c, int l) {
+    if (nd == 2) return c;                        // spin c, one colour
+    return (2 * c + l / ncol) * ncol + l % ncol;  // spins 2c, 2c+1; colours
+}
+
+// One warp per (aggregate, chirality): Gram-Schmidt (twice) of the nvec
+// vectors' chirality-c halves restricted to the aggregate.
+__global__ void k_block_ortho(const double2* __restrict__ vecs, double2* __restrict__ P, AggIndex ai, int nchd,
+                              int ncol, int dof, int nvec, long long V, int nb, int* status) {
+    extern __shared__ double2 smem[];   // [nvec][nb*nchd]
+    const long long xc = blockIdx.x;
+    const int c = blockIdx.y;
+    const int lane = threadIdx.x;
+    const int na = nb * nchd;
+    for (int k = 0; k < nvec; ++k)
+        for (int e = lane; e < na; e += 32) {
+            int l = e / nchd, cd = e % nchd;
+            long long site = ai.fine_site(xc, l);
+            smem[k * na + e] = vecs[(long long)k * V * dof + site * dof + chiral_dof(ai.nd, ncol, c, cd)];
+        }
+    __syncwarp();
+    for (int k = 0; k < nvec; ++k) {
+        double2* vk = smem + k * na;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = 0; j < k; ++j) {
+                const double2* vj = smem + j * na;
+                double re = 0.0, im = 0.0;
+                for (int e = lane; e < na; e += 32) {
+                    double2 a = vj[e], b = vk[e];
+                    re += a.x * b.x + a.y * b.y;
+                    im += a.x * b.y - a.y * b.x;
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, off);
+                    im += __shfl_xor_sync(0xffffffffu, im, off);
+                }
+                for (int e = lane; e < na; e += 32) {
+                    double2 a = vj[e], b = vk[e];
+                    b.x -= re * a.x - im * a.y;
+                    b.y -= re * a.y + im * a.x;
+                    vk[e] = b;
+                }
+                __syncwarp();
+            }
+        }
+        double nn = 0.0;
+        for (int e = lane; e < na; e += 32) nn += vk[e].x * vk[e].x + vk[e].y * vk[e].y;
+        for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+        if (!(nn > 0.0)) {
+            if (lane == 0) atomicExch(status, 1);
+            nn = 1.0;
+        }
+        const double inv = 1.0 / sqrt(nn);
+        for (int e = lane; e < na; e += 32) { vk[e].x *= inv; vk[e].y *= inv; }
+        __syncwarp();
+    }
+    for (int k = 0; k < nvec; ++k)
+        for (int e = lane; e < na; e += 32) {
+            int l = e / nchd, cd = e % nchd;
+            long long site = ai.fine_site(xc, l);
+            P[((site * 2 + c) * nchd + cd) * nvec + k] = smem[k * na + e];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// 3. Galerkin kernel Dhat_W = P^dag D_W P, 2-d U(1)
+// ---------------------------------------------------------------------------
+// (1 + sgn gamma_mu)[a][b] in the 2-d basis gamma_1 = sigma_1, gamma_2 = sigma_2
+__device__ __forceinline__ double2 spin2(int mu, int sgn, int a, int b) {
+    if (a == b) return make_double2(1.0, 0.0);
+    if (mu == 0) return make_double2((double)sgn, 0.0);
+    // gamma_2 = [[0, -i], [i, 0]]
+    return (a == 0) ? make_double2(0.0, -(double)sgn) : make_double2(0.0, (double)sgn);
+}
+
+__global__ void k_galerkin_2d(const double2* __restrict__ U, const double2* __restrict__ P, double2* __restrict__ Y,
+                              AggIndex ai, int nvec, long long V, double diag, int anti0, int anti1) {
+    const long long xc = blockIdx.x;
+    const int dir = blockIdx.y;         // 0 self, 1 +0, 2 -0, 3 +1, 4 -1
+    const int ncd = 2 * nvec;
+    const int nb = ai.b[0] * ai.b[1];
+    const int L0 = ai.L[0], L1 = ai.L[1];
+    for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) {
+        const int i = e / ncd, j = e % ncd;
+        const int ci = i / nvec, ki = i % nvec, cj = j / nvec, kj = j % nvec;
+        double sre = 0.0, sim = 0.0;
+        for (int l = 0; l < nb; ++l) {
+            const long long x = ai.fine_site(xc, l);
+            const int x0 = (int)(x % L0), x1 = (int)(x / L0);
+            const int l0 = x0 % ai.b[0], l1 = x1 % ai.b[1];
+            const double2 pxi = P[(x * 2 + ci) * nvec + ki];
+            // sum over terms feeding (x -> y) for this block
+            for (int term = 0; term < 5; ++term) {
+                double2 coef;      // spin entry [ci][cj] times link, including -1/2 and phases
+                long long y;
+                if (term == 0) {
+                    if (dir != 0 || ci != cj) continue;
+                    coef = make_double2(diag, 0.0);
+                    y = x;
+                } else {
+                    const int mu = (term - 1) / 2;
+                    const int fwd = ((term - 1) % 2) == 0;
+                    const int lc = mu == 0 ? l0 : l1;
+                    const int bm = ai.b[mu];
+                    const bool crosses = fwd ? (lc == bm - 1) : (lc == 0);
+                    const int want_dir = crosses ? (1 + 2 * mu + (fwd ? 0 : 1)) : 0;
+                    if (want_dir != dir) continue;
+                    int y0 = x0, y1 = x1;
+                    bool wrap;
+                    if (mu == 0) { y0 = fwd ? x0 + 1 : x0 - 1; wrap = (y0 < 0 || y0 >= L0); y0 = (y0 + L0) % L0; }
+                    else         { y1 = fwd ? x1 + 1 : x1 - 1; wrap = (y1 < 0 || y1 >= L1); y1 = (y1 + L1) % L1; }
+                    y = (long long)y1 * L0 + y0;
+                    const double ph = (wrap && (mu == 0 ? anti0 : anti1)) ? -1.0 : 1.0;
+                    double2 u = fwd ? U[mu * V + x] : U[mu * V + y];
+                    if (!fwd) u.y = -u.y;                          // U_mu(x - mu)^*
+                    const double2 sm = spin2(mu, fwd ? -1 : 1, ci, cj);
+                    coef = make_double2(-0.5 * ph * (sm.x * u.x - sm.y * u.y), -0.5 * ph * (sm.x * u.y + sm.y * u.x));
+                }
+                const double2 pyj = P[(y * 2 + cj) * nvec + kj];
+                // conj(pxi) * coef * pyj
+                const double ar = pxi.x * coef.x + pxi.y * coef.y, ai_ = pxi.x * coef.y - pxi.y * coef.x;
+                sre += ar * pyj.x - ai_ * pyj.y;
+                sim += ar * pyj.y + ai_ * pyj.x;
+            }
+        }
+        Y[(xc * 5 + dir) * (long long)(ncd * ncd) + (long long)i * ncd + j] = make_double2(sre, sim);
+    }
+}
+
+__global__ void k_blocks_to_f32(const double2* __restrict__ Y, float2* __restrict__ Y32, long long nblocks, int ncd) {
+    const long long n = nblocks * ncd * ncd;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long blk = t / (ncd * ncd);
+        const int e = (int)(t % (ncd * ncd));
+        const int i = e / ncd, j = e % ncd;            // row-major source
+        double2 v = Y[t];
+        Y32[blk * ncd * ncd + (long long)j * ncd + i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+__global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+
+dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes < 256 ? 256 : bytes);
+    if (e != cudaSuccess) {
+        set_error("multigrid allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        *p = nullptr;
+        return DWF_ERR_OOM;
+    }
+    h->allocs.push_back(*p);
+    return DWF_OK;
+}
+
+static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
+    const MgGeom& m = h->mg;
+    const Geom& G = h->G;
+    cudaStream_t st = h->st;
+    const long long dof = site_dof(G);
+    const long long n1 = G.V * dof;     // one d-dim vector
+    DWF_TRY(h->ws.reserve(st));
+    DWF_TRY(mg_alloc(h, &h->U64, link_len(G) * sizeof(double2)));
+    DWF_CHECK_CUDA(cudaMemcpyAsync(h->U64, U, link_len(G) * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    size_t lo_b = h->prm.fine_prec == DWF_F64 ? 16 : (h->prm.fine_prec == DWF_F32 ? 8 : 4);
+    DWF_TRY(mg_alloc(h, &h->Ulo, link_len(G) * lo_b));
+    {
+        dwf_geom g;
+        g.nd = G.nd; g.Ls = G.Ls; g.group = G.group;
+        for (int mu = 0; mu < 4; ++mu) { g.L[mu] = G.L[mu]; g.antiperiodic[mu] = G.anti[mu]; }
+        DWF_TRY(dwf_convert_links(&g, h->U64, h->Ulo, h->prm.fine_prec, st));
+    }
+    DWF_TRY(mg_alloc(h, (void**)&h->nullv, m.nvec * n1 * sizeof(double2)));
+    DWF_CHECK_CUDA(cudaMemcpyAsync(h->nullv, starts, m.nvec * n1 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    DWF_TRY(mg_alloc(h, (void**)&h->status, 256));
+    DWF_CHECK_CUDA(cudaMemsetAsync(h->status, 0, 256, st));
+
+    // 1. relaxation
+    if (h->prm.setup_maxiter > 0) {
+        void* tmp = nullptr;
+        DWF_CHECK_CUDA(cudaMallocAsync(&tmp, 4 * n1 * sizeof(double2) + 256, st));
+        double2* r = (double2*)tmp;
+        double2* p = r + n1;
+        double2* t = p + n1;
+        double2* Ap = t + n1;
+        NvState* S = (NvState*)(h->ws.scal + 16);
+        dwf_status s = DWF_OK;
+        for (int k = 0; k < m.nvec && s == DWF_OK; ++k) {
+            int it = 0;
+            s = relax_null(h, h->nullv + k * n1, r, p, t, Ap, S, &it);
+        }
+        cudaFreeAsync(tmp, st);
+        DWF_TRY(s);
+    }
+    // 2. prolongator
+    const long long Psz = G.V * 2 * m.nchd * m.nvec;
+    DWF_TRY(mg_alloc(h, (void**)&h->P64, Psz * sizeof(double2)));
+    DWF_TRY(mg_alloc(h, (void**)&h->P32, Psz * sizeof(float2)));
+    AggIndex ai;
+    ai.nd = m.nd;
+    for (int mu = 0; mu < 4; ++mu) { ai.L[mu] = m.L[mu]; ai.b[mu] = m.b[mu]; ai.Lc[mu] = m.Lc[mu]; }
+    {
+        dim3 grid((unsigned)m.Vc, 2);
+        size_t sh = (size_t)m.nvec * m.nb * m.nchd * sizeof(double2);
+        if (sh > 48 * 1024) DWF_CHECK_CUDA(cudaFuncSetAttribute(k_block_ortho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        k_block_ortho<<<grid, 32, sh, st>>>(h->nullv, h->P64, ai, m.nchd, G.ncol, (int)dof, m.nvec, G.V, m.nb, h->status);
+        DWF_CHECK_LAUNCH();
+    }
+    k_d2f<<<ew_grid(Psz), 256, 0, st>>>(h->P64, h->P32, Psz);
+    DWF_CHECK_LAUNCH();
+    // 3. Galerkin blocks
+    const long long nblk = m.Vc * m.ndir;
+    DWF_TRY(mg_alloc(h, (void**)&h->Y64, nblk * m.ncd * m.ncd * sizeof(double2)));
+    DWF_TRY(mg_alloc(h, (void**)&h->Y32, nblk * m.ncd * m.ncd * sizeof(float2)));
+    if (m.nd == 2) {
+        dim3 grid((unsigned)m.Vc, 5);
+        int thr = m.ncd * m.ncd < 256 ? m.ncd * m.ncd : 256;
+        k_galerkin_2d<<<grid, thr, 0, st>>>((const double2*)h->U64, h->P64, h->Y64, ai, m.nvec, G.V,
+                                             (double)G.nd - h->M5, G.anti[0], G.anti[1]);
+        DWF_CHECK_LAUNCH();
+    } else {
+        set_error("4-d multigrid setup not built yet");
+        return DWF_ERR_UNSUPPORTED;
+    }
+    k_blocks_to_f32<<<ew_grid(nblk * m.ncd * m.ncd), 256, 0, st>>>(h->Y64, h->Y32, nblk, m.ncd);
+    DWF_CHECK_LAUNCH();
+    int hstat = 0;
+    DWF_CHECK_CUDA(cudaMemcpyAsync(&hstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DWF_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (hstat) {
+        set_error("a near-null vector vanishes on an aggregate: the prolongator is rank deficient");
+        return DWF_ERR_ARG;
+    }
+    return DWF_OK;
+}
+
+}  // namespace dwf
+
+using namespace dwf;
+
+extern "C" {
+
+void dwf_mg_default_params(dwf_mg_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->nvec = 8;
+    p->block[0] = p->block[1] = p->block[2] = p->block[3] = 4;
+    p->Ls_c = 4;
+    p->setup_maxiter = 250;
+    p->setup_tol = 1e-4;
+    p->setup_mass = 0.0;
+    p->gcr_restart = 16;
+    p->pre_smooth = 0;
+    p->post_smooth = 8;
+    p->coarse_tol = 0.05;
+    p->coarse_maxiter = 1024;
+    p->fine_prec = DWF_F32_L16;
+    p->inner_tol = 1e-5;
+    p->max_restarts = 1000;
+}
+
+dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,
+                    const void* null_starts, dwf_mg** out, void* stream) {
+    clear_error();
+    if (!out) { set_error("NULL handle pointer"); return DWF_ERR_ARG; }
+    *out = nullptr;
+    Geom G;
+    DWF_TRY(check_geom(g, &G));
+    dwf_mg_params prm;
+    if (p) prm = *p; else dwf_mg_default_params(&prm);
+    if (!U || !null_starts) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
+    if (prm.nvec < 1 || prm.nvec > MG_MAX_NVEC) { set_error("nvec must be in [1, %d]", MG_MAX_NVEC); return DWF_ERR_ARG; }
+    if (prm.Ls_c < 1) { set_error("Ls_c must be >= 1"); return DWF_ERR_ARG; }
+    if (!valid_prec(prm.fine_prec) || prm.fine_prec == DWF_F64) {
+        set_error("fine_prec must be one of the FP32 precisions"); return DWF_ERR_ARG;
+    }
+    if (prm.gcr_restart < 1 || prm.post_smooth < 0 || prm.coarse_maxiter < 1 || prm.setup_maxiter < 0) {
+        set_error("bad solver parameters"); return DWF_ERR_ARG;
+    }
+    MgGeom m;
+    memset(&m, 0, sizeof(m));
+    m.nd = G.nd;
+    m.V = G.V;
+    m.Vc = 1;
+    m.nb = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        m.L[mu] = G.L[mu];
+        m.b[mu] = mu < G.nd ? prm.block[mu] : 1;
+        if (m.b[mu] < 1 || m.L[mu] % m.b[mu]) {
+            set_error("block[%d] = %d must divide L[%d] = %d", mu, m.b[mu], mu, m.L[mu]);
+            return DWF_ERR_ARG;
+        }
+        m.Lc[mu] = m.L[mu] / m.b[mu];
+        m.Vc *= m.Lc[mu];
+        m.nb *= m.b[mu];
+    }
+    m.nchd = G.nspin / 2 * G.ncol;
+    m.nvec = prm.nvec;
+    m.ncd = 2 * prm.nvec;
+    m.ndir = 2 * G.nd + 1;
+    m.Ls = G.Ls;
+    m.Ls_c = prm.Ls_c;
+    if ((long long)m.nb * m.nchd < m.nvec) {
+        set_error("aggregates of %d dof per chirality cannot hold %d orthonormal vectors", m.nb * m.nchd, m.nvec);
+        return DWF_ERR_ARG;
+    }
+    dwf_mg* h = new (std::nothrow) dwf_mg();
+    if (!h) { set_error("host allocation failed"); return DWF_ERR_OOM; }
+    h->G = G;
+    h->mg = m;
+    h->M5 = M5;
+    h->mf = mf;
+    h->prm = prm;
+    h->st = as_stream(stream);
+    h->ws_ready = false;
+    h->hsc = nullptr;
+    h->x64 = h->r64 = nullptr;
+    dwf_status s = setup_impl(h, U, null_starts);
+    if (s != DWF_OK) {
+        std::string msg = dwf_last_error();
+        mg_destroy(h);
+        set_error("%s", msg.c_str());
+        return s;
+    }
+    *out = h;
+    return DWF_OK;
+}
+
+void mg_destroy(dwf_mg* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    for (void* p : h->allocs) cudaFree(p);
+    for (void* p : h->fine_vecs) cudaFree(p);
+    for (void* p : h->coarse_vecs) cudaFree(p);
+    if (h->hsc) cudaFreeHost(h->hsc);
+    delete h;
+}
+
+dwf_status mg_coarse_geom(const dwf_mg* h, dwf_geom* c, int* ncdof) {
+    clear_error();
+    if (!h || !c) { set_error("NULL argument"); return DWF_ERR_ARG; }
+    memset(c, 0, sizeof(*c));
+    c->nd = h->mg.nd;
+    for (int mu = 0; mu < 4; ++mu) c->L[mu] = mu < h->mg.nd ? h->mg.Lc[mu] : 0;
+    c->Ls = h->mg.Ls_c;
+    c->group = h->G.group;
+    if (ncdof) *ncdof = h->mg.ncd;
+    return DWF_OK;
+}
+
+dwf_status mg_get_prolongator(const dwf_mg* h, void* P_out, void* stream) {
+    clear_error();
+    if (!h || !P_out) { set_error("NULL argument"); return DWF_ERR_ARG; }
+    const long long n = h->G.V * 2 * h->mg.nchd * h->mg.nvec;
+    DWF_CHECK_CUDA(cudaMemcpyAsync(P_out, h->P64, n * sizeof(double2), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return DWF_OK;
+}
+
+dwf_status mg_get_null_vectors(const dwf_mg* h, void* v_out, void* stream) {
+    clear_error();
+    if (!h || !v_out) { set_error("NULL argument"); return DWF_ERR_ARG; }
+    const long long n = h->mg.nvec * h->G.V * site_dof(h->G);
+    DWF_CHECK_CUDA(cudaMemcpyAsync(v_out, h->nullv, n * sizeof(double2), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return DWF_OK;
+}
+
+dwf_status mg_get_coarse_links(const dwf_mg* h, void* Y_out, void* stream) {
+    clear_error();
+    if (!h || !Y_out) { set_error("NULL argument"); return DWF_ERR_ARG; }
+    const long long n = h->mg.Vc * h->mg.ndir * h->mg.ncd * h->mg.ncd;
+    DWF_CHECK_CUDA(cudaMemcpyAsync(Y_out, h->Y64, n * sizeof(double2), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return DWF_OK;
+}
+
+}  // extern "C"
