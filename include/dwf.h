@@ -168,6 +168,7 @@ typedef struct {
     int fine_prec;        /* storage of the fine links in the inner solve (DWF_F32_L16)        */
     double inner_tol;     /* floor of the residual reduction of one reliable-update cycle      */
     int max_restarts;     /* reliable-update cycles before giving up                          */
+    int coarse_persistent;/* 1: the coarsest CGNR runs as one cooperative persistent launch    */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;

@@ -49,7 +49,8 @@ class MgParams(ctypes.Structure):
                 ("setup_maxiter", ctypes.c_int), ("setup_tol", ctypes.c_double), ("setup_mass", ctypes.c_double),
                 ("gcr_restart", ctypes.c_int), ("pre_smooth", ctypes.c_int), ("post_smooth", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("coarse_maxiter", ctypes.c_int), ("fine_prec", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
+                ("coarse_persistent", ctypes.c_int)]
 
 
 _lib = None

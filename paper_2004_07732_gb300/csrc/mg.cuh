@@ -46,6 +46,7 @@ struct dwf_mg {
     float2* P32;
     double2* Y64;         // Galerkin blocks [xc][dir][row][col]
     float2* Y32;          // FP32 copy, column-major per block: [xc][dir][col][row]
+    float2* Yd32;         // FP32 adjoint blocks Y[x+dir][-dir]^dag, column-major
     int* status;          // device status word of the setup kernels
     std::vector<void*> allocs;
     // solver workspace (allocated on first solve)
@@ -66,8 +67,15 @@ dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes);
 // `skip` (device, may be null): the launch does nothing when *skip != 0.
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger,
                             const int* skip, cudaStream_t st);
+dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st);
 dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st);
 dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st);
+
+// One cooperative launch running the whole coarsest CGNR; vec6 = six coarse
+// work vectors, partials = 3 * grid doubles, bar = 16 bytes of barrier state.
+// out_iters accumulates the iteration count over calls.
+dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* vec6, double* partials,
+                                  void* bar, int* out_iters, double* out_rr2, cudaStream_t st);
 
 inline long long fine_len(const dwf_mg* h) { return h->G.V * h->G.Ls * site_dof(h->G); }
 inline long long coarse_len(const dwf_mg* h) { return h->mg.Vc * h->mg.Ls_c * h->mg.ncd; }

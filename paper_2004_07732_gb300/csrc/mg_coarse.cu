@@ -21,15 +21,17 @@ struct CoarseParams {
 
 __device__ __forceinline__ long long coarse_neighbour(const CoarseParams& p, long long xc, int dir) {
     if (dir == 0) return xc;
-    const int mu = (dir - 1) / 2;
-    const int step = ((dir - 1) % 2 == 0) ? 1 : -1;
-    long long stride = 1;
-    for (int k = 0; k < mu; ++k) stride *= p.Lc[k];
-    const int c = (int)((xc / stride) % p.Lc[mu]);
-    int cn = c + step;
-    if (cn < 0) cn += p.Lc[mu];
-    if (cn >= p.Lc[mu]) cn -= p.Lc[mu];
-    return xc + (long long)(cn - c) * stride;
+    const int mu = (dir - 1) >> 1;
+    const int step = ((dir - 1) & 1) ? -1 : 1;
+    // extent and stride of direction mu without indexing the parameter arrays dynamically
+    const long long L0 = p.Lc[0], L1 = p.Lc[1], L2 = p.Lc[2], L3 = p.Lc[3];
+    const long long Lm = mu == 0 ? L0 : mu == 1 ? L1 : mu == 2 ? L2 : L3;
+    const long long stride = mu == 0 ? 1 : mu == 1 ? L0 : mu == 2 ? L0 * L1 : L0 * L1 * L2;
+    const long long c = (xc / stride) % Lm;
+    long long cn = c + step;
+    if (cn < 0) cn += Lm;
+    if (cn >= Lm) cn -= Lm;
+    return xc + (cn - c) * stride;
 }
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
@@ -43,49 +45,309 @@ __device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc) {   
     return acc;
 }
 
-template <bool DAG>
-__global__ void __launch_bounds__(256) k_coarse_dwf(const float2* __restrict__ Y, const float2* __restrict__ in,
-                                                    float2* __restrict__ out, CoarseParams p, const int* skip) {
-    if (skip && *skip) return;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncd = p.ncd;
-    const long long total = p.Vc * p.Ls_c * ncd;
-    if (t >= total) return;
-    const int i = (int)(t % ncd);
-    const long long rest = t / ncd;
-    const long long xc = rest % p.Vc;
-    const int s = (int)(rest / p.Vc);
+// One warp per coarse site.  B holds (2 nvec)^2 blocks column-major per
+// [coarse site][dir]: the Galerkin blocks of Dhat_W for the operator, or the
+// pre-transposed blocks of Dhat_W^dag (block (x, dir) = Y(x + dir, -dir)^dag)
+// for the adjoint, so both read B coalesced.  Lane l owns rows
+// i = (l & 15) + 16 k and slices s = (l >> 4) + 2 k'; the j loop is unrolled so
+// every block and input load of a direction is in flight together.  CG = true
+// reads the input through L2 (other blocks of a persistent launch wrote it).
+// Returns the lane's share of |out|^2.
+template <int NCD, bool CG>
+__device__ __forceinline__ double warp_site_apply(const float2* __restrict__ B, const float2* __restrict__ in,
+                                                  float2* __restrict__ out, const CoarseParams& p, long long xc,
+                                                  float mf, bool dag, int lane) {
+    const int ncd = NCD > 0 ? NCD : p.ncd;
     const long long slice = p.Vc * ncd;
-    const float2* ins = in + (long long)s * slice;
-    float2 acc = ins[xc * ncd + i];                     // the "+1" of Dhat_W + 1
     const long long bsz = (long long)ncd * ncd;
+    const int sg = lane >> 4;
+    double nrm = 0.0;
+    for (int i = lane & 15; i < ncd; i += 16) {
+        float2 acc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = sg + 2 * k;
+            acc[k] = make_float2(0.f, 0.f);
+            if (s < p.Ls_c) acc[k] = CG ? __ldcg(in + s * slice + xc * ncd + i) : __ldg(in + s * slice + xc * ncd + i);
+        }
+        for (int dir = 0; dir < p.ndir; ++dir) {
+            const long long nb = coarse_neighbour(p, xc, dir);
+            const float2* Bb = B + (xc * p.ndir + dir) * bsz + i;
+            const float2* v = in + nb * ncd;
+#pragma unroll
+            for (int j = 0; j < ncd; ++j) {
+                const float2 y = __ldg(Bb + (long long)j * ncd);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int s = sg + 2 * k;
+                    if (s < p.Ls_c) acc[k] = cfma(y, CG ? __ldcg(v + s * slice + j) : __ldg(v + s * slice + j), acc[k]);
+                }
+            }
+        }
+        const int c = i / p.nvec;
+        const bool from_below = dag ? (c == 1) : (c == 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = sg + 2 * k;
+            if (s >= p.Ls_c) break;
+            long long hi;
+            float sc = 1.f;
+            if (from_below) { if (s > 0) hi = (s - 1) * slice; else { hi = (p.Ls_c - 1) * slice; sc = -mf; } }
+            else            { if (s < p.Ls_c - 1) hi = (s + 1) * slice; else { hi = 0; sc = -mf; } }
+            const float2 h = CG ? __ldcg(in + hi + xc * ncd + i) : __ldg(in + hi + xc * ncd + i);
+            acc[k].x += sc * h.x;
+            acc[k].y += sc * h.y;
+            out[s * slice + xc * ncd + i] = acc[k];
+            nrm += (double)acc[k].x * acc[k].x + (double)acc[k].y * acc[k].y;
+        }
+    }
+    return nrm;
+}
+
+// Specialisation for 2 nvec = 16 coarse dof and Ls_c <= 4: lane i = l & 15,
+// slices sg = l >> 4 and sg + 2.  For each direction all 16 block columns and
+// both 16-value input rows are loaded into registers before any arithmetic
+// (the inputs as 128-bit broadcast loads), so a warp keeps 32 loads in flight.
+template <bool CG>
+__device__ __forceinline__ float4 ld4(const float2* p) {
+    return CG ? __ldcg(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
+}
+
+template <bool CG>
+__device__ __forceinline__ double warp_site16(const float2* __restrict__ B, const float2* __restrict__ in,
+                                              float2* __restrict__ out, const CoarseParams& p, long long xc, float mf,
+                                              bool dag, int lane) {
+    const long long slice = p.Vc * 16;
+    const int i = lane & 15, sg = lane >> 4;
+    const bool h0 = sg < p.Ls_c, h1 = sg + 2 < p.Ls_c;
+    const int s0 = h0 ? sg : 0, s1 = h1 ? sg + 2 : 0;
+    float2 acc0 = CG ? __ldcg(in + s0 * slice + xc * 16 + i) : __ldg(in + s0 * slice + xc * 16 + i);
+    float2 acc1 = CG ? __ldcg(in + s1 * slice + xc * 16 + i) : __ldg(in + s1 * slice + xc * 16 + i);
     for (int dir = 0; dir < p.ndir; ++dir) {
         const long long nb = coarse_neighbour(p, xc, dir);
-        const float2* v = ins + nb * ncd;
-        if (!DAG) {
-            const float2* Yb = Y + (xc * p.ndir + dir) * bsz + i;     // column-major: (i, j) at j*ncd + i
-#pragma unroll 4
-            for (int j = 0; j < ncd; ++j) acc = cfma(__ldg(Yb + (long long)j * ncd), v[j], acc);
-        } else {
-            const int opp = dir == 0 ? 0 : (((dir - 1) % 2 == 0) ? dir + 1 : dir - 1);
-            const float2* Yb = Y + (nb * p.ndir + opp) * bsz + (long long)i * ncd;   // (j, i) at i*ncd + j
-#pragma unroll 4
-            for (int j = 0; j < ncd; ++j) acc = cfma_conj(__ldg(Yb + j), v[j], acc);
+        const float2* Bb = B + (xc * p.ndir + dir) * 256 + i;
+        const float2* va = in + s0 * slice + nb * 16;
+        const float2* vb = in + s1 * slice + nb * 16;
+        float2 y[16];
+        float4 a[8], b[8];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) y[j] = __ldg(Bb + j * 16);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) a[m] = ld4<CG>(va + 2 * m);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) b[m] = ld4<CG>(vb + 2 * m);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            acc0 = cfma(y[2 * m], make_float2(a[m].x, a[m].y), acc0);
+            acc0 = cfma(y[2 * m + 1], make_float2(a[m].z, a[m].w), acc0);
+            acc1 = cfma(y[2 * m], make_float2(b[m].x, b[m].y), acc1);
+            acc1 = cfma(y[2 * m + 1], make_float2(b[m].z, b[m].w), acc1);
         }
     }
     const int c = i / p.nvec;
-    const bool from_below = DAG ? (c == 1) : (c == 0);
-    float2 h;
-    if (from_below) {
-        if (s > 0) h = in[(long long)(s - 1) * slice + xc * ncd + i];
-        else { h = in[(long long)(p.Ls_c - 1) * slice + xc * ncd + i]; h.x *= -p.mf; h.y *= -p.mf; }
-    } else {
-        if (s < p.Ls_c - 1) h = in[(long long)(s + 1) * slice + xc * ncd + i];
-        else { h = in[xc * ncd + i]; h.x *= -p.mf; h.y *= -p.mf; }
+    const bool from_below = dag ? (c == 1) : (c == 0);
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool has = k == 0 ? h0 : h1;
+        if (!has) continue;
+        const int s = k == 0 ? s0 : s1;
+        float2 acc = k == 0 ? acc0 : acc1;
+        long long hi;
+        float sc = 1.f;
+        if (from_below) { if (s > 0) hi = (s - 1) * slice; else { hi = (p.Ls_c - 1) * slice; sc = -mf; } }
+        else            { if (s < p.Ls_c - 1) hi = (s + 1) * slice; else { hi = 0; sc = -mf; } }
+        const float2 hv = CG ? __ldcg(in + hi + xc * 16 + i) : __ldg(in + hi + xc * 16 + i);
+        acc.x += sc * hv.x;
+        acc.y += sc * hv.y;
+        out[s * slice + xc * 16 + i] = acc;
+        nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
     }
-    acc.x += h.x;
-    acc.y += h.y;
-    out[t] = acc;
+    return nrm;
+}
+
+// ---------------------------------------------------------------------------
+// 2-d tile kernel (16 coarse dof, Ls_c <= 4).  A block of 8 warps applies the
+// operator on a 4 x 2 tile of coarse sites, one warp per site:
+//   * the five 16 x 16 blocks of every site of the tile (10 KB contiguous per
+//     site) are copied into shared memory by one cp.async.bulk per site,
+//     completing on an mbarrier (asynchronous: no registers, all in flight);
+//   * meanwhile the threads stage the tile's inputs and their one-site halo
+//     (6 x 4 sites x Ls_c slices x 16 values) into shared memory;
+//   * the warp then multiplies from shared memory only.
+// The mbarrier wait is bounded (%globaltimer); on expiry the block records
+// an error in *status, waits once more (bounded) for its copies and returns.
+// ---------------------------------------------------------------------------
+constexpr int TILE_X = 4, TILE_Y = 2, TILE_HX = TILE_X + 2, TILE_HY = TILE_Y + 2;
+constexpr int TILE_SITES = TILE_X * TILE_Y;
+constexpr int TILE_THREADS = 32 * TILE_SITES;
+constexpr unsigned SITE_BLOCK_BYTES = 5u * 256u * sizeof(float2);   // 10240
+
+struct TileSmem {
+    float2 Y[TILE_SITES][5][256];          // column-major blocks per direction
+    float2 v[4][TILE_HY][TILE_HX][16];     // staged inputs with halo
+    unsigned long long mbar;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on phase `parity`; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long budget_ns) {
+    const unsigned long long t0 = now_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (now_ns() - t0 > budget_ns) return false;
+    }
+    return true;
+}
+
+template <bool CG>
+__device__ __forceinline__ void tile_stage(TileSmem& sm, const float2* __restrict__ in, const CoarseParams& p, int x0,
+                                           int y0) {
+    const int L0 = p.Lc[0], L1 = p.Lc[1];
+    const long long slice = p.Vc * 16;
+    const int total = p.Ls_c * TILE_HY * TILE_HX * 16;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int j = e & 15;
+        const int h = (e >> 4) % (TILE_HY * TILE_HX);
+        const int s = (e >> 4) / (TILE_HY * TILE_HX);
+        const int hx = h % TILE_HX, hy = h / TILE_HX;
+        int gx = x0 + hx - 1, gy = y0 + hy - 1;
+        gx = (gx % L0 + L0) % L0;
+        gy = (gy % L1 + L1) % L1;
+        const long long site = (long long)gy * L0 + gx;
+        sm.v[s][hy][hx][j] = CG ? __ldcg(in + s * slice + site * 16 + j) : __ldg(in + s * slice + site * 16 + j);
+    }
+}
+
+// Thread 0 starts the bulk copies of the tile's blocks (phase completes when
+// all bytes have landed).  Returns the number of bytes expected.
+__device__ __forceinline__ void tile_issue_blocks(TileSmem& sm, const float2* __restrict__ B, const CoarseParams& p,
+                                                  int x0, int y0) {
+    if (threadIdx.x != 0) return;
+    unsigned bytes = 0;
+    for (int w = 0; w < TILE_SITES; ++w) {
+        const int gx = x0 + w % TILE_X, gy = y0 + w / TILE_X;
+        if (gx < p.Lc[0] && gy < p.Lc[1]) bytes += SITE_BLOCK_BYTES;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&sm.mbar, bytes);
+    for (int w = 0; w < TILE_SITES; ++w) {
+        const int gx = x0 + w % TILE_X, gy = y0 + w / TILE_X;
+        if (gx < p.Lc[0] && gy < p.Lc[1]) {
+            const long long xc = (long long)gy * p.Lc[0] + gx;
+            bulk_g2s(&sm.Y[w][0][0], B + xc * 5 * 256, SITE_BLOCK_BYTES, &sm.mbar);
+        }
+    }
+}
+
+// Multiply for this warp's site from shared memory; returns the lane's |out|^2.
+__device__ __forceinline__ double tile_site(const TileSmem& sm, float2* __restrict__ out, const CoarseParams& p, int x0,
+                                            int y0, float mf, bool dag) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = warp % TILE_X, ty = warp / TILE_X;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx >= p.Lc[0] || gy >= p.Lc[1]) return 0.0;
+    const long long xc = (long long)gy * p.Lc[0] + gx;
+    const long long slice = p.Vc * 16;
+    const int i = lane & 15, sg = lane >> 4;
+    const bool h0 = sg < p.Ls_c, h1 = sg + 2 < p.Ls_c;
+    const int s0 = h0 ? sg : 0, s1 = h1 ? sg + 2 : 0;
+    const int hx = tx + 1, hy = ty + 1;
+    float2 acc0 = sm.v[s0][hy][hx][i], acc1 = sm.v[s1][hy][hx][i];
+#pragma unroll
+    for (int dir = 0; dir < 5; ++dir) {
+        const int nx = hx + (dir == 1 ? 1 : dir == 2 ? -1 : 0);
+        const int ny = hy + (dir == 3 ? 1 : dir == 4 ? -1 : 0);
+        const float2* Yd = &sm.Y[warp][dir][i];
+        const float4* va = reinterpret_cast<const float4*>(&sm.v[s0][ny][nx][0]);
+        const float4* vb = reinterpret_cast<const float4*>(&sm.v[s1][ny][nx][0]);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const float4 a = va[m], b = vb[m];
+            const float2 y0v = Yd[(2 * m) * 16], y1v = Yd[(2 * m + 1) * 16];
+            acc0 = cfma(y0v, make_float2(a.x, a.y), acc0);
+            acc0 = cfma(y1v, make_float2(a.z, a.w), acc0);
+            acc1 = cfma(y0v, make_float2(b.x, b.y), acc1);
+            acc1 = cfma(y1v, make_float2(b.z, b.w), acc1);
+        }
+    }
+    const int c = i / p.nvec;
+    const bool from_below = dag ? (c == 1) : (c == 0);
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool has = k == 0 ? h0 : h1;
+        if (!has) continue;
+        const int s = k == 0 ? s0 : s1;
+        float2 acc = k == 0 ? acc0 : acc1;
+        int sh;
+        float sc = 1.f;
+        if (from_below) { if (s > 0) sh = s - 1; else { sh = p.Ls_c - 1; sc = -mf; } }
+        else            { if (s < p.Ls_c - 1) sh = s + 1; else { sh = 0; sc = -mf; } }
+        const float2 hv = sm.v[sh][hy][hx][i];
+        acc.x += sc * hv.x;
+        acc.y += sc * hv.y;
+        out[s * slice + xc * 16 + i] = acc;
+        nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
+    }
+    return nrm;
+}
+
+constexpr unsigned long long TILE_WAIT_NS = 2000000000ULL;   // 2 s
+
+__global__ void __launch_bounds__(TILE_THREADS) k_coarse_tile(const float2* __restrict__ B, const float2* __restrict__ in,
+                                                              float2* __restrict__ out, CoarseParams p, bool dag,
+                                                              const int* skip, int* status) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(128) unsigned char tile_raw[];
+    TileSmem& sm = *reinterpret_cast<TileSmem*>(tile_raw);
+    const int ntx = (p.Lc[0] + TILE_X - 1) / TILE_X;
+    const int x0 = (blockIdx.x % ntx) * TILE_X, y0 = (blockIdx.x / ntx) * TILE_Y;
+    if (threadIdx.x == 0) mbar_init(&sm.mbar, 1);
+    __syncthreads();
+    tile_issue_blocks(sm, B, p, x0, y0);
+    tile_stage<false>(sm, in, p, x0, y0);
+    __syncthreads();
+    if (!mbar_wait_bounded(&sm.mbar, 0, TILE_WAIT_NS)) {
+        if (threadIdx.x == 0) atomicExch(status, 2);
+        mbar_wait_bounded(&sm.mbar, 0, TILE_WAIT_NS);     // let the copies land before the block exits
+        return;
+    }
+    tile_site(sm, out, p, x0, y0, p.mf, dag);
+}
+
+static bool tile_ok(const CoarseParams& p) { return p.nd == 2 && p.ncd == 16 && p.Ls_c <= 4; }
+
+template <int NCD>
+__global__ void __launch_bounds__(256) k_coarse_dwf(const float2* __restrict__ B, const float2* __restrict__ in,
+                                                    float2* __restrict__ out, CoarseParams p, bool dag, const int* skip) {
+    if (skip && *skip) return;
+    const long long xc = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (xc >= p.Vc) return;
+    if (NCD == 16 && p.Ls_c <= 4) warp_site16<false>(B, in, out, p, xc, p.mf, dag, threadIdx.x & 31);
+    else warp_site_apply<NCD, false>(B, in, out, p, xc, p.mf, dag, threadIdx.x & 31);
 }
 
 static CoarseParams coarse_params(const dwf_mg* h, double mf) {
@@ -104,11 +366,49 @@ static CoarseParams coarse_params(const dwf_mg* h, double mf) {
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger, const int* skip,
                             cudaStream_t st) {
     CoarseParams p = coarse_params(h, mf);
-    const long long total = p.Vc * p.Ls_c * p.ncd;
+    if (p.Ls_c > 8) { set_error("the coarse stencil supports Ls_c <= 8"); return DWF_ERR_UNSUPPORTED; }
     const int thr = 256;
-    const unsigned grid = (unsigned)((total + thr - 1) / thr);
-    if (dagger) k_coarse_dwf<true><<<grid, thr, 0, st>>>(h->Y32, in, out, p, skip);
-    else        k_coarse_dwf<false><<<grid, thr, 0, st>>>(h->Y32, in, out, p, skip);
+    const unsigned grid = (unsigned)((p.Vc * 32 + thr - 1) / thr);
+    const float2* B = dagger ? h->Yd32 : h->Y32;
+    if (tile_ok(p)) {
+        const int ntiles = ((p.Lc[0] + TILE_X - 1) / TILE_X) * ((p.Lc[1] + TILE_Y - 1) / TILE_Y);
+        static bool attr_set[64] = {};
+        int dev = 0;
+        DWF_CHECK_CUDA(cudaGetDevice(&dev));
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)));
+            attr_set[dev] = true;
+        }
+        k_coarse_tile<<<ntiles, TILE_THREADS, sizeof(TileSmem), st>>>(B, in, out, p, dagger, skip, h->status + 1);
+    } else if (p.ncd == 16) k_coarse_dwf<16><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
+    else             k_coarse_dwf<0><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+// Yd[x][dir] (column-major) = Y[x + dir][-dir]^dag from the row-major FP64 blocks.
+__global__ void k_adjoint_blocks(const double2* __restrict__ Y, float2* __restrict__ Yd, CoarseParams p) {
+    const int ncd = p.ncd;
+    const long long bsz = (long long)ncd * ncd;
+    const long long n = p.Vc * p.ndir * bsz;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long blk = t / bsz;
+        const int e = (int)(t % bsz);           // column-major index j * ncd + i
+        const long long xc = blk / p.ndir;
+        const int dir = (int)(blk % p.ndir);
+        const int opp = dir == 0 ? 0 : (((dir - 1) % 2 == 0) ? dir + 1 : dir - 1);
+        const long long nb = coarse_neighbour(p, xc, dir);
+        // element (i, j) of the adjoint block = conj(Y_nb,opp(j, i)); row-major (j, i) sits at j * ncd + i
+        const double2 v = Y[(nb * p.ndir + opp) * bsz + e];
+        Yd[t] = make_float2((float)v.x, (float)-v.y);
+    }
+}
+
+dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st) {
+    CoarseParams p = coarse_params(h, h->mf);
+    const long long n = p.Vc * p.ndir * (long long)p.ncd * p.ncd;
+    const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    k_adjoint_blocks<<<grid, 256, 0, st>>>(h->Y64, h->Yd32, p);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }
@@ -265,3 +565,282 @@ dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, double mf
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Persistent coarse CGNR: one cooperative launch per coarse solve.
+//
+// Solves (Dhat_PV^dag Dhat_DW)^dag (Dhat_PV^dag Dhat_DW) e = (..)^dag r_c by CG
+// (the coarsest-level CGNR of Table kcycle), with every block resident for
+// the whole solve and phases separated by a software grid barrier.  The
+// barrier's spin is bounded by a %globaltimer deadline: on expiry the block
+// raises an error flag that every other block sees at its next barrier, and
+// all blocks return (the host reports DWF_ERR_TIMEOUT).  Reductions: each
+// block writes one FP64 partial per quantity; after the barrier every block
+// sums all partials in the same order, so all blocks hold identical scalars.
+// Mutable vectors are read through L2 (ld.global.cg) because other blocks wrote
+// them earlier in the same launch.
+// ===========================================================================
+namespace dwf {
+
+constexpr int PCG_THREADS = 256;
+
+struct PcgBarrier {
+    unsigned count;
+    unsigned gen;
+    int error;
+    int pad;
+};
+
+struct PcgArgs {
+    CoarseParams cp;
+    const float2* Y;    // Galerkin blocks (column-major)
+    const float2* Yd;   // adjoint blocks (column-major)
+    const float2* rc;   // right-hand side
+    float2* e;          // solution
+    float2 *rr, *r, *p, *q, *t, *w;
+    double* partials;   // [3][gridDim.x]
+    PcgBarrier* bar;
+    int* out_iters;
+    double* out_rr2;    // final |rr|^2 / |rc|^2
+    double tol2;
+    int maxiter;
+    double mf;
+    unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false if the barrier timed out here or anywhere else, or if this
+// block reports a failure of its own (local_ok == false).
+__device__ bool pcg_sync(PcgBarrier* b, unsigned long long deadline, bool local_ok = true) {
+    __shared__ int ok;
+    __shared__ int any_fail;
+    if (threadIdx.x == 0) any_fail = 0;
+    __syncthreads();
+    if (!local_ok) any_fail = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (any_fail) atomicExch(&b->error, 1);
+        volatile unsigned* vgen = &b->gen;
+        volatile int* verr = &b->error;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            b->count = 0u;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            while (*vgen == g) {
+                if (*verr) break;
+                if (global_ns() > deadline) { atomicExch(&b->error, 1); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = (*verr == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// block-sum of up to 3 doubles into partials[k * grid + block]
+__device__ void pcg_partial(double (&v)[3], int nv, double* partials) {
+    __shared__ double sh[3][PCG_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < nv; ++k)
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+        for (int k = 0; k < nv; ++k) sh[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nv; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < PCG_THREADS / 32; ++w) s += sh[k][w];
+            partials[k * gridDim.x + blockIdx.x] = s;
+        }
+    __syncthreads();
+}
+
+// every block: fixed-order total of partial k
+__device__ double pcg_total(const double* partials, int k) {
+    __shared__ double tot;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + k * gridDim.x + b);
+        tot = s;
+    }
+    __syncthreads();
+    const double r = tot;
+    __syncthreads();
+    return r;
+}
+
+// out = Dhat_DW(m) in (or adjoint) over all tiles (grid-stride), shared-memory
+// tiles as in k_coarse_tile.  `phase` is this block's mbarrier parity, flipped
+// per tile.  Returns this thread's share of |out|^2; false in *ok on a timeout.
+__device__ double pcg_apply(const PcgArgs& a, TileSmem& sm, unsigned& phase, const float2* __restrict__ in,
+                            float2* __restrict__ out, double mf, bool dag, bool* ok) {
+    const CoarseParams& p = a.cp;
+    const float2* B = dag ? a.Yd : a.Y;
+    const int ntx = (p.Lc[0] + TILE_X - 1) / TILE_X;
+    const int ntiles = ntx * ((p.Lc[1] + TILE_Y - 1) / TILE_Y);
+    double nrm = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % ntx) * TILE_X, y0 = (tile / ntx) * TILE_Y;
+        __syncthreads();                        // previous tile's shared data fully consumed
+        tile_issue_blocks(sm, B, p, x0, y0);
+        tile_stage<true>(sm, in, p, x0, y0);
+        __syncthreads();
+        if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
+            mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
+            *ok = false;
+            return nrm;
+        }
+        phase ^= 1u;
+        nrm += tile_site(sm, out, p, x0, y0, (float)mf, dag);
+    }
+    return nrm;
+}
+
+#define PCG_LOOP(k, n) for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (n); k += (long long)gridDim.x * blockDim.x)
+
+__global__ void __launch_bounds__(PCG_THREADS) k_coarse_cgnr_persistent(PcgArgs a) {
+    extern __shared__ __align__(128) unsigned char pcg_raw[];
+    TileSmem& sm = *reinterpret_cast<TileSmem*>(pcg_raw);
+    const long long n = a.cp.Vc * a.cp.Ls_c * a.cp.ncd;
+    const unsigned long long deadline = global_ns() + a.timeout_ns;
+    const double mf = a.mf;
+    unsigned phase = 0;
+    bool ok = true;
+    if (threadIdx.x == 0) mbar_init(&sm.mbar, 1);
+    __syncthreads();
+    // prologue: e = 0, rr = rc, t = Dhat_PV rr, r = Dhat_DW^dag t (= B^dag rr), p = r
+    PCG_LOOP(k, n) { a.e[k] = make_float2(0.f, 0.f); a.rr[k] = __ldcg(a.rc + k); }
+    if (!pcg_sync(a.bar, deadline, ok)) return;
+    pcg_apply(a, sm, phase, a.rr, a.t, 1.0, false, &ok);
+    if (!pcg_sync(a.bar, deadline, ok)) return;
+    double v[3] = {pcg_apply(a, sm, phase, a.t, a.r, mf, true, &ok), 0.0, 0.0};
+    PCG_LOOP(k, n) {
+        float2 y = __ldcg(a.rc + k);
+        v[1] += (double)y.x * y.x + (double)y.y * y.y;
+    }
+    pcg_partial(v, 2, a.partials);
+    if (!pcg_sync(a.bar, deadline, ok)) return;
+    PCG_LOOP(k, n) a.p[k] = __ldcg(a.r + k);
+    double rn2 = pcg_total(a.partials, 0);
+    const double bn2 = pcg_total(a.partials, 1);
+    double rr2 = bn2;
+    int it = 0;
+    if (bn2 > 0.0 && rn2 > 0.0) {
+        while (it < a.maxiter) {
+            // q = Dhat_PV^dag Dhat_DW p  (p = r on the first pass: r is complete,
+            // the copy into p is not visible to other blocks yet)
+            pcg_apply(a, sm, phase, it == 0 ? a.r : a.p, a.t, mf, false, &ok);
+            if (!pcg_sync(a.bar, deadline, ok)) return;
+            double u[3] = {pcg_apply(a, sm, phase, a.t, a.q, 1.0, true, &ok), 0.0, 0.0};
+            pcg_partial(u, 1, a.partials);
+            if (!pcg_sync(a.bar, deadline, ok)) return;
+            const double qq = pcg_total(a.partials, 0);
+            if (!(qq > 0.0)) break;
+            const double alpha = rn2 / qq;
+            const float af = (float)alpha;
+            // e += alpha p; rr -= alpha q; t = Dhat_PV q (q is complete)
+            double u2[3] = {0.0, 0.0, 0.0};
+            PCG_LOOP(k, n) {
+                float2 pk = __ldcg(a.p + k), qk = __ldcg(a.q + k), ek = __ldcg(a.e + k), rk = __ldcg(a.rr + k);
+                ek.x += af * pk.x; ek.y += af * pk.y;
+                rk.x -= af * qk.x; rk.y -= af * qk.y;
+                a.e[k] = ek; a.rr[k] = rk;
+                u2[0] += (double)rk.x * rk.x + (double)rk.y * rk.y;
+            }
+            pcg_partial(u2, 1, a.partials + 2 * gridDim.x);
+            pcg_apply(a, sm, phase, a.q, a.t, 1.0, false, &ok);
+            if (!pcg_sync(a.bar, deadline, ok)) return;
+            rr2 = pcg_total(a.partials, 2);
+            ++it;
+            if (rr2 <= a.tol2 * bn2) break;
+            // w = Dhat_DW^dag t; r -= alpha w
+            pcg_apply(a, sm, phase, a.t, a.w, mf, true, &ok);
+            if (!pcg_sync(a.bar, deadline, ok)) return;
+            double u3[3] = {0.0, 0.0, 0.0};
+            PCG_LOOP(k, n) {
+                float2 rk = __ldcg(a.r + k), wk = __ldcg(a.w + k);
+                rk.x -= af * wk.x; rk.y -= af * wk.y;
+                a.r[k] = rk;
+                u3[0] += (double)rk.x * rk.x + (double)rk.y * rk.y;
+            }
+            pcg_partial(u3, 1, a.partials + gridDim.x);
+            if (!pcg_sync(a.bar, deadline, ok)) return;
+            const double rn2n = pcg_total(a.partials, 1);
+            const float beta = (float)(rn2n / rn2);
+            rn2 = rn2n;
+            PCG_LOOP(k, n) {
+                float2 pk = __ldcg(a.p + k), rk = __ldcg(a.r + k);
+                a.p[k] = make_float2(rk.x + beta * pk.x, rk.y + beta * pk.y);
+            }
+            if (!pcg_sync(a.bar, deadline, ok)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.out_iters += it;                       // running total over solves
+        *a.out_rr2 = bn2 > 0 ? rr2 / bn2 : 0.0;
+    }
+}
+
+struct PcgPlan {
+    int grid = 0;
+};
+
+static PcgPlan g_pcg_plan[64];
+
+dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* vec6, double* partials,
+                                  void* bar, int* out_iters, double* out_rr2, cudaStream_t st) {
+    int dev = 0;
+    DWF_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device ordinal out of range"); return DWF_ERR_UNSUPPORTED; }
+    if (h->mg.Ls_c > 4 || h->mg.ncd != 16 || h->mg.nd != 2) {
+        set_error("persistent coarse solver supports 2-d, 16 coarse dof and Ls_c <= 4");
+        return DWF_ERR_UNSUPPORTED;
+    }
+    PcgPlan& plan = g_pcg_plan[dev];
+    if (plan.grid == 0) {
+        int nsm = 0, per = 0;
+        DWF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_cgnr_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(TileSmem)));
+        DWF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_cgnr_persistent, PCG_THREADS,
+                                                                     sizeof(TileSmem)));
+        if (per < 1) { set_error("persistent coarse solver cannot be resident"); return DWF_ERR_UNSUPPORTED; }
+        plan.grid = nsm * per;
+    }
+    PcgArgs a;
+    a.cp = coarse_params(h, h->mf);
+    a.Y = h->Y32;
+    a.Yd = h->Yd32;
+    a.rc = rc;
+    a.e = ec;
+    a.rr = vec6[0]; a.r = vec6[1]; a.p = vec6[2]; a.q = vec6[3]; a.t = vec6[4]; a.w = vec6[5];
+    a.partials = partials;
+    a.bar = (PcgBarrier*)bar;
+    a.out_iters = out_iters;
+    a.out_rr2 = out_rr2;
+    a.tol2 = h->prm.coarse_tol * h->prm.coarse_tol;
+    a.maxiter = h->prm.coarse_maxiter;
+    a.mf = h->mf;
+    a.timeout_ns = 5000000000ULL;   // 5 s per solve
+    const int ntiles = ((a.cp.Lc[0] + TILE_X - 1) / TILE_X) * ((a.cp.Lc[1] + TILE_Y - 1) / TILE_Y);
+    int grid = plan.grid < ntiles ? plan.grid : ntiles;
+    if (grid < 1) grid = 1;
+    DWF_CHECK_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));   // count, gen; the error flag persists
+    void* args[] = {&a};
+    DWF_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_cgnr_persistent, dim3(grid), dim3(PCG_THREADS), args,
+                                               sizeof(TileSmem), st));
+    return DWF_OK;
+}
+
+}  // namespace dwf

@@ -361,6 +361,7 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
     const long long nblk = m.Vc * m.ndir;
     DWF_TRY(mg_alloc(h, (void**)&h->Y64, nblk * m.ncd * m.ncd * sizeof(double2)));
     DWF_TRY(mg_alloc(h, (void**)&h->Y32, nblk * m.ncd * m.ncd * sizeof(float2)));
+    DWF_TRY(mg_alloc(h, (void**)&h->Yd32, nblk * m.ncd * m.ncd * sizeof(float2)));
     if (m.nd == 2) {
         dim3 grid((unsigned)m.Vc, 5);
         int thr = m.ncd * m.ncd < 256 ? m.ncd * m.ncd : 256;
@@ -373,6 +374,7 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
     }
     k_blocks_to_f32<<<ew_grid(nblk * m.ncd * m.ncd), 256, 0, st>>>(h->Y64, h->Y32, nblk, m.ncd);
     DWF_CHECK_LAUNCH();
+    DWF_TRY(build_adjoint_blocks(h, st));
     int hstat = 0;
     DWF_CHECK_CUDA(cudaMemcpyAsync(&hstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     DWF_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -406,6 +408,7 @@ void dwf_mg_default_params(dwf_mg_params* p) {
     p->fine_prec = DWF_F32_L16;
     p->inner_tol = 1e-5;
     p->max_restarts = 1000;
+    p->coarse_persistent = 1;
 }
 
 dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,

@@ -43,6 +43,10 @@ struct SolveScal {
     GcrScal smooth;
     CoarseCg ccg;
     double misc[8];
+    double pcg_rr2;
+    int pcg_iters;
+    int pad;
+    unsigned bar[4];
 };
 
 // --------------------------------------------------------------------------
@@ -233,6 +237,7 @@ struct Solver {
     float2 *rc, *ec, *crr, *cr, *cp, *cq, *cw, *ct;
     // FP64
     double2 *r64, *t64;
+    double* partials;    // persistent coarse solver partial sums
     long long fine_applies, coarse_applies, coarse_iters, coarse_solves;
 };
 
@@ -247,9 +252,9 @@ static dwf_status ensure_workspace(dwf_mg* h) {
         if (e != cudaSuccess) { set_error("solver vectors: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
         h->fine_vecs.push_back(p);
     }
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 9; ++k) {      // 8 coarse vectors + partial sums of the persistent solver
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, nc * sizeof(float2) + 256);
+        cudaError_t e = cudaMalloc(&p, k < 8 ? nc * sizeof(float2) + 256 : 3 * 4096 * sizeof(double));
         if (e != cudaSuccess) { set_error("coarse vectors: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
         h->coarse_vecs.push_back(p);
     }
@@ -279,7 +284,8 @@ static void bind(Solver& s, dwf_mg* h) {
     for (int k = 0; k < h->prm.post_smooth; ++k) { s.Ps[k] = F(); s.Qs[k] = F(); }
     auto C = [&](int j) { return (float2*)h->coarse_vecs[j]; };
     s.rc = C(0); s.ec = C(1); s.crr = C(2); s.cr = C(3); s.cp = C(4); s.cq = C(5); s.cw = C(6); s.ct = C(7);
-    s.d = (SolveScal*)h->coarse_vecs[8];
+    s.partials = (double*)h->coarse_vecs[8];
+    s.d = (SolveScal*)h->coarse_vecs[9];
     s.hs = (SolveScal*)h->hsc;
     s.r64 = (double2*)h->r64;
     s.t64 = (double2*)h->x64;
@@ -321,6 +327,12 @@ static dwf_status gcr_orthogonalise(Solver& s, GcrScal* g, float2** Zb, float2**
 // Coarse solve: CGNR on B^dag B e = B^dag r, B = Dhat_PV^dag Dhat_DW.
 static dwf_status coarse_solve(Solver& s) {
     dwf_mg* h = s.h;
+    if (h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
+        float2* v6[6] = {s.crr, s.cr, s.cp, s.cq, s.ct, s.cw};
+        DWF_TRY(coarse_cgnr_persistent(h, s.rc, s.ec, v6, s.partials, s.d->bar, &s.d->pcg_iters, &s.d->pcg_rr2, s.st));
+        s.coarse_solves += 1;
+        return DWF_OK;
+    }
     RedScratch rs = h->ws.red();
     CoarseCg* S = &s.d->ccg;
     const int* done = &S->done;
@@ -425,6 +437,8 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
     double2* X = (double2*)x;
     RedScratch rs = h->ws.red();
     DWF_CHECK_CUDA(cudaMemsetAsync(X, 0, n * sizeof(double2), s.st));
+    DWF_CHECK_CUDA(cudaMemsetAsync(&s.d->pcg_iters, 0, sizeof(int), s.st));
+    DWF_CHECK_CUDA(cudaMemsetAsync(s.d->bar, 0, sizeof(s.d->bar), s.st));
     DWF_TRY(dot_device(B, B, n, true, rs, s.d->misc, s.st));
     DWF_CHECK_CUDA(cudaMemcpyAsync(s.hs->misc, s.d->misc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s.st));
     DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
@@ -468,11 +482,36 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
             DWF_CHECK_LAUNCH();
             ++outer;
             DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->outer.rr2, &g->rr2, sizeof(double), cudaMemcpyDeviceToHost, s.st));
+            DWF_CHECK_CUDA(cudaMemcpyAsync(s.hs->bar, s.d->bar, sizeof(s.d->bar), cudaMemcpyDeviceToHost, s.st));
             DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
+            if (s.hs->bar[2] != 0u) {
+                set_error("persistent coarse solver: a grid barrier timed out");
+                return DWF_ERR_TIMEOUT;
+            }
             if (s.hs->outer.rr2 <= delta * delta * rA2) break;
         }
         k_axpy_64_32<<<s.eg, 256, 0, s.st>>>(X, s.e, rn, n);
         DWF_CHECK_LAUNCH();
+    }
+    if (h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
+        DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->pcg_iters, &s.d->pcg_iters, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaMemcpyAsync(s.hs->bar, s.d->bar, sizeof(s.d->bar), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
+        s.coarse_iters = s.hs->pcg_iters;
+        s.coarse_applies = 2 * s.coarse_solves + 4LL * s.coarse_iters;
+        if (s.hs->bar[2] != 0u) {
+            set_error("persistent coarse solver: a grid barrier or bulk copy timed out");
+            status = DWF_ERR_TIMEOUT;
+        }
+    }
+    {
+        int st1 = 0;
+        DWF_CHECK_CUDA(cudaMemcpyAsync(&st1, h->status + 1, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
+        if (st1 != 0) {
+            set_error("coarse stencil: a bulk copy wait timed out");
+            status = DWF_ERR_TIMEOUT;
+        }
     }
     if (status != DWF_OK && dwf_last_error()[0] == 0)
         set_error("mg_solve stopped after %d outer iterations with true residual %.3e > tol %.3e", outer, res, tol);
