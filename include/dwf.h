@@ -163,12 +163,17 @@ typedef struct {
     int gcr_restart;      /* outer flexible GCR restart length (16)                            */
     int pre_smooth;       /* GCR pre-smoothing iterations (0)                                  */
     int post_smooth;      /* GCR post-smoothing iterations on the accumulated error (8)        */
-    double coarse_tol;    /* coarsest CGNR relative residual tolerance (0.05)                  */
-    int coarse_maxiter;   /* coarsest CGNR iteration cap (1024)                                */
+    double coarse_tol;    /* coarse-solve relative residual tolerance: 0.25 with GCR (the
+                             paper's level-2 value), 0.05 for CGNR (its coarsest level)  */
+    int coarse_maxiter;   /* coarse-solve iteration cap (1024)                                 */
     int fine_prec;        /* storage of the fine links in the inner solve (DWF_F32_L16)        */
     double inner_tol;     /* floor of the residual reduction of one reliable-update cycle      */
     int max_restarts;     /* reliable-update cycles before giving up                          */
     int coarse_persistent;/* 1: the coarsest CGNR runs as one cooperative persistent launch    */
+    int coarse_solver;    /* 0: CGNR on the coarse normal operator (Table kcycle, coarsest
+                             level); 1: restarted GCR on Dhat_PV^dag Dhat_DW (the paper's
+                             level-2 solver; valid by the right-half-plane property, App. B) */
+    int coarse_restart;   /* restart length of the coarse GCR (16)                        */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;

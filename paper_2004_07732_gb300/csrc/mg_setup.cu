@@ -403,12 +403,14 @@ void dwf_mg_default_params(dwf_mg_params* p) {
     p->gcr_restart = 16;
     p->pre_smooth = 0;
     p->post_smooth = 8;
-    p->coarse_tol = 0.05;
+    p->coarse_tol = 0.25;
     p->coarse_maxiter = 1024;
     p->fine_prec = DWF_F32_L16;
     p->inner_tol = 1e-5;
     p->max_restarts = 1000;
     p->coarse_persistent = 1;
+    p->coarse_solver = 1;
+    p->coarse_restart = 16;
 }
 
 dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,

@@ -41,6 +41,9 @@ struct CoarseCg {
 struct SolveScal {
     GcrScal outer;
     GcrScal smooth;
+    GcrScal cgcr;        // coarse GCR
+    int cdone, citers;   // coarse GCR stop flag and iteration count (per solve)
+    double cref2;        // |r_c|^2 of the coarse right-hand side
     CoarseCg ccg;
     double misc[8];
     double pcg_rr2;
@@ -56,7 +59,9 @@ struct SolveScal {
 
 // coef = <Wj, w> / nrm_j
 __global__ void __launch_bounds__(RED_THREADS) k_ortho_first(const float2* __restrict__ Wj, const float2* __restrict__ w,
-                                                             long long n, RedScratch rs, double* coef, const double* nrm_j) {
+                                                             long long n, RedScratch rs, double* coef, const double* nrm_j,
+                                                             const int* skip) {
+    if (skip && *skip) return;
     double v[2] = {0.0, 0.0};
     GRID_LOOP(i, n) {
         float2 a = Wj[i], b = w[i];
@@ -78,7 +83,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_ortho_step(float2* __restrict__
                                                             const float2* __restrict__ Wj, const float2* __restrict__ Zj,
                                                             const double* coef, const float2* __restrict__ Wn,
                                                             const float2* __restrict__ r, long long n, RedScratch rs,
-                                                            double* out, const double* nrm_next, double* alpha_out) {
+                                                            double* out, const double* nrm_next, double* alpha_out,
+                                                            const int* skip) {
+    if (skip && *skip) return;
     float cr = 0.f, ci = 0.f;
     if (Wj) { cr = (float)coef[0]; ci = (float)coef[1]; }
     double v[3] = {0.0, 0.0, 0.0};
@@ -114,10 +121,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_ortho_step(float2* __restrict__
     });
 }
 
-// x += alpha z, r -= alpha w, rr2 = |r|^2
+// x += alpha z, r -= alpha w, rr2 = |r|^2.  With a stop flag: skipped once
+// *done is set, and *done is set when rr2 <= tol2 * (*ref2) or the iteration
+// counter reaches maxit.
 __global__ void __launch_bounds__(RED_THREADS) k_gcr_update(float2* __restrict__ x, float2* __restrict__ r,
                                                             const float2* __restrict__ z, const float2* __restrict__ w,
-                                                            const double* alpha, long long n, RedScratch rs, double* rr2) {
+                                                            const double* alpha, long long n, RedScratch rs, double* rr2,
+                                                            int* done, const double* ref2, double tol2, int* iters,
+                                                            int maxit) {
+    if (done && *done) return;
     const float ar = (float)alpha[0], ai = (float)alpha[1];
     double v[1] = {0.0};
     GRID_LOOP(i, n) {
@@ -127,7 +139,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_update(float2* __restrict__
         x[i] = xi; r[i] = ri;
         v[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
     }
-    grid_reduce<1>(v, rs, [=] __device__(double* t) { *rr2 = t[0]; });
+    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+        *rr2 = t[0];
+        if (done) {
+            *iters += 1;
+            if (t[0] <= tol2 * (*ref2) || *iters >= maxit) *done = 1;
+        }
+    });
 }
 
 __global__ void k_sub32(float2* __restrict__ out, const float2* __restrict__ a, const float2* __restrict__ b, long long n) {
@@ -238,6 +256,7 @@ struct Solver {
     // FP64
     double2 *r64, *t64;
     double* partials;    // persistent coarse solver partial sums
+    float2 *Zc[GCR_MAXK], *Wc[GCR_MAXK];   // coarse GCR basis
     long long fine_applies, coarse_applies, coarse_iters, coarse_solves;
 };
 
@@ -252,9 +271,10 @@ static dwf_status ensure_workspace(dwf_mg* h) {
         if (e != cudaSuccess) { set_error("solver vectors: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
         h->fine_vecs.push_back(p);
     }
-    for (int k = 0; k < 9; ++k) {      // 8 coarse vectors + partial sums of the persistent solver
+    const int KC = h->prm.coarse_restart;
+    for (int k = 0; k < 9 + 2 * KC; ++k) {   // 8 coarse vectors, persistent-solver partials, coarse GCR basis
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, k < 8 ? nc * sizeof(float2) + 256 : 3 * 4096 * sizeof(double));
+        cudaError_t e = cudaMalloc(&p, k == 8 ? 3 * 4096 * sizeof(double) : nc * sizeof(float2) + 256);
         if (e != cudaSuccess) { set_error("coarse vectors: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
         h->coarse_vecs.push_back(p);
     }
@@ -285,7 +305,11 @@ static void bind(Solver& s, dwf_mg* h) {
     auto C = [&](int j) { return (float2*)h->coarse_vecs[j]; };
     s.rc = C(0); s.ec = C(1); s.crr = C(2); s.cr = C(3); s.cp = C(4); s.cq = C(5); s.cw = C(6); s.ct = C(7);
     s.partials = (double*)h->coarse_vecs[8];
-    s.d = (SolveScal*)h->coarse_vecs[9];
+    for (int k = 0; k < h->prm.coarse_restart; ++k) {
+        s.Zc[k] = (float2*)h->coarse_vecs[9 + 2 * k];
+        s.Wc[k] = (float2*)h->coarse_vecs[10 + 2 * k];
+    }
+    s.d = (SolveScal*)h->coarse_vecs[9 + 2 * h->prm.coarse_restart];
     s.hs = (SolveScal*)h->hsc;
     s.r64 = (double2*)h->r64;
     s.t64 = (double2*)h->x64;
@@ -303,30 +327,72 @@ static dwf_status apply_A(Solver& s, const float2* in, float2* out) {
 
 // Orthogonalise (z, w) = (Z[k], W[k]) against the first k pairs of the basis
 // and compute nrm[k], alpha = <w, r> / nrm[k].
-static dwf_status gcr_orthogonalise(Solver& s, GcrScal* g, float2** Zb, float2** Wb, int k, const float2* r, long long n) {
+static dwf_status gcr_orthogonalise(Solver& s, GcrScal* g, float2** Zb, float2** Wb, int k, const float2* r, long long n,
+                                    const int* skip = nullptr) {
     RedScratch rs = s.h->ws.red();
+    const int rg = red_grid(n);
     if (k == 0) {
-        k_ortho_step<true><<<s.rg, RED_THREADS, 0, s.st>>>(Wb[0], Zb[0], nullptr, nullptr, nullptr, nullptr, r, n, rs,
-                                                           &g->nrm[0], nullptr, g->alpha);
+        k_ortho_step<true><<<rg, RED_THREADS, 0, s.st>>>(Wb[0], Zb[0], nullptr, nullptr, nullptr, nullptr, r, n, rs,
+                                                         &g->nrm[0], nullptr, g->alpha, skip);
         DWF_CHECK_LAUNCH();
         return DWF_OK;
     }
-    k_ortho_first<<<s.rg, RED_THREADS, 0, s.st>>>(Wb[0], Wb[k], n, rs, g->coef[0], &g->nrm[0]);
+    k_ortho_first<<<rg, RED_THREADS, 0, s.st>>>(Wb[0], Wb[k], n, rs, g->coef[0], &g->nrm[0], skip);
     for (int j = 0; j < k; ++j) {
         if (j + 1 < k)
-            k_ortho_step<false><<<s.rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], Wb[j], Zb[j], g->coef[j], Wb[j + 1], nullptr,
-                                                                n, rs, g->coef[j + 1], &g->nrm[j + 1], nullptr);
+            k_ortho_step<false><<<rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], Wb[j], Zb[j], g->coef[j], Wb[j + 1], nullptr,
+                                                              n, rs, g->coef[j + 1], &g->nrm[j + 1], nullptr, skip);
         else
-            k_ortho_step<true><<<s.rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], Wb[j], Zb[j], g->coef[j], nullptr, r, n, rs,
-                                                               &g->nrm[k], nullptr, g->alpha);
+            k_ortho_step<true><<<rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], Wb[j], Zb[j], g->coef[j], nullptr, r, n, rs,
+                                                             &g->nrm[k], nullptr, g->alpha, skip);
     }
     DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+// Coarse solve with restarted GCR on B e = r_c, B = Dhat_PV^dag Dhat_DW (the
+// paper's level-2 operator and solver type; B's spectrum lies in the right
+// half plane, App. B).  Iterations run in batches of one restart cycle with a
+// device-side stop flag; the host reads the flag once per cycle.
+static dwf_status coarse_solve_gcr(Solver& s) {
+    dwf_mg* h = s.h;
+    const long long n = s.nc;
+    RedScratch rs = h->ws.red();
+    GcrScal* g = &s.d->cgcr;
+    int* done = &s.d->cdone;
+    const int K = h->prm.coarse_restart;
+    const int maxit = h->prm.coarse_maxiter;
+    const double tol2 = h->prm.coarse_tol * h->prm.coarse_tol;
+    DWF_CHECK_CUDA(cudaMemsetAsync(s.ec, 0, n * sizeof(float2), s.st));
+    DWF_CHECK_CUDA(cudaMemcpyAsync(s.crr, s.rc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
+    DWF_CHECK_CUDA(cudaMemsetAsync(&s.d->cdone, 0, 2 * sizeof(int), s.st));
+    DWF_TRY(dot_device(s.rc, s.rc, n, false, rs, s.d->misc + 4, s.st));
+    DWF_CHECK_CUDA(cudaMemcpyAsync(&s.d->cref2, s.d->misc + 4, sizeof(double), cudaMemcpyDeviceToDevice, s.st));
+    int launched = 0;
+    while (launched < maxit) {
+        for (int k = 0; k < K && launched < maxit; ++k, ++launched) {
+            DWF_CHECK_CUDA(cudaMemcpyAsync(s.Zc[k], s.crr, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
+            DWF_TRY(coarse_dwf_apply(h, s.Zc[k], s.ct, h->mf, false, done, s.st));
+            DWF_TRY(coarse_dwf_apply(h, s.ct, s.Wc[k], 1.0, true, done, s.st));
+            DWF_TRY(gcr_orthogonalise(s, g, s.Zc, s.Wc, k, s.crr, n, done));
+            k_gcr_update<<<s.rgc, RED_THREADS, 0, s.st>>>(s.ec, s.crr, s.Zc[k], s.Wc[k], g->alpha, n, rs, &g->rr2, done,
+                                                          &s.d->cref2, tol2, &s.d->citers, maxit);
+            DWF_CHECK_LAUNCH();
+        }
+        DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->cdone, &s.d->cdone, 2 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
+        if (s.hs->cdone) break;
+    }
+    s.coarse_iters += s.hs->citers;
+    s.coarse_applies += 2LL * s.hs->citers;
+    s.coarse_solves += 1;
     return DWF_OK;
 }
 
 // Coarse solve: CGNR on B^dag B e = B^dag r, B = Dhat_PV^dag Dhat_DW.
 static dwf_status coarse_solve(Solver& s) {
     dwf_mg* h = s.h;
+    if (h->prm.coarse_solver == 1) return coarse_solve_gcr(s);
     if (h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
         float2* v6[6] = {s.crr, s.cr, s.cp, s.cq, s.ct, s.cw};
         DWF_TRY(coarse_cgnr_persistent(h, s.rc, s.ec, v6, s.partials, s.d->bar, &s.d->pcg_iters, &s.d->pcg_rr2, s.st));
@@ -392,7 +458,8 @@ static dwf_status precondition(Solver& s, const float2* r, float2* zout, float2*
         DWF_CHECK_CUDA(cudaMemcpyAsync(s.Ps[j], s.rs_, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
         DWF_TRY(apply_A(s, s.Ps[j], s.Qs[j]));
         DWF_TRY(gcr_orthogonalise(s, g, s.Ps, s.Qs, j, s.rs_, n));
-        k_gcr_update<<<s.rg, RED_THREADS, 0, s.st>>>(zout, s.rs_, s.Ps[j], s.Qs[j], g->alpha, n, rs, &g->rr2);
+        k_gcr_update<<<s.rg, RED_THREADS, 0, s.st>>>(zout, s.rs_, s.Ps[j], s.Qs[j], g->alpha, n, rs, &g->rr2,
+                                                     nullptr, nullptr, 0.0, nullptr, 0);
         DWF_CHECK_LAUNCH();
     }
     // A z = r - r_s
@@ -425,8 +492,9 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
     if (stats) memset(stats, 0, sizeof(*stats));
     if (!h || !b || !x) { set_error("NULL argument"); return DWF_ERR_ARG; }
     if (!(tol > 0.0)) { set_error("tol must be > 0"); return DWF_ERR_ARG; }
-    if (h->prm.gcr_restart > GCR_MAXK || h->prm.post_smooth > GCR_MAXK) {
-        set_error("gcr_restart and post_smooth must be <= %d", GCR_MAXK); return DWF_ERR_ARG;
+    if (h->prm.gcr_restart > GCR_MAXK || h->prm.post_smooth > GCR_MAXK || h->prm.coarse_restart > GCR_MAXK ||
+        h->prm.coarse_restart < 1) {
+        set_error("gcr_restart, post_smooth and coarse_restart must be in [1, %d]", GCR_MAXK); return DWF_ERR_ARG;
     }
     if (stream) h->st = as_stream(stream);
     DWF_TRY(ensure_workspace(h));
@@ -478,7 +546,8 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
         for (int k = 0; k < K && outer < maxiter; ++k) {
             DWF_TRY(precondition(s, s.r, s.Z[k], s.W[k]));
             DWF_TRY(gcr_orthogonalise(s, g, s.Z, s.W, k, s.r, n));
-            k_gcr_update<<<s.rg, RED_THREADS, 0, s.st>>>(s.e, s.r, s.Z[k], s.W[k], g->alpha, n, rs, &g->rr2);
+            k_gcr_update<<<s.rg, RED_THREADS, 0, s.st>>>(s.e, s.r, s.Z[k], s.W[k], g->alpha, n, rs, &g->rr2,
+                                                         nullptr, nullptr, 0.0, nullptr, 0);
             DWF_CHECK_LAUNCH();
             ++outer;
             DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->outer.rr2, &g->rr2, sizeof(double), cudaMemcpyDeviceToHost, s.st));
@@ -493,7 +562,7 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
         k_axpy_64_32<<<s.eg, 256, 0, s.st>>>(X, s.e, rn, n);
         DWF_CHECK_LAUNCH();
     }
-    if (h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
+    if (h->prm.coarse_solver == 0 && h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
         DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->pcg_iters, &s.d->pcg_iters, sizeof(int), cudaMemcpyDeviceToHost, s.st));
         DWF_CHECK_CUDA(cudaMemcpyAsync(s.hs->bar, s.d->bar, sizeof(s.d->bar), cudaMemcpyDeviceToHost, s.st));
         DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));

@@ -139,10 +139,14 @@ def test_coarse_operator_and_transfers_match_oracle(dw, Ls, Ls_c):
 
 @pytest.mark.parametrize("dims,Ls,sigma,mset", [((16, 16), 8, 0.3, -0.08), ((32, 32), 8, 0.5, -0.19),
                                                  ((24, 16), 6, 0.5, -0.19)])
-def test_mg_solve_reaches_tolerance(dw, dims, Ls, sigma, mset):
+@pytest.mark.parametrize("coarse", [{"coarse_solver": 1}, {"coarse_solver": 0, "coarse_persistent": 1},
+                                    {"coarse_solver": 0, "coarse_persistent": 0}])
+def test_mg_solve_reaches_tolerance(dw, dims, Ls, sigma, mset, coarse):
     M5, mf = 1.0, 0.01
     U, starts, b = _problem(dims, Ls, sigma, 8, 9)
-    h, g = _setup(dw, dims, Ls, U, starts, M5, mf, {"setup_mass": mset})
+    prm = {"setup_mass": mset}
+    prm.update(coarse)
+    h, g = _setup(dw, dims, Ls, U, starts, M5, mf, prm)
     x = torch.empty(len(b), dtype=torch.complex128, device="cuda")
     stats, status = dw.mg_solve(h, _dev(b), x, tol=1e-10)
     D = dirac.dwf_matrix(U, dims, Ls, M5, mf)
