@@ -148,6 +148,26 @@ DWF_API dwf_status cgne_solve(const dwf_geom* g, const void* U, const void* b, v
                       dwf_solve_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Differentiation of x = D_DW^-1 b (U(1) links U = exp(i theta))
+ * ------------------------------------------------------------------------ */
+
+/* U_mu(x) = exp(i theta_mu(x)) on the GPU; theta is FP64 [mu][site], U_out
+ * complex128 in the canonical link layout.  U(1) only. */
+DWF_API dwf_status dwf_links_from_angles(const dwf_geom* g, const double* theta, void* U_out, void* stream);
+
+/* out = Gamma_5 in with Gamma_5 = gamma_5 R, R_{ss'} = delta_{(s+s'-1) % Ls, 0}
+ * (Sec. 2.1): out_s = gamma_5 in_{Ls+1-s} (1-based s).  D_DW^dag = Gamma_5 D_DW
+ * Gamma_5, so an adjoint solve is Gamma_5 D_DW^-1 Gamma_5.  in != out. */
+DWF_API dwf_status dwf_gamma5_reflect(const dwf_geom* g, const void* in, void* out, int prec, void* stream);
+
+/* force[mu][site] = Re( lam^dag (dD_DW / dtheta_mu(site)) x ) summed over all
+ * s slices (2-d U(1), FP64; U, lam, x complex128).  With lam = D_DW^-dag g for
+ * the upstream gradient g of a real loss, dL/dtheta = -force.  force is a
+ * device array of nd * V doubles. */
+DWF_API dwf_status dwf_link_force(const dwf_geom* g, const void* U, const void* lam, const void* x, double* force,
+                                  void* stream);
+
+/* ------------------------------------------------------------------------
  * Multigrid (Sec. 2.3, Sec. 3, Table kcycle)
  * ------------------------------------------------------------------------ */
 

@@ -89,6 +89,9 @@ def _setup_signatures(L):
         "dwf_pvdag_apply_noalloc": [G, _VP, _VP, _VP, _D, _D, _I, _VP],
         "dwf_dot": [_VP, _VP, ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _VP],
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "dwf_links_from_angles": [G, _VP, _VP, _VP],
+        "dwf_gamma5_reflect": [G, _VP, _VP, _I, _VP],
+        "dwf_link_force": [G, _VP, _VP, _VP, _VP, _VP],
         "mg_setup": [G, _VP, _D, _D, ctypes.POINTER(MgParams), _VP, ctypes.POINTER(_VP), _VP],
         "mg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
         "mg_coarse_geom": [_VP, G, ctypes.POINTER(ctypes.c_int)],
@@ -232,6 +235,32 @@ def cgne_solve(geom, U, b, x, M5, mf, tol=1e-10, maxiter=100000, stream=None, ra
     if status != OK and (raise_noconv or status != ERR_NOCONV):
         check(status)
     return st.as_dict(), status
+
+
+def links_from_angles(geom, theta, stream=None):
+    """complex128 links exp(i theta) computed on the GPU (U(1))."""
+    if theta.dtype != torch.float64 or not theta.is_cuda or theta.numel() != link_size(geom):
+        raise ValueError("theta must be a CUDA float64 tensor of the link size")
+    U = torch.empty(theta.numel(), dtype=torch.complex128, device=theta.device)
+    check(lib().dwf_links_from_angles(ctypes.byref(geom), _ptr(theta.contiguous()), _ptr(U), _stream(stream)))
+    return U
+
+
+def gamma5_reflect(geom, vin, vout=None, stream=None):
+    prec = "f64" if vin.dtype == torch.complex128 else "f32"
+    _check_spinor(vin, geom, prec, "in")
+    if vout is None:
+        vout = torch.empty_like(vin)
+    check(lib().dwf_gamma5_reflect(ctypes.byref(geom), _ptr(vin), _ptr(vout), PREC[prec], _stream(stream)))
+    return vout
+
+
+def link_force(geom, U, lam, x, stream=None):
+    _check_spinor(lam, geom, "f64", "lam")
+    _check_spinor(x, geom, "f64", "x")
+    F = torch.empty(link_size(geom), dtype=torch.float64, device=lam.device)
+    check(lib().dwf_link_force(ctypes.byref(geom), _ptr(U), _ptr(lam), _ptr(x), _ptr(F), _stream(stream)))
+    return F
 
 
 # ---------------------------------------------------------------------------

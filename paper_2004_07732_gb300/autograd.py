@@ -1,0 +1,53 @@
+"""torch.autograd.Function for x = D_DW(theta)^-1 b on U(1) link angles theta.
+
+Forward: links U = exp(i theta) and the solve run in libdwfmg (FP64 CGNR, or
+the multigrid K-cycle when a handle is given).  Backward: one adjoint solve
+lambda = D_DW^-dag g, done as Gamma_5 D_DW^-1 Gamma_5 g (Gamma_5 = gamma_5 R,
+Sec. 2.1), then dL/db = lambda and dL/dtheta = -Re(lambda^dag dD_DW/dtheta x)
+from the link-force kernel.  Only x is kept between forward and backward (the
+solve iterates are not stored; the adjoint solve recomputes what it needs).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+def _solve(geom, U, b, M5, mf, tol, maxiter, mg):
+    x = torch.empty_like(b)
+    if mg is not None:
+        st, _ = _lib.mg_solve(mg, b.contiguous(), x, tol=tol, maxiter=maxiter)
+    else:
+        st, _ = _lib.cgne_solve(geom, U, b.contiguous(), x, M5, mf, tol=tol, maxiter=maxiter)
+    return x, st
+
+
+class DwfSolve(torch.autograd.Function):
+    """x = D_DW(exp(i theta))^-1 b.  Inputs: theta (float64 [nd*V]), b (complex128)."""
+
+    @staticmethod
+    def forward(ctx, theta, b, geom, M5, mf, tol=1e-12, maxiter=200000, mg=None):
+        U = _lib.links_from_angles(geom, theta.detach())
+        x, st = _solve(geom, U, b.detach(), M5, mf, tol, maxiter, mg)
+        ctx.save_for_backward(x)
+        ctx.geom, ctx.M5, ctx.mf, ctx.tol, ctx.maxiter, ctx.mg = geom, M5, mf, tol, maxiter, mg
+        ctx.U = U
+        ctx.stats = st
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        geom = ctx.geom
+        g = gx.contiguous().to(torch.complex128)
+        # lambda = D^-dag g = Gamma_5 D^-1 Gamma_5 g
+        y, _ = _solve(geom, ctx.U, _lib.gamma5_reflect(geom, g), ctx.M5, ctx.mf, ctx.tol, ctx.maxiter, ctx.mg)
+        lam = _lib.gamma5_reflect(geom, y)
+        F = _lib.link_force(geom, ctx.U, lam, x)
+        return -F, lam, None, None, None, None, None, None
+
+
+def solve(theta, b, geom, M5, mf, tol=1e-12, maxiter=200000, mg=None):
+    """Differentiable x = D_DW^-1 b (see DwfSolve)."""
+    return DwfSolve.apply(theta, b, geom, M5, mf, tol, maxiter, mg)

@@ -1,0 +1,148 @@
+// Differentiation of x = D_DW^-1 b with respect to U(1) link angles.
+//
+// For a real loss L(x) with upstream gradient g = dL/dRe x + i dL/dIm x, the
+// adjoint solution lambda = D_DW^-dag g gives dL/db = lambda and
+//   dL/dtheta_mu(y) = -Re( lambda^dag (dD_DW / dtheta_mu(y)) x ).
+// Only the Wilson hops of D_W (Sec. 2) depend on U_mu(y) = exp(i theta_mu(y)),
+// on every s slice: the forward hop -1/2 (1 - gamma_mu) U_mu(y) (row y, column
+// y + mu) differentiates to -1/2 (1 - gamma_mu) i U_mu(y), the backward hop
+// -1/2 (1 + gamma_mu) U_mu(y)^* (row y + mu, column y) to
+// -1/2 (1 + gamma_mu) (-i) U_mu(y)^*.
+//
+// The adjoint solve uses Gamma_5 = gamma_5 R (Sec. 2.1): D^dag = Gamma_5 D Gamma_5,
+// so D^-dag g = Gamma_5 D^-1 Gamma_5 g and any forward solver serves.
+#include "common.cuh"
+#include "fine_kernels.cuh"
+
+namespace dwf {
+
+__global__ void k_links_from_angles(const double* __restrict__ th, double2* __restrict__ U, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincos(th[i], &sn, &cs);
+        U[i] = make_double2(cs, sn);
+    }
+}
+
+// out_s = gamma_5 in_{Ls-1-s}; chirality - components change sign.
+template <class C>
+__global__ void k_gamma5_reflect(const C* __restrict__ in, C* __restrict__ out, long long V, int Ls, int dof,
+                                 int half) {
+    const long long n = V * Ls * dof;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(t % dof);
+        const long long rest = t / dof;
+        const long long x = rest % V;
+        const int s = (int)(rest / V);
+        C v = in[((long long)(Ls - 1 - s) * V + x) * dof + d];
+        if (d >= half) { v.x = -v.x; v.y = -v.y; }
+        out[t] = v;
+    }
+}
+
+// conj(a) . M . b for a 2x2 spin matrix M = (1 + sgn gamma_mu) (2-d basis)
+__device__ __forceinline__ double2 bilinear(double2 a0, double2 a1, double2 b0, double2 b1, int mu, int sgn) {
+    // M b
+    double2 m0, m1;
+    if (mu == 0) {           // gamma_1 = sigma_1
+        m0 = make_double2(b0.x + sgn * b1.x, b0.y + sgn * b1.y);
+        m1 = make_double2(b1.x + sgn * b0.x, b1.y + sgn * b0.y);
+    } else {                 // gamma_2 = sigma_2 = [[0,-i],[i,0]]
+        m0 = make_double2(b0.x + sgn * b1.y, b0.y - sgn * b1.x);   // b0 - i sgn b1
+        m1 = make_double2(b1.x - sgn * b0.y, b1.y + sgn * b0.x);   // b1 + i sgn b0
+    }
+    return make_double2(a0.x * m0.x + a0.y * m0.y + a1.x * m1.x + a1.y * m1.y,
+                        a0.x * m0.y - a0.y * m0.x + a1.x * m1.y - a1.y * m1.x);
+}
+
+__global__ void k_force_u1_2d(const double2* __restrict__ U, const double2* __restrict__ lam,
+                              const double2* __restrict__ x, double* __restrict__ F, int L0, long long V, int Ls,
+                              int anti0, int anti1) {
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= V) return;
+    const int x0 = (int)(site % L0);
+    for (int mu = 0; mu < 2; ++mu) {
+        long long nb;
+        bool cross;
+        if (mu == 0) { cross = (x0 == L0 - 1); nb = cross ? site - (L0 - 1) : site + 1; }
+        else         { cross = (site + L0 >= V); nb = cross ? site + L0 - V : site + L0; }
+        const double ph = (cross && (mu == 0 ? anti0 : anti1)) ? -1.0 : 1.0;
+        const double2 u = U[mu * V + site];
+        double2 acc1 = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+        for (int s = 0; s < Ls; ++s) {
+            const long long b = (long long)s * V;
+            const double2* l0 = lam + 2 * (b + site);
+            const double2* xn = x + 2 * (b + nb);
+            const double2* ln = lam + 2 * (b + nb);
+            const double2* x0p = x + 2 * (b + site);
+            // lambda(site)^dag (1 - gamma_mu) x(site + mu)
+            double2 t1 = bilinear(l0[0], l0[1], xn[0], xn[1], mu, -1);
+            // lambda(site + mu)^dag (1 + gamma_mu) x(site)
+            double2 t2 = bilinear(ln[0], ln[1], x0p[0], x0p[1], mu, +1);
+            acc1.x += t1.x; acc1.y += t1.y;
+            acc2.x += t2.x; acc2.y += t2.y;
+        }
+        // -1/2 * i U * acc1  +  -1/2 * (-i) conj(U) * acc2, real part
+        const double2 iu = make_double2(-u.y, u.x);                 // i U
+        const double2 miuc = make_double2(-u.y, -u.x);              // -i conj(U)
+        const double r1 = iu.x * acc1.x - iu.y * acc1.y;
+        const double r2 = miuc.x * acc2.x - miuc.y * acc2.y;
+        F[mu * V + site] = -0.5 * ph * (r1 + r2);
+    }
+}
+
+}  // namespace dwf
+
+using namespace dwf;
+
+extern "C" {
+
+dwf_status dwf_links_from_angles(const dwf_geom* g, const double* theta, void* U_out, void* stream) {
+    clear_error();
+    Geom G;
+    DWF_TRY(check_geom(g, &G));
+    if (G.group != DWF_U1) { set_error("link angles apply to U(1) only"); return DWF_ERR_ARG; }
+    const long long n = link_len(G);
+    if (n == 0) return DWF_OK;
+    if (!theta || !U_out) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
+    const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    k_links_from_angles<<<grid, 256, 0, as_stream(stream)>>>(theta, (double2*)U_out, n);
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+dwf_status dwf_gamma5_reflect(const dwf_geom* g, const void* in, void* out, int prec, void* stream) {
+    clear_error();
+    Geom G;
+    DWF_TRY(check_geom(g, &G));
+    if (!valid_prec(prec)) { set_error("bad precision %d", prec); return DWF_ERR_ARG; }
+    const long long n = spinor_len(G);
+    if (n == 0) return DWF_OK;
+    if (!in || !out) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
+    if (in == out) { set_error("in and out must be distinct buffers"); return DWF_ERR_ARG; }
+    const int dof = (int)site_dof(G);
+    const int half = dof / 2;
+    const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    cudaStream_t st = as_stream(stream);
+    if (prec == DWF_F64) k_gamma5_reflect<double2><<<grid, 256, 0, st>>>((const double2*)in, (double2*)out, G.V, G.Ls, dof, half);
+    else                 k_gamma5_reflect<float2><<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, G.V, G.Ls, dof, half);
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+dwf_status dwf_link_force(const dwf_geom* g, const void* U, const void* lam, const void* x, double* force,
+                          void* stream) {
+    clear_error();
+    Geom G;
+    DWF_TRY(check_geom(g, &G));
+    if (G.nd != 2 || G.group != DWF_U1) { set_error("the link force is built for 2-d U(1)"); return DWF_ERR_UNSUPPORTED; }
+    if (G.V == 0) return DWF_OK;
+    if (!U || !lam || !x || !force) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
+    const int thr = 256;
+    k_force_u1_2d<<<(unsigned)((G.V + thr - 1) / thr), thr, 0, as_stream(stream)>>>(
+        (const double2*)U, (const double2*)lam, (const double2*)x, force, G.L[0], G.V, G.Ls, G.anti[0], G.anti[1]);
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+}  // extern "C"
