@@ -233,13 +233,13 @@ def run_ours(args):
         dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
     barrier()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(dev.index) as clk:
-        for a, b in evs:
-            flush.fill_(1.0)
-            a.record(stream)
-            dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
-            b.record(stream)
-        barrier()
+    clk = ClockSampler(dev.index).__enter__()
+    for a, b in evs:
+        flush.fill_(1.0)
+        a.record(stream)
+        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+        b.record(stream)
+    barrier()
     times = [a.elapsed_time(b) * 1e-3 for a, b in evs]
     t_apply = max_over_ranks(float(np.mean(times)))
     value = world * nbytes / t_apply / 1e9
@@ -267,11 +267,17 @@ def run_ours(args):
     d2h = out_h.numel() * out_h.element_size()
     del flush, out_h, Ud_h, psi, out, Ud, psi_h
 
+    # ---------------- 4-d SU(3) apply (16^3 x 32 x Ls=16), same method ----------------
+    su3 = None
+    if not args.skip_su3:
+        su3 = time_su3_apply(dw, dev, stream, args)
+
     # ---------------- time to solution on the 256^2 workload ----------------
     solve = None
     if not args.skip_solve:
         solve = time_solves(dw, dev, args)
 
+    clk.__exit__(None, None, None)
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     achieved = nbytes / float(np.mean(times)) / 1e9
@@ -293,10 +299,39 @@ def run_ours(args):
                 "e2e": {"value": world * nbytes / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "gpu_launches": launches, "solve": solve}
+                "gpu_launches": launches, "su3_apply": su3, "solve": solve}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_su3_apply(dw, dev, stream, args):
+    """FP32/FP16-link 4-d SU(3) apply on 16^3 x 32 x Ls=16 (421 MB per apply)."""
+    import torch
+    wl = synth.SU3_16x32
+    U, srcs = wl.draw(1)
+    g = dw.make_geom(wl.dims, wl.Ls, group="su3")
+    Ud = dw.links_to(g, torch.from_numpy(U.reshape(-1)).to(dev), "f32_l16")
+    psi = torch.from_numpy(srcs[0].reshape(-1).astype(np.complex64)).to(dev)
+    out = torch.empty_like(psi)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    nbytes = wl.V * wl.Ls * 2 * 96 + 4 * wl.V * 36
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in evs:
+        flush.fill_(1.0)
+        a.record(stream)
+        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    t = float(np.mean([a.elapsed_time(b) * 1e-3 for a, b in evs]))
+    peaks, _ = measured_peaks()
+    return {"workload": f"{wl.name}: 4-d SU(3) D_DW(m) apply, FP32 spinors, FP16 links, M5 {wl.M5}, m {wl.mf}",
+            "algorithmic_bytes_per_launch": nbytes, "ms": t * 1e3, "GBps": nbytes / t / 1e9,
+            "frac_of_hbm": nbytes / t / 1e9 / float(peaks["hbm_gbs"])}
 
 
 def time_solves(dw, dev, args):
@@ -355,6 +390,7 @@ def main():
     ap.add_argument("--skip-solve", action="store_true")
     ap.add_argument("--skip-mg", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-su3", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

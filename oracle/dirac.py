@@ -326,3 +326,42 @@ def dwf_apply_points_2d(U, psi, dims, Ls, M5, mf, points, dagger_=False, antiper
             acc = acc - mf * B @ psi[Ls - 1, site]
         out.append(acc)
     return np.array(out)
+
+
+def dwf_apply_points(U, psi, dims, Ls, M5, mf, points, group="u1", dagger_=False, antiperiodic=None):
+    """(D_DW psi)_{s, x} at selected (s, site) points for any d and group,
+    straight from Eq. DWoperator; pure-Python loop for spot checks of large
+    lattices.  U: (nd, V) or (nd, V, 3, 3); psi: (Ls, V, ns, nc)."""
+    nd = len(dims)
+    ns = n_spin(nd)
+    nc = 1 if group == "u1" else 3
+    g, g5 = gammas(nd)
+    I = np.eye(ns)
+    Pp, Pm = 0.5 * (I + g5), 0.5 * (I - g5)
+    anti = antiperiodic or [0] * nd
+    V = int(np.prod(dims))
+    psi = np.asarray(psi).reshape(Ls, V, ns, nc)
+    Ub = np.asarray(U).reshape(nd, V, nc, nc)
+    strides = np.cumprod([1] + list(dims[:-1]))
+    out = []
+    for s, site in points:
+        coords = [(site // strides[mu]) % dims[mu] for mu in range(nd)]
+        acc = (nd - M5 + 1) * psi[s, site]
+        sg = -1 if dagger_ else 1
+        for mu in range(nd):
+            c = list(coords)
+            cross_f = c[mu] + 1 == dims[mu]
+            c[mu] = (c[mu] + 1) % dims[mu]
+            fwd = int(sum(ci * st for ci, st in zip(c, strides)))
+            c = list(coords)
+            cross_b = c[mu] == 0
+            c[mu] = (c[mu] - 1) % dims[mu]
+            bwd = int(sum(ci * st for ci, st in zip(c, strides)))
+            uf = Ub[mu, site] * (-1 if (cross_f and anti[mu]) else 1)
+            ub = np.conj(Ub[mu, bwd]).T * (-1 if (cross_b and anti[mu]) else 1)
+            acc = acc - 0.5 * (I - sg * g[mu]) @ (psi[s, fwd] @ uf.T) - 0.5 * (I + sg * g[mu]) @ (psi[s, bwd] @ ub.T)
+        A, B = (Pp, Pm) if dagger_ else (Pm, Pp)
+        acc = acc + (A @ psi[s + 1, site] if s + 1 < Ls else -mf * A @ psi[0, site])
+        acc = acc + (B @ psi[s - 1, site] if s > 0 else -mf * B @ psi[Ls - 1, site])
+        out.append(acc)
+    return np.array(out)

@@ -1,0 +1,97 @@
+"""GPU parity of the 4-d SU(3) domain-wall operator against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dirac
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f32_l16": 1e-5, "f32_lbf16": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def dw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2004_07732_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to("cuda").to(dtype)
+
+
+def _rounded(U, prec):
+    if prec == "f64":
+        return U
+    if prec == "f32":
+        return U.astype(np.complex64).astype(np.complex128)
+    if prec == "f32_l16":
+        return U.real.astype(np.float16).astype(np.float64) + 1j * U.imag.astype(np.float16).astype(np.float64)
+    t = torch.from_numpy(np.stack([U.real, U.imag], -1)).to(torch.bfloat16).to(torch.float64).numpy()
+    return t[..., 0] + 1j * t[..., 1]
+
+
+@pytest.mark.parametrize("dims,Ls,anti", [((4, 4, 4, 4), 4, None), ((3, 5, 2, 3), 3, [0, 0, 0, 1]),
+                                          ((2, 2, 2, 2), 2, [1, 1, 1, 1]), ((6, 4, 4, 8), 5, None)])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_l16", "f32_lbf16"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dwf4d_apply_parity(dw, dims, Ls, anti, prec, dagger):
+    M5, mf = 1.8, 0.01
+    rng = synth.rng_for(hash((dims, Ls)) % 997)
+    U = synth.su3_links(rng, dims, 0.3)
+    psi = synth.gaussian_spinor(rng, dims, Ls, "su3")
+    g = dw.make_geom(dims, Ls, group="su3", antiperiodic=anti)
+    Ud = dw.links_to(g, _dev(U), prec)
+    pd = _dev(psi, dw.spinor_dtype(prec))
+    out = torch.empty_like(pd)
+    dw.dwf_apply(g, Ud, pd, out, M5, mf, dagger=dagger, prec=prec)
+    Uo = _rounded(U, prec)
+    ps = psi if prec == "f64" else psi.astype(np.complex64).astype(np.complex128)
+    want = dirac.dwf_apply(Uo, ps, dims, Ls, M5, mf, dagger_=dagger, group="su3", antiperiodic=anti).reshape(-1)
+    got = out.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < TOL[prec]
+
+
+def test_dwf4d_full_size_sampled(dw):
+    """16^3 x 32 x Ls=16 SU(3), FP32 spinors + FP16 links, spot-checked point by point."""
+    wl = synth.SU3_16x32
+    U, srcs = wl.draw(1)
+    psi = srcs[0]
+    g = dw.make_geom(wl.dims, wl.Ls, group="su3")
+    Ud = dw.links_to(g, _dev(U), "f32_l16")
+    pd = _dev(psi, torch.complex64)
+    out = torch.empty_like(pd)
+    dw.dwf_apply(g, Ud, pd, out, wl.M5, wl.mf, prec="f32_l16")
+    got = out.cpu().numpy().reshape(wl.Ls, wl.V, 4, 3)
+    rng = np.random.default_rng(1)
+    pts = [(int(rng.integers(0, wl.Ls)), int(rng.integers(0, wl.V))) for _ in range(120)]
+    pts += [(0, 0), (wl.Ls - 1, wl.V - 1), (0, wl.V - 1), (wl.Ls - 1, 0)]
+    Uo = _rounded(U, "f32_l16")
+    ps = psi.astype(np.complex64).astype(np.complex128)
+    want = dirac.dwf_apply_points(Uo, ps, wl.dims, wl.Ls, wl.M5, wl.mf, pts, group="su3")
+    g_pts = np.array([got[s, x] for s, x in pts])
+    assert np.abs(g_pts - want).max() < 1e-5 * np.abs(want).max()
+
+
+def test_dwf4d_adjoint_and_cgne(dw):
+    dims, Ls, M5, mf = (4, 4, 4, 4), 4, 1.8, 0.05
+    rng = synth.rng_for(11)
+    U = synth.su3_links(rng, dims, 0.3)
+    b = synth.gaussian_spinor(rng, dims, Ls, "su3").reshape(-1)
+    y = synth.gaussian_spinor(rng, dims, Ls, "su3").reshape(-1)
+    g = dw.make_geom(dims, Ls, group="su3")
+    Ud, bd, yd = _dev(U), _dev(b), _dev(y)
+    Dy, Ddb = torch.empty_like(yd), torch.empty_like(bd)
+    dw.dwf_apply(g, Ud, yd, Dy, M5, mf)
+    dw.dwf_apply(g, Ud, bd, Ddb, M5, mf, dagger=True)
+    a1, a2 = dw.dwf_dot(bd, Dy), dw.dwf_dot(Ddb, yd)
+    assert abs(a1 - a2) < 1e-12 * abs(a1)
+    x = torch.empty_like(bd)
+    st, status = dw.cgne_solve(g, Ud, bd, x, M5, mf, tol=1e-10)
+    D = dirac.dwf_matrix(U, dims, Ls, M5, mf, group="su3")
+    res = np.linalg.norm(b - D @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert status == 0 and res <= 1e-10

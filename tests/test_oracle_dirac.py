@@ -254,3 +254,22 @@ def test_point_evaluator_matches_assembled_operator(anti, dag):
     pts = [(s, x) for s in range(Ls) for x in range(30)]
     pv = dirac.dwf_apply_points_2d(U, psi, dims, Ls, 1.0, 0.07, pts, dagger_=dag, antiperiodic=anti)
     assert np.abs(pv - np.array([full[s, x] for s, x in pts])).max() < 1e-13
+
+
+@pytest.mark.parametrize("group,dims", [("u1", (5, 4)), ("su3", (2, 3, 2, 4))])
+@pytest.mark.parametrize("dag", [False, True])
+def test_generic_point_evaluator_matches_assembled_operator(group, dims, dag):
+    Ls = 3
+    rng = synth.rng_for(8)
+    if group == "u1":
+        U = synth.u1_links(synth.u1_angles(rng, dims, 0.6))
+    else:
+        U = synth.su3_links(rng, dims, 0.3)
+    psi = synth.gaussian_spinor(rng, dims, Ls, group)
+    V = int(np.prod(dims))
+    anti = [1] + [0] * (len(dims) - 1)
+    full = dirac.dwf_apply(U, psi, dims, Ls, 1.3, 0.05, dagger_=dag, group=group, antiperiodic=anti)
+    full = full.reshape(Ls, V, -1)
+    pts = [(s, x) for s in range(Ls) for x in range(V)]
+    pv = dirac.dwf_apply_points(U, psi, dims, Ls, 1.3, 0.05, pts, group=group, dagger_=dag, antiperiodic=anti)
+    assert np.abs(pv.reshape(len(pts), -1) - np.array([full[s, x] for s, x in pts])).max() < 1e-13
