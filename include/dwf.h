@@ -193,7 +193,9 @@ typedef struct {
     int coarse_solver;    /* 0: CGNR on the coarse normal operator (Table kcycle, coarsest
                              level); 1: restarted GCR on Dhat_PV^dag Dhat_DW (the paper's
                              level-2 solver; valid by the right-half-plane property, App. B) */
-    int coarse_restart;   /* restart length of the coarse GCR (16)                        */
+    int coarse_restart;   /* restart length of the coarse GCR (8)                         */
+    int coarse_block_prec;/* storage of the Galerkin blocks read by the coarse stencil:
+                             DWF_F32 or DWF_F32_L16 (FP16 blocks, FP32 arithmetic; default) */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;

@@ -51,7 +51,7 @@ class MgParams(ctypes.Structure):
                 ("coarse_tol", ctypes.c_double), ("coarse_maxiter", ctypes.c_int), ("fine_prec", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("coarse_persistent", ctypes.c_int), ("coarse_solver", ctypes.c_int),
-                ("coarse_restart", ctypes.c_int)]
+                ("coarse_restart", ctypes.c_int), ("coarse_block_prec", ctypes.c_int)]
 
 
 _lib = None
@@ -281,8 +281,8 @@ def _params(d: dict) -> MgParams:
         if k == "block":
             for i, b in enumerate(v):
                 p.block[i] = int(b)
-        elif k == "fine_prec" and isinstance(v, str):
-            p.fine_prec = PREC[v]
+        elif k in ("fine_prec", "coarse_block_prec") and isinstance(v, str):
+            setattr(p, k, PREC[v])
         else:
             setattr(p, k, v)
     return p

@@ -149,7 +149,7 @@ dwf_status dwf_dot(const void* x, const void* y, size_t n, int prec, double* res
     cudaStream_t st = as_stream(stream);
     Workspace ws;
     DWF_TRY(ws.reserve(st));
-    DWF_TRY(dot_device(x, y, (long long)n, prec == DWF_F64, ws.red(), ws.scal, st));
+    DWF_TRY(dot_device(x, y, (long long)n, prec == DWF_F64, ws.red(), ws.scal, st, true));
     double h[2];
     DWF_CHECK_CUDA(cudaMemcpyAsync(h, ws.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     DWF_CHECK_CUDA(cudaStreamSynchronize(st));

@@ -12,11 +12,19 @@
 namespace dwf {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 152 * 4;   // upper bound on reduction grid size
+constexpr int RED_BLOCKS = 152 * 8;   // upper bound on reduction grid size
 constexpr int RED_MAX = 4;            // reduced quantities per kernel
 
 inline int red_grid(long long n) {
     long long b = (n + RED_THREADS - 1) / RED_THREADS;
+    if (b < 1) b = 1;
+    return (int)(b < RED_BLOCKS ? b : RED_BLOCKS);
+}
+
+// Grid for reductions over FP32 vectors read as float4: about 8 complex values
+// per thread (fewer, fuller blocks keep the block-sum and completion tail short).
+inline int red_grid4(long long n) {
+    long long b = (n + 8LL * RED_THREADS - 1) / (8LL * RED_THREADS);
     if (b < 1) b = 1;
     return (int)(b < RED_BLOCKS ? b : RED_BLOCKS);
 }
@@ -66,20 +74,43 @@ __device__ __forceinline__ void block_sum(double (&v)[N]) {
     }
 }
 
+// Completion counters: RED_GROUPS group counters and one top counter, each
+// on its own 128-byte line, so that the blocks of a grid do not all contend
+// for one address (a single counter serialised ~1000 atomics per reduction).
+constexpr int RED_GROUPS = 32;
+constexpr int RED_CSTRIDE = 32;   // unsigneds between counters (128 bytes)
+
+// True in exactly one block: the last to finish.  Group g = blockIdx % 32
+// counts its blocks; the last block of each group bumps the top counter.
+__device__ __forceinline__ bool grid_last_block(unsigned* counters) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned g = blockIdx.x % RED_GROUPS;
+        const unsigned gsize = (gridDim.x - g + RED_GROUPS - 1) / RED_GROUPS;
+        const unsigned ngroups = gridDim.x < RED_GROUPS ? gridDim.x : RED_GROUPS;
+        bool l = false;
+        if (atomicAdd(counters + g * RED_CSTRIDE, 1u) == gsize - 1) {
+            counters[g * RED_CSTRIDE] = 0u;
+            __threadfence();
+            l = atomicAdd(counters + RED_GROUPS * RED_CSTRIDE, 1u) == ngroups - 1;
+            if (l) counters[RED_GROUPS * RED_CSTRIDE] = 0u;
+        }
+        last = l;
+    }
+    __syncthreads();
+    return last;
+}
+
 // Grid-wide reduction with a finaliser fin(double* totals) run by one thread.
 template <int N, class Fin>
 __device__ __forceinline__ void grid_reduce(double (&v)[N], RedScratch rs, Fin fin) {
-    __shared__ bool last;
     block_sum<N>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < N; ++k) rs.partials[k * RED_BLOCKS + blockIdx.x] = v[k];
-        __threadfence();
-        unsigned t = atomicAdd(rs.counter, 1u);
-        last = (t == gridDim.x - 1);
     }
-    __syncthreads();
-    if (!last) return;
+    if (!grid_last_block(rs.counter)) return;
     __threadfence();
     double w[N];
 #pragma unroll
@@ -88,14 +119,14 @@ __device__ __forceinline__ void grid_reduce(double (&v)[N], RedScratch rs, Fin f
         for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) w[k] += __ldcg(rs.partials + k * RED_BLOCKS + b);
     }
     block_sum<N>(w);
-    if (threadIdx.x == 0) {
-        fin(w);
-        *rs.counter = 0u;
-    }
+    if (threadIdx.x == 0) fin(w);
 }
 
-// <x, y> over n complex values into out[0..1] (device), FP64 accumulation.
+// <x, y> over n complex values into out[0..1] (device).  FP64 data, or exact =
+// true: every product accumulated in FP64.  FP32 data with exact = false:
+// per-thread FP32 partials over a few elements, FP64 across threads (GB300's
+// FP64 units make per-element FP64 accumulation the bottleneck otherwise).
 dwf_status dot_device(const void* x, const void* y, long long n, bool f64, RedScratch rs, double* out,
-                      cudaStream_t st);
+                      cudaStream_t st, bool exact = false);
 
 }  // namespace dwf

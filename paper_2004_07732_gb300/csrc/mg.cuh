@@ -46,7 +46,9 @@ struct dwf_mg {
     float2* P32;
     double2* Y64;         // Galerkin blocks [xc][dir][row][col]
     float2* Y32;          // FP32 copy, column-major per block: [xc][dir][col][row]
-    float2* Yd32;         // FP32 adjoint blocks Y[x+dir][-dir]^dag, column-major
+    float2* Yd32;         // FP32 adjoint blocks Y[x+dir][-dir]^dag, column-major (generic stencil)
+    void* Ytile;          // blocks read by the 2-d tile stencil: Y32, or an FP16 column-major copy
+    int ytile_half;       // 1 when Ytile holds FP16 (half2) blocks
     int* status;          // device status word of the setup kernels
     std::vector<void*> allocs;
     // solver workspace (allocated on first solve)
@@ -57,6 +59,11 @@ struct dwf_mg {
     std::vector<void*> coarse_vecs; // FP32 coarse vectors
     void* x64;            // FP64 solution accumulator
     void* r64;            // FP64 residual
+    void* solver_meta;    // device pointer arrays and CGS scratch of the solver
+    bool solver_meta_ready;
+    cudaGraphExec_t coarse_graph_first;   // captured coarse GCR: prologue + one restart cycle
+    cudaGraphExec_t coarse_graph_cycle;   // captured coarse GCR: one restart cycle
+    cudaStream_t cap_stream;              // private stream used only to record graphs
 };
 
 namespace dwf {
@@ -68,6 +75,8 @@ dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes);
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger,
                             const int* skip, cudaStream_t st);
 dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st);
+// one-time kernel attributes of the coarse stencil (outside any stream capture)
+dwf_status coarse_init_attributes();
 dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st);
 dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st);
 

@@ -181,13 +181,17 @@ __device__ __forceinline__ double warp_site16(const float2* __restrict__ B, cons
 constexpr int TILE_X = 4, TILE_Y = 2, TILE_HX = TILE_X + 2, TILE_HY = TILE_Y + 2;
 constexpr int TILE_SITES = TILE_X * TILE_Y;
 constexpr int TILE_THREADS = 32 * TILE_SITES;
-constexpr unsigned SITE_BLOCK_BYTES = 5u * 256u * sizeof(float2);   // 10240
-
-struct TileSmem {
-    float2 Y[TILE_SITES][5][256];          // column-major blocks per direction
+// BT: storage of the Galerkin blocks, float2 (FP32) or __half2 (FP16)
+template <class BT>
+struct TileSmemT {
+    BT Y[TILE_SITES][5][256];              // column-major blocks per direction
     float2 v[4][TILE_HY][TILE_HX][16];     // staged inputs with halo
     unsigned long long mbar;
 };
+template <class BT> __host__ __device__ constexpr unsigned site_block_bytes() { return 5u * 256u * (unsigned)sizeof(BT); }
+
+__device__ __forceinline__ float2 to_f2(float2 a) { return a; }
+__device__ __forceinline__ float2 to_f2(__half2 a) { return __half22float2(a); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -222,9 +226,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     return true;
 }
 
-template <bool CG>
-__device__ __forceinline__ void tile_stage(TileSmem& sm, const float2* __restrict__ in, const CoarseParams& p, int x0,
-                                           int y0) {
+template <bool CG, class BT>
+__device__ __forceinline__ void tile_stage(TileSmemT<BT>& sm, const float2* __restrict__ in, const CoarseParams& p,
+                                           int x0, int y0) {
     const int L0 = p.Lc[0], L1 = p.Lc[1];
     const long long slice = p.Vc * 16;
     const int total = p.Ls_c * TILE_HY * TILE_HX * 16;
@@ -243,9 +247,11 @@ __device__ __forceinline__ void tile_stage(TileSmem& sm, const float2* __restric
 
 // Thread 0 starts the bulk copies of the tile's blocks (phase completes when
 // all bytes have landed).  Returns the number of bytes expected.
-__device__ __forceinline__ void tile_issue_blocks(TileSmem& sm, const float2* __restrict__ B, const CoarseParams& p,
+template <class BT>
+__device__ __forceinline__ void tile_issue_blocks(TileSmemT<BT>& sm, const BT* __restrict__ B, const CoarseParams& p,
                                                   int x0, int y0) {
     if (threadIdx.x != 0) return;
+    constexpr unsigned SITE_BLOCK_BYTES = site_block_bytes<BT>();
     unsigned bytes = 0;
     for (int w = 0; w < TILE_SITES; ++w) {
         const int gx = x0 + w % TILE_X, gy = y0 + w / TILE_X;
@@ -263,8 +269,13 @@ __device__ __forceinline__ void tile_issue_blocks(TileSmem& sm, const float2* __
 }
 
 // Multiply for this warp's site from shared memory; returns the lane's |out|^2.
-__device__ __forceinline__ double tile_site(const TileSmem& sm, float2* __restrict__ out, const CoarseParams& p, int x0,
-                                            int y0, float mf, bool dag) {
+// The adjoint uses gamma_5-hermiticity of the Galerkin kernel: the chirality-
+// preserving prolongator gives Dhat_W^dag = sigma_3 Dhat_W sigma_3 (P^dag gamma_5
+// D_W gamma_5 P), so the same blocks serve with sign flips on the chirality -
+// components of input and output (2 nvec = 16: components 8..15).
+template <class BT>
+__device__ __forceinline__ double tile_site(const TileSmemT<BT>& sm, float2* __restrict__ out, const CoarseParams& p,
+                                            int x0, int y0, float mf, bool dag) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = warp % TILE_X, ty = warp / TILE_X;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -275,24 +286,37 @@ __device__ __forceinline__ double tile_site(const TileSmem& sm, float2* __restri
     const bool h0 = sg < p.Ls_c, h1 = sg + 2 < p.Ls_c;
     const int s0 = h0 ? sg : 0, s1 = h1 ? sg + 2 : 0;
     const int hx = tx + 1, hy = ty + 1;
-    float2 acc0 = sm.v[s0][hy][hx][i], acc1 = sm.v[s1][hy][hx][i];
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);   // hopping sums for the up / down halves
+    float2 acm0 = make_float2(0.f, 0.f), acm1 = make_float2(0.f, 0.f);   // contributions of chirality - inputs
 #pragma unroll
     for (int dir = 0; dir < 5; ++dir) {
         const int nx = hx + (dir == 1 ? 1 : dir == 2 ? -1 : 0);
         const int ny = hy + (dir == 3 ? 1 : dir == 4 ? -1 : 0);
-        const float2* Yd = &sm.Y[warp][dir][i];
+        const BT* Yd = &sm.Y[warp][dir][i];
         const float4* va = reinterpret_cast<const float4*>(&sm.v[s0][ny][nx][0]);
         const float4* vb = reinterpret_cast<const float4*>(&sm.v[s1][ny][nx][0]);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const float4 a = va[m], b = vb[m];
-            const float2 y0v = Yd[(2 * m) * 16], y1v = Yd[(2 * m + 1) * 16];
-            acc0 = cfma(y0v, make_float2(a.x, a.y), acc0);
-            acc0 = cfma(y1v, make_float2(a.z, a.w), acc0);
-            acc1 = cfma(y0v, make_float2(b.x, b.y), acc1);
-            acc1 = cfma(y1v, make_float2(b.z, b.w), acc1);
+            const float2 y0v = to_f2(Yd[(2 * m) * 16]), y1v = to_f2(Yd[(2 * m + 1) * 16]);
+            if (m < 4) {
+                acc0 = cfma(y0v, make_float2(a.x, a.y), acc0);
+                acc0 = cfma(y1v, make_float2(a.z, a.w), acc0);
+                acc1 = cfma(y0v, make_float2(b.x, b.y), acc1);
+                acc1 = cfma(y1v, make_float2(b.z, b.w), acc1);
+            } else {
+                acm0 = cfma(y0v, make_float2(a.x, a.y), acm0);
+                acm0 = cfma(y1v, make_float2(a.z, a.w), acm0);
+                acm1 = cfma(y0v, make_float2(b.x, b.y), acm1);
+                acm1 = cfma(y1v, make_float2(b.z, b.w), acm1);
+            }
         }
     }
+    // hop sum: Dhat_W v (operator) or sigma_3 Dhat_W sigma_3 v (adjoint)
+    const float si = (dag && i >= 8) ? -1.f : 1.f;
+    const float sm_ = dag ? -1.f : 1.f;
+    const float2 hop0 = make_float2(si * (acc0.x + sm_ * acm0.x), si * (acc0.y + sm_ * acm0.y));
+    const float2 hop1 = make_float2(si * (acc1.x + sm_ * acm1.x), si * (acc1.y + sm_ * acm1.y));
     const int c = i / p.nvec;
     const bool from_below = dag ? (c == 1) : (c == 0);
     double nrm = 0.0;
@@ -301,14 +325,16 @@ __device__ __forceinline__ double tile_site(const TileSmem& sm, float2* __restri
         const bool has = k == 0 ? h0 : h1;
         if (!has) continue;
         const int s = k == 0 ? s0 : s1;
-        float2 acc = k == 0 ? acc0 : acc1;
+        const float2 hop = k == 0 ? hop0 : hop1;
+        const float2 self = sm.v[s][hy][hx][i];                 // the "+1" of Dhat_W + 1
         int sh;
         float sc = 1.f;
         if (from_below) { if (s > 0) sh = s - 1; else { sh = p.Ls_c - 1; sc = -mf; } }
         else            { if (s < p.Ls_c - 1) sh = s + 1; else { sh = 0; sc = -mf; } }
         const float2 hv = sm.v[sh][hy][hx][i];
-        acc.x += sc * hv.x;
-        acc.y += sc * hv.y;
+        float2 acc;
+        acc.x = hop.x + self.x + sc * hv.x;
+        acc.y = hop.y + self.y + sc * hv.y;
         out[s * slice + xc * 16 + i] = acc;
         nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
     }
@@ -317,18 +343,19 @@ __device__ __forceinline__ double tile_site(const TileSmem& sm, float2* __restri
 
 constexpr unsigned long long TILE_WAIT_NS = 2000000000ULL;   // 2 s
 
-__global__ void __launch_bounds__(TILE_THREADS) k_coarse_tile(const float2* __restrict__ B, const float2* __restrict__ in,
+template <class BT>
+__global__ void __launch_bounds__(TILE_THREADS) k_coarse_tile(const BT* __restrict__ B, const float2* __restrict__ in,
                                                               float2* __restrict__ out, CoarseParams p, bool dag,
                                                               const int* skip, int* status) {
     if (skip && *skip) return;
     extern __shared__ __align__(128) unsigned char tile_raw[];
-    TileSmem& sm = *reinterpret_cast<TileSmem*>(tile_raw);
+    TileSmemT<BT>& sm = *reinterpret_cast<TileSmemT<BT>*>(tile_raw);
     const int ntx = (p.Lc[0] + TILE_X - 1) / TILE_X;
     const int x0 = (blockIdx.x % ntx) * TILE_X, y0 = (blockIdx.x / ntx) * TILE_Y;
     if (threadIdx.x == 0) mbar_init(&sm.mbar, 1);
     __syncthreads();
     tile_issue_blocks(sm, B, p, x0, y0);
-    tile_stage<false>(sm, in, p, x0, y0);
+    tile_stage<false, BT>(sm, in, p, x0, y0);
     __syncthreads();
     if (!mbar_wait_bounded(&sm.mbar, 0, TILE_WAIT_NS)) {
         if (threadIdx.x == 0) atomicExch(status, 2);
@@ -339,6 +366,14 @@ __global__ void __launch_bounds__(TILE_THREADS) k_coarse_tile(const float2* __re
 }
 
 static bool tile_ok(const CoarseParams& p) { return p.nd == 2 && p.ncd == 16 && p.Ls_c <= 4; }
+
+dwf_status coarse_init_attributes() {
+    DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tile<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(TileSmemT<float2>)));
+    DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tile<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(TileSmemT<__half2>)));
+    return DWF_OK;
+}
 
 template <int NCD>
 __global__ void __launch_bounds__(256) k_coarse_dwf(const float2* __restrict__ B, const float2* __restrict__ in,
@@ -372,14 +407,12 @@ dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, doub
     const float2* B = dagger ? h->Yd32 : h->Y32;
     if (tile_ok(p)) {
         const int ntiles = ((p.Lc[0] + TILE_X - 1) / TILE_X) * ((p.Lc[1] + TILE_Y - 1) / TILE_Y);
-        static bool attr_set[64] = {};
-        int dev = 0;
-        DWF_CHECK_CUDA(cudaGetDevice(&dev));
-        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)));
-            attr_set[dev] = true;
-        }
-        k_coarse_tile<<<ntiles, TILE_THREADS, sizeof(TileSmem), st>>>(B, in, out, p, dagger, skip, h->status + 1);
+        if (h->ytile_half)
+            k_coarse_tile<__half2><<<ntiles, TILE_THREADS, sizeof(TileSmemT<__half2>), st>>>(
+                (const __half2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
+        else
+            k_coarse_tile<float2><<<ntiles, TILE_THREADS, sizeof(TileSmemT<float2>), st>>>(
+                (const float2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
     } else if (p.ncd == 16) k_coarse_dwf<16><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
     else             k_coarse_dwf<0><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
     DWF_CHECK_LAUNCH();
@@ -666,12 +699,19 @@ __device__ void pcg_partial(double (&v)[3], int nv, double* partials) {
     __syncthreads();
 }
 
-// every block: fixed-order total of partial k
+// every block: fixed-order total of partial k (strided loads by all threads,
+// then a fixed-order block reduction)
 __device__ double pcg_total(const double* partials, int k) {
+    __shared__ double sh[PCG_THREADS / 32];
     __shared__ double tot;
+    double v = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += __ldcg(partials + k * gridDim.x + b);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + k * gridDim.x + b);
+        for (int w = 0; w < PCG_THREADS / 32; ++w) s += sh[w];
         tot = s;
     }
     __syncthreads();
@@ -683,10 +723,10 @@ __device__ double pcg_total(const double* partials, int k) {
 // out = Dhat_DW(m) in (or adjoint) over all tiles (grid-stride), shared-memory
 // tiles as in k_coarse_tile.  `phase` is this block's mbarrier parity, flipped
 // per tile.  Returns this thread's share of |out|^2; false in *ok on a timeout.
-__device__ double pcg_apply(const PcgArgs& a, TileSmem& sm, unsigned& phase, const float2* __restrict__ in,
+__device__ double pcg_apply(const PcgArgs& a, TileSmemT<float2>& sm, unsigned& phase, const float2* __restrict__ in,
                             float2* __restrict__ out, double mf, bool dag, bool* ok) {
     const CoarseParams& p = a.cp;
-    const float2* B = dag ? a.Yd : a.Y;
+    const float2* B = a.Y;
     const int ntx = (p.Lc[0] + TILE_X - 1) / TILE_X;
     const int ntiles = ntx * ((p.Lc[1] + TILE_Y - 1) / TILE_Y);
     double nrm = 0.0;
@@ -694,7 +734,7 @@ __device__ double pcg_apply(const PcgArgs& a, TileSmem& sm, unsigned& phase, con
         const int x0 = (tile % ntx) * TILE_X, y0 = (tile / ntx) * TILE_Y;
         __syncthreads();                        // previous tile's shared data fully consumed
         tile_issue_blocks(sm, B, p, x0, y0);
-        tile_stage<true>(sm, in, p, x0, y0);
+        tile_stage<true, float2>(sm, in, p, x0, y0);
         __syncthreads();
         if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
             mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
@@ -711,7 +751,7 @@ __device__ double pcg_apply(const PcgArgs& a, TileSmem& sm, unsigned& phase, con
 
 __global__ void __launch_bounds__(PCG_THREADS) k_coarse_cgnr_persistent(PcgArgs a) {
     extern __shared__ __align__(128) unsigned char pcg_raw[];
-    TileSmem& sm = *reinterpret_cast<TileSmem*>(pcg_raw);
+    TileSmemT<float2>& sm = *reinterpret_cast<TileSmemT<float2>*>(pcg_raw);
     const long long n = a.cp.Vc * a.cp.Ls_c * a.cp.ncd;
     const unsigned long long deadline = global_ns() + a.timeout_ns;
     const double mf = a.mf;
@@ -812,9 +852,9 @@ dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec,
         int nsm = 0, per = 0;
         DWF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_cgnr_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)sizeof(TileSmem)));
+                                            (int)sizeof(TileSmemT<float2>)));
         DWF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_cgnr_persistent, PCG_THREADS,
-                                                                     sizeof(TileSmem)));
+                                                                     sizeof(TileSmemT<float2>)));
         if (per < 1) { set_error("persistent coarse solver cannot be resident"); return DWF_ERR_UNSUPPORTED; }
         plan.grid = nsm * per;
     }
@@ -839,7 +879,7 @@ dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec,
     DWF_CHECK_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));   // count, gen; the error flag persists
     void* args[] = {&a};
     DWF_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_cgnr_persistent, dim3(grid), dim3(PCG_THREADS), args,
-                                               sizeof(TileSmem), st));
+                                               sizeof(TileSmemT<float2>), st));
     return DWF_OK;
 }
 

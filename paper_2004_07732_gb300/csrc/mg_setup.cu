@@ -286,6 +286,17 @@ __global__ void k_blocks_to_f32(const double2* __restrict__ Y, float2* __restric
     }
 }
 
+__global__ void k_blocks_to_f16(const double2* __restrict__ Y, __half2* __restrict__ Y16, long long nblocks, int ncd) {
+    const long long n = nblocks * ncd * ncd;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long blk = t / (ncd * ncd);
+        const int e = (int)(t % (ncd * ncd));
+        const int i = e / ncd, j = e % ncd;            // row-major source
+        const double2 v = Y[t];
+        Y16[blk * ncd * ncd + (long long)j * ncd + i] = __halves2half2(__double2half(v.x), __double2half(v.y));
+    }
+}
+
 __global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         b[t] = make_float2((float)a[t].x, (float)a[t].y);
@@ -375,6 +386,15 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
     k_blocks_to_f32<<<ew_grid(nblk * m.ncd * m.ncd), 256, 0, st>>>(h->Y64, h->Y32, nblk, m.ncd);
     DWF_CHECK_LAUNCH();
     DWF_TRY(build_adjoint_blocks(h, st));
+    if (h->prm.coarse_block_prec == DWF_F32_L16) {
+        DWF_TRY(mg_alloc(h, &h->Ytile, nblk * m.ncd * m.ncd * sizeof(__half2)));
+        k_blocks_to_f16<<<ew_grid(nblk * m.ncd * m.ncd), 256, 0, st>>>(h->Y64, (__half2*)h->Ytile, nblk, m.ncd);
+        DWF_CHECK_LAUNCH();
+        h->ytile_half = 1;
+    } else {
+        h->Ytile = h->Y32;
+        h->ytile_half = 0;
+    }
     int hstat = 0;
     DWF_CHECK_CUDA(cudaMemcpyAsync(&hstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     DWF_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -410,7 +430,8 @@ void dwf_mg_default_params(dwf_mg_params* p) {
     p->max_restarts = 1000;
     p->coarse_persistent = 1;
     p->coarse_solver = 1;
-    p->coarse_restart = 16;
+    p->coarse_restart = 8;
+    p->coarse_block_prec = DWF_F32_L16;
 }
 
 dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,
@@ -427,6 +448,9 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
     if (prm.Ls_c < 1) { set_error("Ls_c must be >= 1"); return DWF_ERR_ARG; }
     if (!valid_prec(prm.fine_prec) || prm.fine_prec == DWF_F64) {
         set_error("fine_prec must be one of the FP32 precisions"); return DWF_ERR_ARG;
+    }
+    if (prm.coarse_block_prec != DWF_F32 && prm.coarse_block_prec != DWF_F32_L16) {
+        set_error("coarse_block_prec must be DWF_F32 or DWF_F32_L16"); return DWF_ERR_ARG;
     }
     if (prm.gcr_restart < 1 || prm.post_smooth < 0 || prm.coarse_maxiter < 1 || prm.setup_maxiter < 0) {
         set_error("bad solver parameters"); return DWF_ERR_ARG;
@@ -469,7 +493,13 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
     h->ws_ready = false;
     h->hsc = nullptr;
     h->x64 = h->r64 = nullptr;
-    dwf_status s = setup_impl(h, U, null_starts);
+    h->solver_meta = nullptr;
+    h->solver_meta_ready = false;
+    h->coarse_graph_first = nullptr;
+    h->coarse_graph_cycle = nullptr;
+    h->cap_stream = nullptr;
+    dwf_status s = coarse_init_attributes();
+    if (s == DWF_OK) s = setup_impl(h, U, null_starts);
     if (s != DWF_OK) {
         std::string msg = dwf_last_error();
         mg_destroy(h);
@@ -486,6 +516,10 @@ void mg_destroy(dwf_mg* h) {
     for (void* p : h->allocs) cudaFree(p);
     for (void* p : h->fine_vecs) cudaFree(p);
     for (void* p : h->coarse_vecs) cudaFree(p);
+    if (h->solver_meta) cudaFree(h->solver_meta);
+    if (h->coarse_graph_first) cudaGraphExecDestroy(h->coarse_graph_first);
+    if (h->coarse_graph_cycle) cudaGraphExecDestroy(h->coarse_graph_cycle);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->hsc) cudaFreeHost(h->hsc);
     delete h;
 }

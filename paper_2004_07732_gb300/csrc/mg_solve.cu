@@ -24,6 +24,8 @@
 namespace dwf {
 
 constexpr int GCR_MAXK = 32;
+// Gram-Schmidt passes per GCR step (2 = CGS2, re-orthogonalised)
+constexpr int CGS_PASSES = 2;
 
 struct GcrScal {
     double coef[GCR_MAXK][2];
@@ -57,70 +59,6 @@ struct SolveScal {
 // --------------------------------------------------------------------------
 #define GRID_LOOP(i, n) for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-// coef = <Wj, w> / nrm_j
-__global__ void __launch_bounds__(RED_THREADS) k_ortho_first(const float2* __restrict__ Wj, const float2* __restrict__ w,
-                                                             long long n, RedScratch rs, double* coef, const double* nrm_j,
-                                                             const int* skip) {
-    if (skip && *skip) return;
-    double v[2] = {0.0, 0.0};
-    GRID_LOOP(i, n) {
-        float2 a = Wj[i], b = w[i];
-        v[0] += (double)a.x * b.x + (double)a.y * b.y;
-        v[1] += (double)a.x * b.y - (double)a.y * b.x;
-    }
-    grid_reduce<2>(v, rs, [=] __device__(double* t) {
-        const double nn = *nrm_j;
-        coef[0] = nn > 0 ? t[0] / nn : 0.0;
-        coef[1] = nn > 0 ? t[1] / nn : 0.0;
-    });
-}
-
-// w -= c Wj, z -= c Zj (if Wj != null); then either
-//   next coef = <Wn, w> / nrm_next           (Wn != null), or
-//   nrm_out = |w|^2, alpha = <w, r> / |w|^2 (Wn == null)
-template <bool LAST>
-__global__ void __launch_bounds__(RED_THREADS) k_ortho_step(float2* __restrict__ w, float2* __restrict__ z,
-                                                            const float2* __restrict__ Wj, const float2* __restrict__ Zj,
-                                                            const double* coef, const float2* __restrict__ Wn,
-                                                            const float2* __restrict__ r, long long n, RedScratch rs,
-                                                            double* out, const double* nrm_next, double* alpha_out,
-                                                            const int* skip) {
-    if (skip && *skip) return;
-    float cr = 0.f, ci = 0.f;
-    if (Wj) { cr = (float)coef[0]; ci = (float)coef[1]; }
-    double v[3] = {0.0, 0.0, 0.0};
-    GRID_LOOP(i, n) {
-        float2 wi = w[i];
-        if (Wj) {
-            float2 a = Wj[i], b = Zj[i], zi = z[i];
-            wi.x -= cr * a.x - ci * a.y; wi.y -= cr * a.y + ci * a.x;
-            zi.x -= cr * b.x - ci * b.y; zi.y -= cr * b.y + ci * b.x;
-            w[i] = wi; z[i] = zi;
-        }
-        if (!LAST) {
-            float2 a = Wn[i];
-            v[0] += (double)a.x * wi.x + (double)a.y * wi.y;
-            v[1] += (double)a.x * wi.y - (double)a.y * wi.x;
-        } else {
-            float2 ri = r[i];
-            v[0] += (double)wi.x * wi.x + (double)wi.y * wi.y;
-            v[1] += (double)wi.x * ri.x + (double)wi.y * ri.y;
-            v[2] += (double)wi.x * ri.y - (double)wi.y * ri.x;
-        }
-    }
-    grid_reduce<3>(v, rs, [=] __device__(double* t) {
-        if (!LAST) {
-            const double nn = *nrm_next;
-            out[0] = nn > 0 ? t[0] / nn : 0.0;
-            out[1] = nn > 0 ? t[1] / nn : 0.0;
-        } else {
-            out[0] = t[0];
-            alpha_out[0] = t[0] > 0 ? t[1] / t[0] : 0.0;
-            alpha_out[1] = t[0] > 0 ? t[2] / t[0] : 0.0;
-        }
-    });
-}
-
 // x += alpha z, r -= alpha w, rr2 = |r|^2.  With a stop flag: skipped once
 // *done is set, and *done is set when rr2 <= tol2 * (*ref2) or the iteration
 // counter reaches maxit.
@@ -131,12 +69,30 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_update(float2* __restrict__
                                                             int maxit) {
     if (done && *done) return;
     const float ar = (float)alpha[0], ai = (float)alpha[1];
+    float acc = 0.f;     // per-thread FP32 partial; FP64 from the warp sum on
     double v[1] = {0.0};
-    GRID_LOOP(i, n) {
-        float2 zi = z[i], wi = w[i], xi = x[i], ri = r[i];
+    float4* x4 = reinterpret_cast<float4*>(x);
+    float4* r4 = reinterpret_cast<float4*>(r);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    const long long n2 = n >> 1;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        const float4 zi = z4[i], wi = w4[i];
+        float4 xi = x4[i], ri = r4[i];
+        xi.x += ar * zi.x - ai * zi.y; xi.y += ar * zi.y + ai * zi.x;
+        xi.z += ar * zi.z - ai * zi.w; xi.w += ar * zi.w + ai * zi.z;
+        ri.x -= ar * wi.x - ai * wi.y; ri.y -= ar * wi.y + ai * wi.x;
+        ri.z -= ar * wi.z - ai * wi.w; ri.w -= ar * wi.w + ai * wi.z;
+        x4[i] = xi; r4[i] = ri;
+        acc += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
+    }
+    v[0] = acc;
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const float2 zi = z[n - 1], wi = w[n - 1];
+        float2 xi = x[n - 1], ri = r[n - 1];
         xi.x += ar * zi.x - ai * zi.y; xi.y += ar * zi.y + ai * zi.x;
         ri.x -= ar * wi.x - ai * wi.y; ri.y -= ar * wi.y + ai * wi.x;
-        x[i] = xi; r[i] = ri;
+        x[n - 1] = xi; r[n - 1] = ri;
         v[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
     }
     grid_reduce<1>(v, rs, [=] __device__(double* t) {
@@ -146,6 +102,141 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_update(float2* __restrict__
             if (t[0] <= tol2 * (*ref2) || *iters >= maxit) *done = 1;
         }
     });
+}
+
+// ---- classical Gram-Schmidt ------------------------------------------------
+// Vectors are read as float4 (two complex values) so that every load moves 16
+// bytes; loops are unrolled so several loads are in flight per thread.
+// coef[j] (+)= <W_j, w> / nrm[j] for j < k.  Grid (B, k): block (b, j) reduces
+// a slice of row j; the last block of row j (per-row completion counter)
+// finalises coef[j] in a fixed order.
+constexpr int MDOT_BLOCKS = 152;
+
+// per-thread partials of FP32 products are kept in FP32 (a few terms per
+// thread); the cross-thread sums are FP64
+__device__ __forceinline__ void cdot_acc(const float4 a, const float4 b, float& re, float& im) {
+    re += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    im += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(float2* const* __restrict__ W, const float2* __restrict__ w,
+                                                      long long n, double* __restrict__ part, unsigned* counters,
+                                                      double (*coef)[2], const double* nrm, int accumulate,
+                                                      const int* skip) {
+    if (skip && *skip) return;
+    const int j = blockIdx.y;
+    const float4* Wj = reinterpret_cast<const float4*>(W[j]);
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    const long long n2 = n >> 1;
+    float re = 0.f, im = 0.f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n2; i += 4 * stride) {
+        const float4 a0 = Wj[i], a1 = Wj[i + stride], a2 = Wj[i + 2 * stride], a3 = Wj[i + 3 * stride];
+        const float4 b0 = w4[i], b1 = w4[i + stride], b2 = w4[i + 2 * stride], b3 = w4[i + 3 * stride];
+        cdot_acc(a0, b0, re, im);
+        cdot_acc(a1, b1, re, im);
+        cdot_acc(a2, b2, re, im);
+        cdot_acc(a3, b3, re, im);
+    }
+    for (; i < n2; i += stride) cdot_acc(Wj[i], w4[i], re, im);
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const float2 a = W[j][n - 1], b = w[n - 1];
+        re += a.x * b.x + a.y * b.y;
+        im += a.x * b.y - a.y * b.x;
+    }
+    double v[2] = {re, im};
+    block_sum<2>(v);
+    if (threadIdx.x == 0) {
+        part[(2 * j) * MDOT_BLOCKS + blockIdx.x] = v[0];
+        part[(2 * j + 1) * MDOT_BLOCKS + blockIdx.x] = v[1];
+    }
+    if (!grid_last_block(counters + (size_t)j * (RED_GROUPS + 1) * RED_CSTRIDE)) return;
+    __threadfence();
+    // the partials of row j are summed by the whole block (strided, then a
+    // fixed-order block reduction)
+    double w2[2] = {0.0, 0.0};
+    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
+        w2[0] += __ldcg(part + (2 * j) * MDOT_BLOCKS + bb);
+        w2[1] += __ldcg(part + (2 * j + 1) * MDOT_BLOCKS + bb);
+    }
+    block_sum<2>(w2);
+    if (threadIdx.x == 0) {
+        const double nn = nrm[j];
+        const double re = nn > 0 ? w2[0] / nn : 0.0;
+        const double im = nn > 0 ? w2[1] / nn : 0.0;
+        if (accumulate) { coef[j][0] += re; coef[j][1] += im; }
+        else { coef[j][0] = re; coef[j][1] = im; }
+    }
+}
+
+// w -= sum_j c_j W_j and z -= sum_j c_j Z_j.  FINAL: also nrm_out = |w|^2 and
+// alpha = <w, r> / |w|^2 (grid reduction).
+__device__ __forceinline__ void csub2(float4& x, const float4 a, const float2 c) {
+    x.x -= c.x * a.x - c.y * a.y; x.y -= c.x * a.y + c.y * a.x;
+    x.z -= c.x * a.z - c.y * a.w; x.w -= c.x * a.w + c.y * a.z;
+}
+
+template <bool FINAL>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy(float2* __restrict__ w, float2* __restrict__ z,
+                                                       float2* const* __restrict__ W, float2* const* __restrict__ Z,
+                                                       const double (*coef)[2], int k, const float2* __restrict__ r,
+                                                       long long n, RedScratch rs, double* nrm_out, double* alpha_out,
+                                                       const int* skip) {
+    if (skip && *skip) return;
+    __shared__ float2 c[GCR_MAXK];
+    __shared__ const float4* Wp[GCR_MAXK];
+    __shared__ const float4* Zp[GCR_MAXK];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        c[j] = make_float2((float)coef[j][0], (float)coef[j][1]);
+        Wp[j] = reinterpret_cast<const float4*>(W[j]);
+        Zp[j] = reinterpret_cast<const float4*>(Z[j]);
+    }
+    __syncthreads();
+    float4* w4 = reinterpret_cast<float4*>(w);
+    float4* z4 = reinterpret_cast<float4*>(z);
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    const long long n2 = n >> 1;
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        float4 wi = w4[i], zi = k > 0 ? z4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int j = 0;
+        for (; j + 3 < k; j += 4) {
+            const float4 a0 = Wp[j][i], a1 = Wp[j + 1][i], a2 = Wp[j + 2][i], a3 = Wp[j + 3][i];
+            const float4 b0 = Zp[j][i], b1 = Zp[j + 1][i], b2 = Zp[j + 2][i], b3 = Zp[j + 3][i];
+            csub2(wi, a0, c[j]); csub2(wi, a1, c[j + 1]); csub2(wi, a2, c[j + 2]); csub2(wi, a3, c[j + 3]);
+            csub2(zi, b0, c[j]); csub2(zi, b1, c[j + 1]); csub2(zi, b2, c[j + 2]); csub2(zi, b3, c[j + 3]);
+        }
+        for (; j < k; ++j) { csub2(wi, Wp[j][i], c[j]); csub2(zi, Zp[j][i], c[j]); }
+        if (k > 0) { w4[i] = wi; z4[i] = zi; }
+        if (FINAL) {
+            const float4 ri = r4[i];
+            f0 += wi.x * wi.x + wi.y * wi.y + wi.z * wi.z + wi.w * wi.w;
+            cdot_acc(wi, ri, f1, f2);
+        }
+    }
+    double v[3] = {f0, f1, f2};
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {     // odd tail element
+        float2 wi = w[n - 1], zi = z[n - 1];
+        for (int j = 0; j < k; ++j) {
+            const float2 a = W[j][n - 1], b = Z[j][n - 1];
+            wi.x -= c[j].x * a.x - c[j].y * a.y; wi.y -= c[j].x * a.y + c[j].y * a.x;
+            zi.x -= c[j].x * b.x - c[j].y * b.y; zi.y -= c[j].x * b.y + c[j].y * b.x;
+        }
+        if (k > 0) { w[n - 1] = wi; z[n - 1] = zi; }
+        if (FINAL) {
+            const float2 ri = r[n - 1];
+            v[0] += (double)wi.x * wi.x + (double)wi.y * wi.y;
+            v[1] += (double)wi.x * ri.x + (double)wi.y * ri.y;
+            v[2] += (double)wi.x * ri.y - (double)wi.y * ri.x;
+        }
+    }
+    if (FINAL)
+        grid_reduce<3>(v, rs, [=] __device__(double* t) {
+            *nrm_out = t[0];
+            alpha_out[0] = t[0] > 0 ? t[1] / t[0] : 0.0;
+            alpha_out[1] = t[0] > 0 ? t[2] / t[0] : 0.0;
+        });
 }
 
 __global__ void k_sub32(float2* __restrict__ out, const float2* __restrict__ a, const float2* __restrict__ b, long long n) {
@@ -257,6 +348,9 @@ struct Solver {
     double2 *r64, *t64;
     double* partials;    // persistent coarse solver partial sums
     float2 *Zc[GCR_MAXK], *Wc[GCR_MAXK];   // coarse GCR basis
+    float2** dptr;       // device copies of the basis pointer arrays: Z, W, Ps, Qs, Zc, Wc
+    double* mpart;       // CGS partial sums [2 GCR_MAXK][MDOT_BLOCKS]
+    unsigned* mcount;    // CGS per-row completion counters [GCR_MAXK]
     long long fine_applies, coarse_applies, coarse_iters, coarse_solves;
 };
 
@@ -270,6 +364,15 @@ static dwf_status ensure_workspace(dwf_mg* h) {
         cudaError_t e = cudaMalloc(&p, nf * sizeof(float2));
         if (e != cudaSuccess) { set_error("solver vectors: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
         h->fine_vecs.push_back(p);
+    }
+    {
+        void* p = nullptr;   // 6 pointer arrays + CGS partials + counters
+        const size_t bytes = 6 * GCR_MAXK * sizeof(float2*) + 2 * GCR_MAXK * MDOT_BLOCKS * sizeof(double) +
+                             (size_t)GCR_MAXK * (RED_GROUPS + 1) * RED_CSTRIDE * sizeof(unsigned);
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) { set_error("solver pointer arrays: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
+        DWF_CHECK_CUDA(cudaMemset(p, 0, bytes));
+        h->solver_meta = p;
     }
     const int KC = h->prm.coarse_restart;
     for (int k = 0; k < 9 + 2 * KC; ++k) {   // 8 coarse vectors, persistent-solver partials, coarse GCR basis
@@ -293,9 +396,9 @@ static void bind(Solver& s, dwf_mg* h) {
     s.st = h->st;
     s.nf = fine_len(h);
     s.nc = coarse_len(h);
-    s.rg = red_grid(s.nf);
+    s.rg = red_grid4(s.nf);
     s.eg = ew_grid(s.nf);
-    s.rgc = red_grid(s.nc);
+    s.rgc = red_grid4(s.nc);
     s.egc = ew_grid(s.nc);
     int i = 0;
     auto F = [&]() { return (float2*)h->fine_vecs[i++]; };
@@ -310,6 +413,22 @@ static void bind(Solver& s, dwf_mg* h) {
         s.Wc[k] = (float2*)h->coarse_vecs[10 + 2 * k];
     }
     s.d = (SolveScal*)h->coarse_vecs[9 + 2 * h->prm.coarse_restart];
+    s.dptr = (float2**)h->solver_meta;
+    s.mpart = (double*)(s.dptr + 6 * GCR_MAXK);
+    s.mcount = (unsigned*)(s.mpart + 2 * GCR_MAXK * MDOT_BLOCKS);
+    if (!h->solver_meta_ready) {
+        float2* hp[6 * GCR_MAXK] = {};
+        for (int k = 0; k < GCR_MAXK; ++k) {
+            hp[0 * GCR_MAXK + k] = k < h->prm.gcr_restart ? s.Z[k] : nullptr;
+            hp[1 * GCR_MAXK + k] = k < h->prm.gcr_restart ? s.W[k] : nullptr;
+            hp[2 * GCR_MAXK + k] = k < h->prm.post_smooth ? s.Ps[k] : nullptr;
+            hp[3 * GCR_MAXK + k] = k < h->prm.post_smooth ? s.Qs[k] : nullptr;
+            hp[4 * GCR_MAXK + k] = k < h->prm.coarse_restart ? s.Zc[k] : nullptr;
+            hp[5 * GCR_MAXK + k] = k < h->prm.coarse_restart ? s.Wc[k] : nullptr;
+        }
+        cudaMemcpy(s.dptr, hp, sizeof(hp), cudaMemcpyHostToDevice);
+        h->solver_meta_ready = true;
+    }
     s.hs = (SolveScal*)h->hsc;
     s.r64 = (double2*)h->r64;
     s.t64 = (double2*)h->x64;
@@ -327,24 +446,30 @@ static dwf_status apply_A(Solver& s, const float2* in, float2* out) {
 
 // Orthogonalise (z, w) = (Z[k], W[k]) against the first k pairs of the basis
 // and compute nrm[k], alpha = <w, r> / nrm[k].
+// Orthogonalise (z, w) = (Zb[k], Wb[k]) against the first k pairs of the basis
+// by classical Gram-Schmidt applied twice, then nrm[k] = |w|^2 and
+// alpha = <w, r> / |w|^2.  dZ / dW: device copies of the pointer arrays.
 static dwf_status gcr_orthogonalise(Solver& s, GcrScal* g, float2** Zb, float2** Wb, int k, const float2* r, long long n,
-                                    const int* skip = nullptr) {
+                                    float2* const* dZ, float2* const* dW, const int* skip = nullptr) {
     RedScratch rs = s.h->ws.red();
-    const int rg = red_grid(n);
-    if (k == 0) {
-        k_ortho_step<true><<<rg, RED_THREADS, 0, s.st>>>(Wb[0], Zb[0], nullptr, nullptr, nullptr, nullptr, r, n, rs,
-                                                         &g->nrm[0], nullptr, g->alpha, skip);
-        DWF_CHECK_LAUNCH();
-        return DWF_OK;
-    }
-    k_ortho_first<<<rg, RED_THREADS, 0, s.st>>>(Wb[0], Wb[k], n, rs, g->coef[0], &g->nrm[0], skip);
-    for (int j = 0; j < k; ++j) {
-        if (j + 1 < k)
-            k_ortho_step<false><<<rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], Wb[j], Zb[j], g->coef[j], Wb[j + 1], nullptr,
-                                                              n, rs, g->coef[j + 1], &g->nrm[j + 1], nullptr, skip);
-        else
-            k_ortho_step<true><<<rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], Wb[j], Zb[j], g->coef[j], nullptr, r, n, rs,
-                                                             &g->nrm[k], nullptr, g->alpha, skip);
+    const int rg = red_grid4(n);
+    if (k > 0) {
+        dim3 mgrid((unsigned)(rg < MDOT_BLOCKS ? rg : MDOT_BLOCKS), (unsigned)k);
+        const long long n2 = (n + 1) / 2;
+        const int eg = (int)((n2 + RED_THREADS - 1) / RED_THREADS < 152LL * 16 ? (n2 + RED_THREADS - 1) / RED_THREADS
+                                                                               : 152LL * 16);
+        for (int pass = 0; pass < CGS_PASSES; ++pass) {
+            k_mdot<<<mgrid, RED_THREADS, 0, s.st>>>(dW, Wb[k], n, s.mpart, s.mcount, g->coef, g->nrm, 0, skip);
+            if (pass + 1 < CGS_PASSES)
+                k_maxpy<false><<<eg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], dW, dZ, g->coef, k, r, n, rs, nullptr,
+                                                             nullptr, skip);
+            else
+                k_maxpy<true><<<rg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], dW, dZ, g->coef, k, r, n, rs, &g->nrm[k],
+                                                            g->alpha, skip);
+        }
+    } else {
+        k_maxpy<true><<<rg, RED_THREADS, 0, s.st>>>(Wb[0], Zb[0], dW, dZ, g->coef, 0, r, n, rs, &g->nrm[0], g->alpha,
+                                                    skip);
     }
     DWF_CHECK_LAUNCH();
     return DWF_OK;
@@ -352,36 +477,77 @@ static dwf_status gcr_orthogonalise(Solver& s, GcrScal* g, float2** Zb, float2**
 
 // Coarse solve with restarted GCR on B e = r_c, B = Dhat_PV^dag Dhat_DW (the
 // paper's level-2 operator and solver type; B's spectrum lies in the right
-// half plane, App. B).  Iterations run in batches of one restart cycle with a
-// device-side stop flag; the host reads the flag once per cycle.
-static dwf_status coarse_solve_gcr(Solver& s) {
+// half plane, App. B).  One restart cycle is a fixed launch sequence whose
+// kernels skip their work once the device-side stop flag is set; it is
+// captured once per handle as a CUDA graph (plus a variant that starts with
+// the prologue), and the host reads the flag once per cycle.
+static dwf_status coarse_gcr_prologue(Solver& s) {
+    const long long n = s.nc;
+    DWF_CHECK_CUDA(cudaMemsetAsync(s.ec, 0, n * sizeof(float2), s.st));
+    DWF_CHECK_CUDA(cudaMemcpyAsync(s.crr, s.rc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
+    DWF_CHECK_CUDA(cudaMemsetAsync(&s.d->cdone, 0, 2 * sizeof(int), s.st));
+    DWF_TRY(dot_device(s.rc, s.rc, n, false, s.h->ws.red(), s.d->misc + 4, s.st));
+    DWF_CHECK_CUDA(cudaMemcpyAsync(&s.d->cref2, s.d->misc + 4, sizeof(double), cudaMemcpyDeviceToDevice, s.st));
+    return DWF_OK;
+}
+
+static dwf_status coarse_gcr_cycle(Solver& s) {
     dwf_mg* h = s.h;
     const long long n = s.nc;
     RedScratch rs = h->ws.red();
     GcrScal* g = &s.d->cgcr;
     int* done = &s.d->cdone;
     const int K = h->prm.coarse_restart;
-    const int maxit = h->prm.coarse_maxiter;
     const double tol2 = h->prm.coarse_tol * h->prm.coarse_tol;
-    DWF_CHECK_CUDA(cudaMemsetAsync(s.ec, 0, n * sizeof(float2), s.st));
-    DWF_CHECK_CUDA(cudaMemcpyAsync(s.crr, s.rc, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
-    DWF_CHECK_CUDA(cudaMemsetAsync(&s.d->cdone, 0, 2 * sizeof(int), s.st));
-    DWF_TRY(dot_device(s.rc, s.rc, n, false, rs, s.d->misc + 4, s.st));
-    DWF_CHECK_CUDA(cudaMemcpyAsync(&s.d->cref2, s.d->misc + 4, sizeof(double), cudaMemcpyDeviceToDevice, s.st));
+    for (int k = 0; k < K; ++k) {
+        DWF_CHECK_CUDA(cudaMemcpyAsync(s.Zc[k], s.crr, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
+        DWF_TRY(coarse_dwf_apply(h, s.Zc[k], s.ct, h->mf, false, done, s.st));
+        DWF_TRY(coarse_dwf_apply(h, s.ct, s.Wc[k], 1.0, true, done, s.st));
+        DWF_TRY(gcr_orthogonalise(s, g, s.Zc, s.Wc, k, s.crr, n, s.dptr + 4 * GCR_MAXK, s.dptr + 5 * GCR_MAXK, done));
+        k_gcr_update<<<s.rgc, RED_THREADS, 0, s.st>>>(s.ec, s.crr, s.Zc[k], s.Wc[k], g->alpha, n, rs, &g->rr2, done,
+                                                      &s.d->cref2, tol2, &s.d->citers, h->prm.coarse_maxiter);
+        DWF_CHECK_LAUNCH();
+    }
+    return DWF_OK;
+}
+
+// Records the launch sequence on the handle's private capture stream (the
+// caller's stream may be the legacy default stream, which cannot capture);
+// the instantiated graph is launched on the caller's stream.
+static dwf_status capture(Solver& s, bool with_prologue, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    if (!s.h->cap_stream) DWF_CHECK_CUDA(cudaStreamCreateWithFlags(&s.h->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t user = s.st;
+    s.st = s.h->cap_stream;
+    DWF_CHECK_CUDA(cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal));
+    dwf_status st = DWF_OK;
+    if (with_prologue) st = coarse_gcr_prologue(s);
+    if (st == DWF_OK) st = coarse_gcr_cycle(s);
+    cudaError_t e = cudaStreamEndCapture(s.st, &graph);
+    s.st = user;
+    if (st != DWF_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) { set_error("graph capture: %s", cudaGetErrorString(e)); return DWF_ERR_CUDA; }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { set_error("graph instantiation: %s", cudaGetErrorString(e)); return DWF_ERR_CUDA; }
+    return DWF_OK;
+}
+
+static dwf_status coarse_solve_gcr(Solver& s) {
+    dwf_mg* h = s.h;
+    const int K = h->prm.coarse_restart;
+    const int maxit = h->prm.coarse_maxiter;
+    if (!h->coarse_graph_first) {
+        DWF_TRY(capture(s, true, &h->coarse_graph_first));
+        DWF_TRY(capture(s, false, &h->coarse_graph_cycle));
+    }
     int launched = 0;
-    while (launched < maxit) {
-        for (int k = 0; k < K && launched < maxit; ++k, ++launched) {
-            DWF_CHECK_CUDA(cudaMemcpyAsync(s.Zc[k], s.crr, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
-            DWF_TRY(coarse_dwf_apply(h, s.Zc[k], s.ct, h->mf, false, done, s.st));
-            DWF_TRY(coarse_dwf_apply(h, s.ct, s.Wc[k], 1.0, true, done, s.st));
-            DWF_TRY(gcr_orthogonalise(s, g, s.Zc, s.Wc, k, s.crr, n, done));
-            k_gcr_update<<<s.rgc, RED_THREADS, 0, s.st>>>(s.ec, s.crr, s.Zc[k], s.Wc[k], g->alpha, n, rs, &g->rr2, done,
-                                                          &s.d->cref2, tol2, &s.d->citers, maxit);
-            DWF_CHECK_LAUNCH();
-        }
+    for (;;) {
+        DWF_CHECK_CUDA(cudaGraphLaunch(launched == 0 ? h->coarse_graph_first : h->coarse_graph_cycle, s.st));
+        launched += K;
         DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->cdone, &s.d->cdone, 2 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
         DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
-        if (s.hs->cdone) break;
+        if (s.hs->cdone || launched >= maxit) break;
     }
     s.coarse_iters += s.hs->citers;
     s.coarse_applies += 2LL * s.hs->citers;
@@ -457,7 +623,7 @@ static dwf_status precondition(Solver& s, const float2* r, float2* zout, float2*
     for (int j = 0; j < S; ++j) {
         DWF_CHECK_CUDA(cudaMemcpyAsync(s.Ps[j], s.rs_, n * sizeof(float2), cudaMemcpyDeviceToDevice, s.st));
         DWF_TRY(apply_A(s, s.Ps[j], s.Qs[j]));
-        DWF_TRY(gcr_orthogonalise(s, g, s.Ps, s.Qs, j, s.rs_, n));
+        DWF_TRY(gcr_orthogonalise(s, g, s.Ps, s.Qs, j, s.rs_, n, s.dptr + 2 * GCR_MAXK, s.dptr + 3 * GCR_MAXK));
         k_gcr_update<<<s.rg, RED_THREADS, 0, s.st>>>(zout, s.rs_, s.Ps[j], s.Qs[j], g->alpha, n, rs, &g->rr2,
                                                      nullptr, nullptr, 0.0, nullptr, 0);
         DWF_CHECK_LAUNCH();
@@ -545,7 +711,7 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
         if (need > delta) delta = need;
         for (int k = 0; k < K && outer < maxiter; ++k) {
             DWF_TRY(precondition(s, s.r, s.Z[k], s.W[k]));
-            DWF_TRY(gcr_orthogonalise(s, g, s.Z, s.W, k, s.r, n));
+            DWF_TRY(gcr_orthogonalise(s, g, s.Z, s.W, k, s.r, n, s.dptr + 0 * GCR_MAXK, s.dptr + 1 * GCR_MAXK));
             k_gcr_update<<<s.rg, RED_THREADS, 0, s.st>>>(s.e, s.r, s.Z[k], s.W[k], g->alpha, n, rs, &g->rr2,
                                                          nullptr, nullptr, 0.0, nullptr, 0);
             DWF_CHECK_LAUNCH();

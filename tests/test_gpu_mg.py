@@ -109,7 +109,7 @@ def test_coarse_operator_and_transfers_match_oracle(dw, Ls, Ls_c):
     dims, block, nvec, M5, mf = (16, 12), (4, 4), 4, 1.0, 0.03
     U, starts, _ = _problem(dims, Ls, 0.5, nvec, 8)
     h, _ = _setup(dw, dims, Ls, U, starts, M5, mf, {"nvec": nvec, "block": [4, 4, 1, 1], "setup_maxiter": 10,
-                                                     "setup_mass": -0.19, "Ls_c": Ls_c})
+                                                     "setup_mass": -0.19, "Ls_c": Ls_c, "coarse_block_prec": "f32"})
     vecs = dw.mg_get_null_vectors(h).cpu().numpy().reshape(nvec, -1)
     P_o, cdims = omg.build_prolongator(list(vecs), dims, block, 2, 1)
     Dhat = omg.galerkin_kernel(P_o, dirac.wilson_matrix(U, dims, -M5))
