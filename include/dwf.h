@@ -196,6 +196,7 @@ typedef struct {
     int coarse_restart;   /* restart length of the coarse GCR (8)                         */
     int coarse_block_prec;/* storage of the Galerkin blocks read by the coarse stencil:
                              DWF_F32 or DWF_F32_L16 (FP16 blocks, FP32 arithmetic; default) */
+    int cgs_passes;       /* classical Gram-Schmidt passes per GCR step: 1, or 2 (re-orthogonalised) */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;

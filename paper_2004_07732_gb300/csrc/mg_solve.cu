@@ -24,8 +24,6 @@
 namespace dwf {
 
 constexpr int GCR_MAXK = 32;
-// Gram-Schmidt passes per GCR step (2 = CGS2, re-orthogonalised)
-constexpr int CGS_PASSES = 2;
 
 struct GcrScal {
     double coef[GCR_MAXK][2];
@@ -458,9 +456,10 @@ static dwf_status gcr_orthogonalise(Solver& s, GcrScal* g, float2** Zb, float2**
         const long long n2 = (n + 1) / 2;
         const int eg = (int)((n2 + RED_THREADS - 1) / RED_THREADS < 152LL * 16 ? (n2 + RED_THREADS - 1) / RED_THREADS
                                                                                : 152LL * 16);
-        for (int pass = 0; pass < CGS_PASSES; ++pass) {
+        const int passes = s.h->prm.cgs_passes;
+        for (int pass = 0; pass < passes; ++pass) {
             k_mdot<<<mgrid, RED_THREADS, 0, s.st>>>(dW, Wb[k], n, s.mpart, s.mcount, g->coef, g->nrm, 0, skip);
-            if (pass + 1 < CGS_PASSES)
+            if (pass + 1 < passes)
                 k_maxpy<false><<<eg, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], dW, dZ, g->coef, k, r, n, rs, nullptr,
                                                              nullptr, skip);
             else
