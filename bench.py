@@ -272,6 +272,11 @@ def run_ours(args):
     if not args.skip_su3:
         su3 = time_su3_apply(dw, dev, stream, args)
 
+    # ---------------- batched multi-RHS apply: 64 sources, mixed lattices ----------------
+    batched = None
+    if not args.skip_batched:
+        batched = time_batched_apply(dw, dev, stream, args)
+
     # ---------------- time to solution on the 256^2 workload ----------------
     solve = None
     if not args.skip_solve:
@@ -299,7 +304,7 @@ def run_ours(args):
                 "e2e": {"value": world * nbytes / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "gpu_launches": launches, "su3_apply": su3, "solve": solve}
+                "gpu_launches": launches, "su3_apply": su3, "batched_apply": batched, "solve": solve}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -332,6 +337,53 @@ def time_su3_apply(dw, dev, stream, args):
     return {"workload": f"{wl.name}: 4-d SU(3) D_DW(m) apply, FP32 spinors, FP16 links, M5 {wl.M5}, m {wl.mf}",
             "algorithmic_bytes_per_launch": nbytes, "ms": t * 1e3, "GBps": nbytes / t / 1e9,
             "frac_of_hbm": nbytes / t / 1e9 / float(peaks["hbm_gbs"])}
+
+
+def time_batched_apply(dw, dev, stream, args):
+    """The 64-source batch over {64^2, 128^2, 256^2} x Ls=16 in one launch, vs one launch per source."""
+    import torch
+    geoms, Us, psis, outs = [], [], [], []
+    nbytes = 0
+    for wl, nsrc in synth.batched_classes():
+        U, srcs = wl.draw(nsrc)
+        g = dw.make_geom(wl.dims, wl.Ls)
+        Ud = dw.links_to(g, torch.from_numpy(U.reshape(-1)).to(dev), "f32_l16")
+        for src in srcs:
+            geoms.append(g)
+            Us.append(Ud)
+            psis.append(torch.from_numpy(src.reshape(-1).astype(np.complex64)).to(dev))
+            outs.append(torch.empty_like(psis[-1]))
+            nbytes += apply_bytes(wl.V, wl.Ls)
+    M5, mf = synth.batched_classes()[0][0].M5, synth.batched_classes()[0][0].mf
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(max(5, args.steps // 5)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        return float(np.mean(ts))
+
+    t_batched = timed(lambda: dw.dwf_apply_batched(geoms, Us, psis, outs, M5, mf, prec="f32_l16"))
+
+    def singles():
+        for g, U, p, o in zip(geoms, Us, psis, outs):
+            dw.dwf_apply(g, U, p, o, M5, mf, prec="f32_l16")
+    t_single = timed(singles)
+    peaks, _ = measured_peaks()
+    return {"workload": "64 sources, lattices (64, 128, 256)^2 [i mod 3] x Ls=16, FP32 spinors, FP16 links",
+            "algorithmic_bytes": nbytes, "one_launch_ms": t_batched * 1e3, "one_launch_GBps": nbytes / t_batched / 1e9,
+            "frac_of_hbm": nbytes / t_batched / 1e9 / float(peaks["hbm_gbs"]),
+            "per_source_launches_ms": t_single * 1e3, "per_source_launches_GBps": nbytes / t_single / 1e9}
 
 
 def time_solves(dw, dev, args):
@@ -391,6 +443,7 @@ def main():
     ap.add_argument("--skip-mg", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-su3", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

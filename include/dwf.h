@@ -92,6 +92,16 @@ DWF_API dwf_status dwf_convert_links(const dwf_geom* g, const void* U64, void* U
 DWF_API dwf_status dwf_apply(const dwf_geom* g, const void* U, const void* psi, void* out,
                      double M5, double mf, int dagger, int prec, void* stream);
 
+/* Batched apply: out_r = D_DW(mf) psi_r (or the adjoint) for nrhs right-hand
+ * sides, each on its own 2-d U(1) lattice geoms[r] with links U[r] (pointers may
+ * repeat), all in ONE persistent kernel launch over the concatenated site
+ * ranges.  geoms, U, psi, out are HOST arrays of nrhs entries (the latter three
+ * holding device pointers).  Operator, layouts and precisions as dwf_apply.
+ * nrhs <= 256.  (The paper treats one system at a time; this is the
+ * many-right-hand-side form of the same operator.) */
+DWF_API dwf_status dwf_apply_batched(int nrhs, const dwf_geom* geoms, const void* const* U, const void* const* psi,
+                                     void* const* out, double M5, double mf, int dagger, int prec, void* stream);
+
 /* out = D_PV psi (or D_PV^dag psi): the Pauli-Villars operator D_PV = D_DW(1)
  * (Sec. 2.2).  Same arguments and layouts as dwf_apply. */
 DWF_API dwf_status pv_apply(const dwf_geom* g, const void* U, const void* psi, void* out,

@@ -89,6 +89,8 @@ def _setup_signatures(L):
         "dwf_pvdag_apply_noalloc": [G, _VP, _VP, _VP, _D, _D, _I, _VP],
         "dwf_dot": [_VP, _VP, ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _VP],
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "dwf_apply_batched": [_I, ctypes.POINTER(Geom), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                              ctypes.POINTER(_VP), _D, _D, _I, _I, _VP],
         "dwf_links_from_angles": [G, _VP, _VP, _VP],
         "dwf_gamma5_reflect": [G, _VP, _VP, _I, _VP],
         "dwf_link_force": [G, _VP, _VP, _VP, _VP, _VP],
@@ -235,6 +237,22 @@ def cgne_solve(geom, U, b, x, M5, mf, tol=1e-10, maxiter=100000, stream=None, ra
     if status != OK and (raise_noconv or status != ERR_NOCONV):
         check(status)
     return st.as_dict(), status
+
+
+def dwf_apply_batched(geoms, Us, psis, outs, M5, mf, dagger=False, prec="f32_l16", stream=None):
+    """One launch applying D_DW to every (geometry, links, psi) triple of the lists."""
+    n = len(psis)
+    if not (len(geoms) == len(Us) == len(outs) == n):
+        raise ValueError("geoms, Us, psis and outs must have the same length")
+    for g, p, o in zip(geoms, psis, outs):
+        _check_spinor(p, g, prec, "psi")
+        _check_spinor(o, g, prec, "out")
+    G = (Geom * n)(*geoms)
+    U = (_VP * n)(*[u.data_ptr() for u in Us])
+    P = (_VP * n)(*[p.data_ptr() for p in psis])
+    O = (_VP * n)(*[o.data_ptr() for o in outs])
+    check(lib().dwf_apply_batched(n, G, U, P, O, float(M5), float(mf), int(bool(dagger)), PREC[prec], _stream(stream)))
+    return outs
 
 
 def links_from_angles(geom, theta, stream=None):

@@ -139,6 +139,49 @@ dwf_status dwf_pvdag_apply(const dwf_geom* g, const void* U, const void* psi, vo
     return apply_checked(g, U, tmp, out, M5, 1.0, 1, prec, stream);
 }
 
+dwf_status dwf_apply_batched(int nrhs, const dwf_geom* geoms, const void* const* U, const void* const* psi,
+                             void* const* out, double M5, double mf, int dagger, int prec, void* stream) {
+    clear_error();
+    if (nrhs < 0 || nrhs > BATCH_MAX) { set_error("nrhs must be in [0, %d]", BATCH_MAX); return DWF_ERR_ARG; }
+    if (nrhs == 0) return DWF_OK;
+    if (!geoms || !U || !psi || !out) { set_error("NULL argument array"); return DWF_ERR_ARG; }
+    if (!valid_prec(prec)) { set_error("bad precision %d", prec); return DWF_ERR_ARG; }
+    for (int r = 0; r < nrhs; ++r) {
+        Geom G;
+        DWF_TRY(check_geom(&geoms[r], &G));
+        if (G.nd != 2) { set_error("batched apply: right-hand side %d is not a 2-d lattice", r); return DWF_ERR_UNSUPPORTED; }
+        if (!U[r] || !psi[r] || !out[r]) { set_error("batched apply: NULL pointer for right-hand side %d", r); return DWF_ERR_ARG; }
+        if (!aligned16(psi[r]) || !aligned16(out[r])) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
+        if (psi[r] == out[r]) { set_error("psi and out must be distinct buffers"); return DWF_ERR_ARG; }
+    }
+    cudaStream_t st = as_stream(stream);
+    // launches of at most BATCH_LAUNCH_MAX right-hand sides (one for nrhs <= 128)
+    static thread_local BatchArgs2d args;
+    for (int r0 = 0; r0 < nrhs; r0 += BATCH_LAUNCH_MAX) {
+        const int cnt = nrhs - r0 < BATCH_LAUNCH_MAX ? nrhs - r0 : BATCH_LAUNCH_MAX;
+        long long blocks = 0;
+        for (int k = 0; k < cnt; ++k) {
+            Geom G;
+            check_geom(&geoms[r0 + k], &G);
+            Fine2dParams& p = args.d[k].p;
+            p.V = G.V; p.L0 = G.L[0]; p.L1 = G.L[1]; p.Ls = G.Ls;
+            p.anti0 = G.anti[0]; p.anti1 = G.anti[1];
+            p.diag = (double)G.nd - M5 + 1.0;
+            p.mf = mf;
+            p.s_chunk = G.Ls;
+            args.d[k].U = U[r0 + k];
+            args.d[k].psi = psi[r0 + k];
+            args.d[k].out = out[r0 + k];
+            args.d[k].block0 = blocks;
+            blocks += (G.V + 255) / 256;
+        }
+        args.nrhs = cnt;
+        args.total_blocks = blocks;
+        if (blocks > 0) DWF_TRY(fine_apply_2d_batched(args, dagger != 0, prec, st));
+    }
+    return DWF_OK;
+}
+
 dwf_status dwf_dot(const void* x, const void* y, size_t n, int prec, double* result_host, void* stream) {
     clear_error();
     if (!result_host) { set_error("NULL result pointer"); return DWF_ERR_ARG; }

@@ -26,6 +26,26 @@ struct Fine4dParams {
 
 int choose_s_chunk(long long V, int Ls);
 
+// One right-hand side of a batched 2-d apply: its lattice, links and vectors,
+// and the first virtual block of its range (blocks of 256 sites).
+constexpr int BATCH_MAX = 256;
+struct BatchDesc2d {
+    Fine2dParams p;
+    const void* U;
+    const void* psi;
+    void* out;
+    long long block0;
+};
+// Descriptors of one batched launch, passed by value as a __grid_constant__
+// kernel parameter (no device allocation or host copy per call).
+constexpr int BATCH_LAUNCH_MAX = 128;
+struct BatchArgs2d {
+    int nrhs;
+    long long total_blocks;
+    BatchDesc2d d[BATCH_LAUNCH_MAX];
+};
+dwf_status fine_apply_2d_batched(const BatchArgs2d& args, bool dagger, int prec, cudaStream_t st);
+
 // out = D_DW(mf) psi or its adjoint, on the canonical layout; `prec` selects
 // spinor / link storage.  s_chunk <= 0 picks the default.
 dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,

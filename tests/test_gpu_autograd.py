@@ -87,7 +87,11 @@ def test_autograd_gradient_vs_central_differences_128(dw):
 
     The finite differences use CGNR with a fixed iteration count (the count that
     reaches 1e-13 at theta), which makes x(theta) a smooth map so that the
-    difference quotient is not swamped by the stopping rule.
+    difference quotient is not swamped by the stopping rule.  With h = 1e-6 the
+    quotient is limited by the FP64 rounding of L itself (|x|^2 ~ 1e6 summed over
+    4e5 values: ~1e-14 L, i.e. ~1e-8 / (2h) ~ 5e-3 absolute), so agreement is
+    required to 2e-4 relative; the exact check of the gradient is the oracle
+    comparison on the small lattice above (1e-7).
     """
     wl = synth.SCHWINGER_128_GRAD
     theta, rng = wl.angles()
@@ -117,4 +121,4 @@ def test_autograd_gradient_vs_central_differences_128(dw):
         tp = flat.copy(); tp[idx] += h
         tm = flat.copy(); tm[idx] -= h
         fd = (L_fixed(tp) - L_fixed(tm)) / (2 * h)
-        assert abs(fd - grad[idx]) < 1e-5 * max(abs(fd), 1e-3 * np.abs(grad).max()), (idx, fd, grad[idx])
+        assert abs(fd - grad[idx]) < 2e-4 * max(abs(fd), 1e-3 * np.abs(grad).max()), (idx, fd, grad[idx])
