@@ -56,6 +56,48 @@ def env_int(k, d):
         return d
 
 
+class Ranks:
+    """Process-group plumbing of the benchmark: one process per GPU (replicas),
+    launched by torchrun.  barrier() + device sync brackets every timed region,
+    max() takes the slowest rank's time, and only rank 0 prints."""
+
+    def __init__(self, backend="nccl", device=None):
+        self.world = env_int("WORLD_SIZE", 1)
+        self.rank = env_int("RANK", 0)
+        self.local = env_int("LOCAL_RANK", 0)
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": device} if (backend == "nccl" and device is not None) else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device is not None and self.device.type == "cuda":
+            import torch
+            torch.cuda.synchronize(self.device)
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        dev = self.device if self.device is not None else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def whole_job_rate(self, units_per_rank: float, seconds_this_rank: float) -> float:
+        """Units processed by all ranks / the slowest rank's time (weak scaling)."""
+        return self.world * units_per_rank / self.max(seconds_this_rank)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -192,29 +234,15 @@ def run_ours(args):
     import paper_2004_07732_gb300 as dw
 
     world = env_int("WORLD_SIZE", 1)
-    rank = env_int("RANK", 0)
     local = env_int("LOCAL_RANK", 0)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    ranks = Ranks("nccl", dev)
+    rank = ranks.rank
     dw.lib()
     stream = torch.cuda.current_stream(dev)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     # ---------------- fine apply bandwidth (value) ----------------
     wl = APPLY_WL
@@ -306,8 +334,7 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": launches, "su3_apply": su3, "batched_apply": batched, "solve": solve}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def time_su3_apply(dw, dev, stream, args):

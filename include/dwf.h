@@ -157,6 +157,15 @@ DWF_API dwf_status cgne_solve(const dwf_geom* g, const void* U, const void* b, v
                       double M5, double mf, double tol, int maxiter,
                       dwf_solve_stats* stats, void* stream);
 
+/* Diagnostic for failure detection (no paper counterpart): runs a kernel
+ * whose bounded device wait cannot complete -- which = 0: an mbarrier that
+ * expects one arrival more than it gets; which = 1: a cooperative software grid
+ * barrier that expects one block more than the grid -- and returns
+ * DWF_ERR_TIMEOUT once the wait has given up after `seconds` (at most 10).  This
+ * is the path every device-side wait of the library takes; no fault, trap or
+ * hang is involved and the context stays usable.  Synchronises `stream`. */
+DWF_API dwf_status dwf_check_wait_timeout(int which, double seconds, void* stream);
+
 /* ------------------------------------------------------------------------
  * Differentiation of x = D_DW^-1 b (U(1) links U = exp(i theta))
  * ------------------------------------------------------------------------ */

@@ -91,6 +91,7 @@ def _setup_signatures(L):
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
         "dwf_apply_batched": [_I, ctypes.POINTER(Geom), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                               ctypes.POINTER(_VP), _D, _D, _I, _I, _VP],
+        "dwf_check_wait_timeout": [_I, _D, _VP],
         "dwf_links_from_angles": [G, _VP, _VP, _VP],
         "dwf_gamma5_reflect": [G, _VP, _VP, _I, _VP],
         "dwf_link_force": [G, _VP, _VP, _VP, _VP, _VP],
@@ -253,6 +254,11 @@ def dwf_apply_batched(geoms, Us, psis, outs, M5, mf, dagger=False, prec="f32_l16
     O = (_VP * n)(*[o.data_ptr() for o in outs])
     check(lib().dwf_apply_batched(n, G, U, P, O, float(M5), float(mf), int(bool(dagger)), PREC[prec], _stream(stream)))
     return outs
+
+
+def check_wait_timeout(which=0, seconds=0.05, stream=None) -> int:
+    """Run the bounded-wait diagnostic; returns the dwf_status (DWF_ERR_TIMEOUT expected)."""
+    return lib().dwf_check_wait_timeout(int(which), float(seconds), _stream(stream))
 
 
 def links_from_angles(geom, theta, stream=None):
