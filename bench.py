@@ -453,11 +453,48 @@ def time_mg(dw, dev, wl, U, U64, b, g, t_cg):
     st, status = dw.mg_solve(mg, b, x, tol=1e-10, raise_noconv=False)
     torch.cuda.synchronize(dev)
     t_mg = time.perf_counter() - t0
+    coarse_multi = time_coarse_multi(dw, dev, mg, wl.mf)
     dw.mg_destroy(mg)
     return {"mg": {"seconds": t_mg, "setup_seconds": t_setup, "outer_iterations": st["iterations"],
                    "fine_applies": st["fine_applies"], "coarse_avg_iters": st["coarse_avg_iters"],
                    "true_residual": st["true_residual"], "status": status},
-            "mg_speedup_vs_cgne": t_cg / t_mg if t_mg > 0 else None}
+            "mg_speedup_vs_cgne": t_cg / t_mg if t_mg > 0 else None, "coarse_multi_rhs": coarse_multi}
+
+
+def time_coarse_multi(dw, dev, mg, mf, nrhs=64, reps=20):
+    """The Galerkin coarse operator of the solve's hierarchy on nrhs vectors: one tensor-core
+    launch (mg_coarse_apply_multi) against nrhs launches of the one-vector stencil."""
+    import torch
+    nc = mg.coarse_size
+    vin = torch.randn(nrhs, nc, dtype=torch.complex64, device=dev)
+    vout = torch.empty_like(vin)
+    Vc, Ls_c, ncd = mg.Vc, mg.coarse_geom.Ls, mg.ncdof
+    ndir = 1 + 2 * mg.coarse_geom.nd
+    flops = 8.0 * ndir * ncd * ncd * Vc * Ls_c * nrhs
+    nbytes = 8.0 * (ndir * ncd * ncd * Vc + 2 * nrhs * nc)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) * 1e-3 / reps
+
+    t_tc = timed(lambda: dw.mg_coarse_apply_multi(mg, vin, vout, nrhs, mf))
+
+    def singles():
+        for r in range(nrhs):
+            dw.mg_coarse_apply(mg, vin[r], vout[r], mf)
+    t_one = timed(singles)
+    return {"nrhs": nrhs, "coarse_sites": Vc, "Ls_c": Ls_c, "useful_flops": flops, "algorithmic_bytes": nbytes,
+            "tensor_core_ms": t_tc * 1e3, "tensor_core_TFLOPs": flops / t_tc / 1e12,
+            "tensor_core_GBps": nbytes / t_tc / 1e9, "per_vector_launches_ms": t_one * 1e3,
+            "speedup": t_one / t_tc}
 
 
 def main():

@@ -279,6 +279,15 @@ DWF_API dwf_status mg_prolong(const dwf_mg* h, const void* e_coarse, void* e_fin
 DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, double mf, int dagger,
                                    void* stream);
 
+/* The same coarse operator on nrhs right-hand sides at once, on the tensor
+ * cores: in / out hold nrhs coarse vectors back to back ([rhs][s][site][dof],
+ * complex64).  Per coarse site the stencil is a dense contraction over the
+ * nrhs * Ls_c columns, evaluated with mma.sync TF32 products of FP32 data split
+ * into high and low parts (FP32-level accuracy), FP32 accumulation.  2-d, 16
+ * coarse dof. */
+DWF_API dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
+                                         int dagger, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,7 @@ def _setup_signatures(L):
         "mg_restrict": [_VP, _VP, _VP, _VP],
         "mg_prolong": [_VP, _VP, _VP, _VP],
         "mg_coarse_apply": [_VP, _VP, _VP, _D, _I, _VP],
+        "mg_coarse_apply_multi": [_VP, _I, _VP, _VP, _D, _I, _VP],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -419,4 +420,14 @@ def mg_coarse_apply(mg: Multigrid, vin, vout, mf, dagger=False, stream=None):
         if t.dtype != torch.complex64 or t.numel() != mg.coarse_size or not t.is_cuda:
             raise ValueError("coarse vectors must be complex64 CUDA tensors of the coarse size")
     check(lib().mg_coarse_apply(mg.ptr, _ptr(vin), _ptr(vout), float(mf), int(bool(dagger)), _stream(stream)))
+    return vout
+
+
+def mg_coarse_apply_multi(mg: Multigrid, vin, vout, nrhs, mf, dagger=False, stream=None):
+    """Tensor-core coarse operator on nrhs coarse vectors stored back to back."""
+    for t in (vin, vout):
+        if t.dtype != torch.complex64 or t.numel() != nrhs * mg.coarse_size or not t.is_cuda:
+            raise ValueError("coarse vectors must be complex64 CUDA tensors of nrhs x the coarse size")
+    check(lib().mg_coarse_apply_multi(mg.ptr, int(nrhs), _ptr(vin), _ptr(vout), float(mf), int(bool(dagger)),
+                                      _stream(stream)))
     return vout

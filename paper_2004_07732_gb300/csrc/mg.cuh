@@ -75,6 +75,9 @@ dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes);
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger,
                             const int* skip, cudaStream_t st);
 dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st);
+// tensor-core coarse stencil on nrhs right-hand sides ([rhs][s][site][dof])
+dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
+                                 const int* skip, cudaStream_t st);
 // one-time kernel attributes of the coarse stencil (outside any stream capture)
 dwf_status coarse_init_attributes();
 dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st);
