@@ -288,6 +288,31 @@ DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, d
 DWF_API dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
                                          int dagger, void* stream);
 
+/* Batched K-cycle: nrhs right-hand sides that share the hierarchy h (one
+ * gauge field) solved together (the multi-right-hand-side form of the solve
+ * of Sec. 2.3).  b and x hold nrhs complex128 fine vectors back to back; x is
+ * overwritten.  Per right-hand side the iteration is mg_solve's (FP64
+ * reliable updates around FP32 FGCR with the K-cycle preconditioner, stopping
+ * on the FP64 true residual <= tol); every launch covers all right-hand sides,
+ * the coarse operator runs as the tensor-core contraction over the
+ * nrhs * Ls_c columns, and converged systems drop out of the work.  stats:
+ * NULL or an array of nrhs records.  2-d lattices with nvec = 8.  Returns
+ * DWF_ERR_NOCONV if any right-hand side stopped above tol (x holds its last
+ * iterate).  The handle keeps a workspace sized for the largest nrhs seen
+ * (about (6 + 2 gcr_restart + 2 post_smooth) FP32 + 2 FP64 fine vectors per
+ * right-hand side) until mg_destroy. */
+DWF_API dwf_status mg_solve_batched(dwf_mg* h, int nrhs, const void* b, void* x, double tol, int maxiter,
+                                    dwf_solve_stats* stats, void* stream);
+
+/* Several hierarchies (e.g. lattices of different sizes) solved concurrently:
+ * group i runs mg_solve_batched(handles[i], nrhs[i], b[i], x[i], ...) on its
+ * own non-blocking stream and host thread; the call returns when every group
+ * has finished.  The handles must be distinct; stats[i]: NULL or nrhs[i]
+ * records (stats itself may be NULL).  Returns the first failing group's
+ * status, with its index in the message. */
+DWF_API dwf_status mg_solve_groups(int ngroups, dwf_mg* const* handles, const int* nrhs, const void* const* b,
+                                   void* const* x, double tol, int maxiter, dwf_solve_stats* const* stats);
+
 #ifdef __cplusplus
 }
 #endif

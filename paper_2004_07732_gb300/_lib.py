@@ -97,6 +97,9 @@ def _setup_signatures(L):
         "dwf_link_force": [G, _VP, _VP, _VP, _VP, _VP],
         "mg_setup": [G, _VP, _D, _D, ctypes.POINTER(MgParams), _VP, ctypes.POINTER(_VP), _VP],
         "mg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "mg_solve_batched": [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "mg_solve_groups": [_I, ctypes.POINTER(_VP), ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                            _D, _I, ctypes.POINTER(ctypes.POINTER(SolveStats))],
         "mg_coarse_geom": [_VP, G, ctypes.POINTER(ctypes.c_int)],
         "mg_get_prolongator": [_VP, _VP, _VP],
         "mg_get_null_vectors": [_VP, _VP, _VP],
@@ -364,6 +367,43 @@ def mg_solve(mg: Multigrid, b, x, tol=1e-10, maxiter=100000, stream=None, raise_
     if status != OK and (raise_noconv or status != ERR_NOCONV):
         check(status)
     return st.as_dict(), status
+
+
+def _check_block(t, mg: Multigrid, nrhs, name):
+    if not (t.is_cuda and t.is_contiguous()) or t.dtype != torch.complex128:
+        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if t.numel() != nrhs * spinor_size(mg.geom):
+        raise ValueError(f"{name} must hold {nrhs} fine vectors of the hierarchy's lattice")
+
+
+def mg_solve_batched(mg: Multigrid, b, x, nrhs, tol=1e-10, maxiter=100000, stream=None, raise_noconv=True):
+    """Solve D_DW x_r = b_r for nrhs right-hand sides stored back to back (complex128)."""
+    _check_block(b, mg, nrhs, "b")
+    _check_block(x, mg, nrhs, "x")
+    st = (SolveStats * nrhs)()
+    status = lib().mg_solve_batched(mg.ptr, int(nrhs), _ptr(b), _ptr(x), float(tol), int(maxiter), st,
+                                    _stream(stream))
+    if status != OK and (raise_noconv or status != ERR_NOCONV):
+        check(status)
+    return [s.as_dict() for s in st], status
+
+
+def mg_solve_groups(mgs, bs, xs, nrhs, tol=1e-10, maxiter=100000, raise_noconv=True):
+    """Batched solves of several hierarchies at once (one stream and host thread each)."""
+    n = len(mgs)
+    if not (len(bs) == len(xs) == len(nrhs) == n):
+        raise ValueError("mgs, bs, xs and nrhs must have the same length")
+    for mg, b, x, k in zip(mgs, bs, xs, nrhs):
+        _check_block(b, mg, k, "b")
+        _check_block(x, mg, k, "x")
+    stats = [(SolveStats * k)() for k in nrhs]
+    sp = (ctypes.POINTER(SolveStats) * n)(*[ctypes.cast(s, ctypes.POINTER(SolveStats)) for s in stats])
+    status = lib().mg_solve_groups(n, (_VP * n)(*[m.ptr for m in mgs]), (_I * n)(*[int(k) for k in nrhs]),
+                                   (_VP * n)(*[_ptr(b) for b in bs]), (_VP * n)(*[_ptr(x) for x in xs]),
+                                   float(tol), int(maxiter), sp)
+    if status != OK and (raise_noconv or status != ERR_NOCONV):
+        check(status)
+    return [[s.as_dict() for s in st] for st in stats], status
 
 
 def mg_destroy(mg: Multigrid):

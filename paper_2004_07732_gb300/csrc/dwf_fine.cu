@@ -171,6 +171,34 @@ k_dwf2d(const typename LT::store* __restrict__ U, const Sp2<R>* __restrict__ psi
     dwf2d_site<LT, R, DAG, PF>(U, psi, out, p, site, s0, min(s0 + p.s_chunk, p.Ls));
 }
 
+// nrhs right-hand sides on the same lattice and links, stored back to back
+// (stride V * Ls spinors): grid.z walks the right-hand sides; skip[r] != 0
+// (device flags, may be null) leaves right-hand side r untouched.
+template <class LT, class R, bool DAG>
+__global__ void __launch_bounds__(256)
+k_dwf2d_multi(const typename LT::store* __restrict__ U, const Sp2<R>* __restrict__ psi, Sp2<R>* __restrict__ out,
+              Fine2dParams p, const int* __restrict__ skip) {
+    const int r = blockIdx.z;
+    if (skip && skip[r]) return;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.V) return;
+    const int s0 = blockIdx.y * p.s_chunk;
+    if (s0 >= p.Ls) return;
+    const long long off = (long long)r * p.V * p.Ls;
+    dwf2d_site<LT, R, DAG, 1>(U, psi + off, out + off, p, site, s0, min(s0 + p.s_chunk, p.Ls));
+}
+
+template <class LT, class R>
+static void launch2d_multi(const void* U, const void* psi, void* out, const Fine2dParams& p, int nrhs,
+                           const int* skip, bool dagger, cudaStream_t st) {
+    dim3 grid((unsigned)((p.V + 255) / 256), (unsigned)((p.Ls + p.s_chunk - 1) / p.s_chunk), (unsigned)nrhs);
+    auto Ut = reinterpret_cast<const typename LT::store*>(U);
+    auto pi = reinterpret_cast<const Sp2<R>*>(psi);
+    auto po = reinterpret_cast<Sp2<R>*>(out);
+    if (dagger) k_dwf2d_multi<LT, R, true><<<grid, 256, 0, st>>>(Ut, pi, po, p, skip);
+    else        k_dwf2d_multi<LT, R, false><<<grid, 256, 0, st>>>(Ut, pi, po, p, skip);
+}
+
 // Many right-hand sides on possibly different lattices in one launch: virtual
 // block vb of the concatenated block ranges maps to (right-hand side r, block
 // within r) through the descriptors' block offsets (binary search).
@@ -259,6 +287,31 @@ dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* ou
         case DWF_F32:      launch2d<LinkF32, float>(U, psi, out, p, dagger, st); break;
         case DWF_F32_L16:  launch2d<LinkH16, float>(U, psi, out, p, dagger, st); break;
         case DWF_F32_LBF16: launch2d<LinkBF16, float>(U, psi, out, p, dagger, st); break;
+        default: set_error("bad precision %d", prec); return DWF_ERR_ARG;
+    }
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+dwf_status fine_apply_2d_multi(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                               bool dagger, int prec, int nrhs, const int* skip, cudaStream_t st) {
+    if (g.nd != 2) { set_error("multi-right-hand-side fine apply: 2-d lattices only"); return DWF_ERR_UNSUPPORTED; }
+    if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
+    Fine2dParams p;
+    p.V = g.V;
+    p.L0 = g.L[0];
+    p.L1 = g.L[1];
+    p.Ls = g.Ls;
+    p.anti0 = g.anti[0];
+    p.anti1 = g.anti[1];
+    p.diag = (double)g.nd - M5 + 1.0;
+    p.mf = mf;
+    p.s_chunk = choose_s_chunk(g.V * nrhs, g.Ls);
+    switch (prec) {
+        case DWF_F64:       launch2d_multi<LinkF64, double>(U, psi, out, p, nrhs, skip, dagger, st); break;
+        case DWF_F32:       launch2d_multi<LinkF32, float>(U, psi, out, p, nrhs, skip, dagger, st); break;
+        case DWF_F32_L16:   launch2d_multi<LinkH16, float>(U, psi, out, p, nrhs, skip, dagger, st); break;
+        case DWF_F32_LBF16: launch2d_multi<LinkBF16, float>(U, psi, out, p, nrhs, skip, dagger, st); break;
         default: set_error("bad precision %d", prec); return DWF_ERR_ARG;
     }
     DWF_CHECK_LAUNCH();

@@ -50,6 +50,10 @@ dwf_status fine_apply_2d_batched(const BatchArgs2d& args, bool dagger, int prec,
 // spinor / link storage.  s_chunk <= 0 picks the default.
 dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                          bool dagger, int prec, int s_chunk, cudaStream_t st);
+// nrhs right-hand sides of one 2-d lattice stored back to back; skip: per
+// right-hand-side device flags (may be null), nonzero leaves that output untouched.
+dwf_status fine_apply_2d_multi(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                               bool dagger, int prec, int nrhs, const int* skip, cudaStream_t st);
 dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                          bool dagger, int prec, int s_chunk, cudaStream_t st);
 

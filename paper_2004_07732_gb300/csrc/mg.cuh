@@ -64,6 +64,7 @@ struct dwf_mg {
     cudaGraphExec_t coarse_graph_first;   // captured coarse GCR: prologue + one restart cycle
     cudaGraphExec_t coarse_graph_cycle;   // captured coarse GCR: one restart cycle
     cudaStream_t cap_stream;              // private stream used only to record graphs
+    void* batched;                        // workspace and graphs of the batched solver (mg_batched.cu)
 };
 
 namespace dwf {
@@ -75,19 +76,27 @@ dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes);
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger,
                             const int* skip, cudaStream_t st);
 dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st);
-// tensor-core coarse stencil on nrhs right-hand sides ([rhs][s][site][dof])
+// tensor-core coarse stencil on nrhs right-hand sides ([rhs][s][site][dof]);
+// skip_rhs: per right-hand-side device flags (may be null)
 dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
-                                 const int* skip, cudaStream_t st);
+                                 const int* skip_rhs, cudaStream_t st);
 // one-time kernel attributes of the coarse stencil (outside any stream capture)
 dwf_status coarse_init_attributes();
-dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st);
-dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st);
+// Wall transfers (Eq. TruncProjectInterpolate) on nrhs vectors stored back to
+// back; skip: per right-hand-side device flags (may be null).
+dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st,
+                         int nrhs = 1);
+dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st,
+                        int nrhs = 1);
 
 // One cooperative launch running the whole coarsest CGNR; vec6 = six coarse
 // work vectors, partials = 3 * grid doubles, bar = 16 bytes of barrier state.
 // out_iters accumulates the iteration count over calls.
 dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* vec6, double* partials,
                                   void* bar, int* out_iters, double* out_rr2, cudaStream_t st);
+
+// releases the batched solver's workspace of a handle
+void batched_state_free(dwf_mg* h);
 
 inline long long fine_len(const dwf_mg* h) { return h->G.V * h->G.Ls * site_dof(h->G); }
 inline long long coarse_len(const dwf_mg* h) { return h->mg.Vc * h->mg.Ls_c * h->mg.ncd; }

@@ -487,12 +487,15 @@ __device__ __forceinline__ int chir_dof(const TransferParams& p, int c, int cd) 
     return (2 * c + cd / p.ncol) * p.ncol + cd % p.ncol;
 }
 
+// grid.y = right-hand side (vectors back to back); skip[r]: per right-hand side
 __global__ void k_restrict(const float2* __restrict__ P, const float2* __restrict__ r, float2* __restrict__ out,
                            TransferParams p, const int* skip) {
-    if (skip && *skip) return;
+    if (skip && skip[blockIdx.y]) return;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = p.Vc * p.Ls_c * p.ncd;
     if (t >= total) return;
+    r += (long long)blockIdx.y * p.V * p.Ls * p.dof;
+    out += (long long)blockIdx.y * total;
     const int i = (int)(t % p.ncd);
     const long long rest = t / p.ncd;
     const long long xc = rest % p.Vc;
@@ -515,10 +518,12 @@ __global__ void k_restrict(const float2* __restrict__ P, const float2* __restric
 
 __global__ void k_prolong(const float2* __restrict__ P, const float2* __restrict__ e, float2* __restrict__ out,
                           TransferParams p, const int* skip) {
-    if (skip && *skip) return;
+    if (skip && skip[blockIdx.y]) return;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = p.V * p.Ls * p.dof;
     if (t >= total) return;
+    e += (long long)blockIdx.y * p.Vc * p.Ls_c * p.ncd;
+    out += (long long)blockIdx.y * total;
     const int d = (int)(t % p.dof);
     const long long rest = t / p.dof;
     const long long x = rest % p.V;
@@ -556,18 +561,24 @@ static TransferParams transfer_params(const dwf_mg* h) {
     return p;
 }
 
-dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st) {
+dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st,
+                         int nrhs) {
     TransferParams p = transfer_params(h);
     const long long total = p.Vc * p.Ls_c * p.ncd;
-    k_restrict<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(h->P32, r_fine, r_coarse, p, skip);
+    if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
+    k_restrict<<<dim3((unsigned)((total + 255) / 256), (unsigned)nrhs), 256, 0, st>>>(h->P32, r_fine, r_coarse, p,
+                                                                                       skip);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }
 
-dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st) {
+dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st,
+                        int nrhs) {
     TransferParams p = transfer_params(h);
     const long long total = p.V * p.Ls * p.dof;
-    k_prolong<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(h->P32, e_coarse, e_fine, p, skip);
+    if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
+    k_prolong<<<dim3((unsigned)((total + 255) / 256), (unsigned)nrhs), 256, 0, st>>>(h->P32, e_coarse, e_fine, p,
+                                                                                      skip);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }

@@ -59,8 +59,8 @@ __device__ __forceinline__ long long nbr2d(const TcParams& p, long long xc, int 
 // same input values, so every input value is loaded and split once.
 template <int NT>
 __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__ Y, const float2* __restrict__ in,
-                                                      float2* __restrict__ out, TcParams p, const int* skip) {
-    if (skip && *skip) return;
+                                                      float2* __restrict__ out, TcParams p,
+                                                      const int* __restrict__ skip_rhs) {
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int ngroup = (p.ncols + 8 * NT - 1) / (8 * NT);
@@ -75,9 +75,13 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
         const int col = (cg * NT + k) * 8 + g;           // B column owned by this lane in tile k
-        okB[k] = col < p.ncols;
+        okB[k] = col < p.ncols && !(skip_rhs && skip_rhs[col / p.Ls_c]);
         baseB[k] = okB[k] ? (long long)(col / p.Ls_c) * rhs_stride + (long long)(col % p.Ls_c) * slice : 0;
     }
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) any |= okB[k];
+    if (!__any_sync(0xffffffffu, any)) return;        // every column of this warp is skipped
     float acc[NT][2][4];
 #pragma unroll
     for (int k = 0; k < NT; ++k)
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
                 const int col = (cg * NT + k) * 8 + 2 * t + w;
                 if (col >= p.ncols) continue;
                 const int r = col / p.Ls_c, s = col % p.Ls_c;
+                if (skip_rhs && skip_rhs[r]) continue;
                 const long long rb = (long long)r * rhs_stride;
                 const float hr = so * acc[k][0][2 * h + w], hi = so * acc[k][1][2 * h + w];
                 const float2 self = __ldg(in + rb + (long long)s * slice + xc * 16 + i);
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
 }  // namespace
 
 dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
-                                 const int* skip, cudaStream_t st) {
+                                 const int* skip_rhs, cudaStream_t st) {
     if (h->mg.nd != 2 || h->mg.ncd != 16) {
         set_error("the tensor-core coarse stencil supports 2-d lattices with 16 coarse dof");
         return DWF_ERR_UNSUPPORTED;
@@ -186,7 +191,7 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
     const long long warps = p.Vc * ((p.ncols + 8 * NT - 1) / (8 * NT));
     const long long blocks = (warps * 32 + 255) / 256;
     if (blocks > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
-    k_coarse_tc<NT><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip);
+    k_coarse_tc<NT><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip_rhs);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }

@@ -500,6 +500,7 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
     h->coarse_graph_first = nullptr;
     h->coarse_graph_cycle = nullptr;
     h->cap_stream = nullptr;
+    h->batched = nullptr;
     dwf_status s = coarse_init_attributes();
     if (s == DWF_OK) s = setup_impl(h, U, null_starts);
     if (s != DWF_OK) {
@@ -515,6 +516,7 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
 void mg_destroy(dwf_mg* h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
+    batched_state_free(h);
     for (void* p : h->allocs) cudaFree(p);
     for (void* p : h->fine_vecs) cudaFree(p);
     for (void* p : h->coarse_vecs) cudaFree(p);

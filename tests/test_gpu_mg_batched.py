@@ -1,0 +1,147 @@
+"""GPU tests of the batched K-cycle (mg_solve_batched, mg_solve_groups): every
+right-hand side reaches a true FP64 residual of 1e-10, recomputed by the oracle,
+and agrees with the oracle's CGNR solution."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dirac, solvers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dw():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2004_07732_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to("cuda").to(dtype)
+
+
+def _hierarchy(dw, dims, Ls, sigma, seed, M5=1.0, mf=0.01, mset=-0.19, extra=None):
+    rng = synth.rng_for(seed)
+    U = synth.u1_links(synth.u1_angles(rng, dims, sigma))
+    V = int(np.prod(dims))
+    starts = np.stack([synth.gaussian_complex(rng, (V * 2,)) for _ in range(8)])
+    g = dw.make_geom(dims, Ls)
+    prm = {"setup_mass": mset}
+    prm.update(extra or {})
+    h = dw.mg_setup(g, _dev(U), M5, mf, prm, _dev(starts))
+    return h, U, rng
+
+
+@pytest.mark.parametrize("dims,Ls,sigma,mset,nrhs", [((32, 32), 8, 0.5, -0.19, 3), ((16, 16), 8, 0.3, -0.08, 5),
+                                                     ((24, 16), 6, 0.5, -0.19, 1)])
+def test_batched_solve_reaches_tolerance(dw, dims, Ls, sigma, mset, nrhs):
+    M5, mf = 1.0, 0.01
+    h, U, rng = _hierarchy(dw, dims, Ls, sigma, 50 + nrhs, M5, mf, mset)
+    V = int(np.prod(dims))
+    B = np.stack([synth.gaussian_spinor(rng, dims, Ls).reshape(-1) for _ in range(nrhs)])
+    X = torch.empty(nrhs * V * Ls * 2, dtype=torch.complex128, device="cuda")
+    stats, status = dw.mg_solve_batched(h, _dev(B), X, nrhs, tol=1e-10)
+    assert status == 0
+    D = dirac.dwf_matrix(U, dims, Ls, M5, mf)
+    Xs = X.cpu().numpy().reshape(nrhs, -1)
+    for r in range(nrhs):
+        res = np.linalg.norm(B[r] - D @ Xs[r]) / np.linalg.norm(B[r])
+        assert res <= 1e-10 and abs(res - stats[r]["true_residual"]) < 1e-12, (r, res)
+        xo, it_o, _ = solvers.cgnr(D, B[r], tol=1e-11)
+        assert np.linalg.norm(Xs[r] - xo) / np.linalg.norm(xo) < 1e-6
+        assert 0 < stats[r]["iterations"] and stats[r]["fine_applies"] < 2 * it_o
+    # the same systems one at a time through mg_solve take the same number of outer iterations
+    for r in range(nrhs):
+        x1 = torch.empty(V * Ls * 2, dtype=torch.complex128, device="cuda")
+        s1, st1 = dw.mg_solve(h, _dev(B[r]), x1, tol=1e-10)
+        # (the one-vector solver's coarse stencil reads FP16 blocks, the batched one FP32 blocks)
+        assert st1 == 0 and abs(s1["iterations"] - stats[r]["iterations"]) <= max(2, 0.2 * s1["iterations"])
+    h.close()
+
+
+def test_batched_solve_zero_and_repeated_rhs(dw):
+    """A zero right-hand side gives x = 0 at once; two equal right-hand sides give equal solutions;
+    a smaller batch after a larger one reuses the workspace."""
+    dims, Ls, M5, mf = (16, 16), 8, 1.0, 0.01
+    h, U, rng = _hierarchy(dw, dims, Ls, 0.4, 61, M5, mf, -0.12)
+    n = 256 * Ls * 2
+    b = synth.gaussian_spinor(rng, dims, Ls).reshape(-1)
+    B = np.stack([b, np.zeros_like(b), b, 2.0 * b])
+    X = torch.empty(4 * n, dtype=torch.complex128, device="cuda")
+    stats, status = dw.mg_solve_batched(h, _dev(B), X, 4, tol=1e-10)
+    Xs = X.cpu().numpy().reshape(4, -1)
+    assert status == 0
+    assert np.all(Xs[1] == 0) and stats[1]["true_residual"] == 0 and stats[1]["iterations"] == 0
+    assert np.array_equal(Xs[0], Xs[2])                  # fixed-order reductions: bitwise equal
+    D = dirac.dwf_matrix(U, dims, Ls, M5, mf)
+    for r in (0, 2, 3):
+        assert np.linalg.norm(B[r] - D @ Xs[r]) / np.linalg.norm(B[r]) <= 1e-10
+    X2 = torch.empty(2 * n, dtype=torch.complex128, device="cuda")
+    stats2, status2 = dw.mg_solve_batched(h, _dev(B[[3, 0]]), X2, 2, tol=1e-10)
+    X2s = X2.cpu().numpy().reshape(2, -1)
+    assert status2 == 0
+    for r, src in ((0, 3), (1, 0)):
+        assert np.linalg.norm(B[src] - D @ X2s[r]) / np.linalg.norm(B[src]) <= 1e-10
+    h.close()
+
+
+def test_batched_noconv_and_bad_arguments(dw):
+    dims, Ls = (16, 16), 4
+    h, U, rng = _hierarchy(dw, dims, Ls, 0.5, 62)
+    n = 256 * Ls * 2
+    B = np.stack([synth.gaussian_spinor(rng, dims, Ls).reshape(-1) for _ in range(2)])
+    X = torch.empty(2 * n, dtype=torch.complex128, device="cuda")
+    stats, status = dw.mg_solve_batched(h, _dev(B), X, 2, tol=1e-10, maxiter=1, raise_noconv=False)
+    assert status == 3 and all(s["true_residual"] > 1e-10 and s["iterations"] == 1 for s in stats)
+    with pytest.raises(ValueError):
+        dw.mg_solve_batched(h, _dev(B), X[:n], 2)
+    with pytest.raises(dw.DwfError):
+        dw.mg_solve_batched(h, _dev(B[:0]), X[:0], 0)
+    h.close()
+
+
+def test_groups_of_mixed_lattices(dw):
+    """Two lattices of different sizes, 3 and 2 right-hand sides, solved concurrently."""
+    M5, mf = 1.0, 0.01
+    cases = [((32, 32), 8, 0.5, -0.19, 3, 71), ((16, 24), 6, 0.5, -0.19, 2, 72)]
+    hs, Us, Bs, Xs = [], [], [], []
+    for dims, Ls, sigma, mset, k, seed in cases:
+        h, U, rng = _hierarchy(dw, dims, Ls, sigma, seed, M5, mf, mset)
+        B = np.stack([synth.gaussian_spinor(rng, dims, Ls).reshape(-1) for _ in range(k)])
+        hs.append(h); Us.append(U); Bs.append(B)
+        Xs.append(torch.empty(B.size, dtype=torch.complex128, device="cuda"))
+    stats, status = dw.mg_solve_groups(hs, [_dev(B) for B in Bs], Xs, [c[4] for c in cases], tol=1e-10)
+    assert status == 0
+    for (dims, Ls, *_), U, B, X, st in zip(cases, Us, Bs, Xs, stats):
+        D = dirac.dwf_matrix(U, dims, Ls, M5, mf)
+        x = X.cpu().numpy().reshape(len(B), -1)
+        for r in range(len(B)):
+            res = np.linalg.norm(B[r] - D @ x[r]) / np.linalg.norm(B[r])
+            assert res <= 1e-10 and abs(res - st[r]["true_residual"]) < 1e-12
+    with pytest.raises(dw.DwfError):
+        dw.mg_solve_groups([hs[0], hs[0]], [_dev(Bs[0])] * 2, [Xs[0], Xs[0]], [3, 3])
+    for h in hs:
+        h.close()
+
+
+def test_batched_full_size_256(dw):
+    """Four sources on the 256x256 x Ls=16 workload (sigma 0.7, m 0.005) reach 1e-10 (checked by the oracle)."""
+    wl = synth.SCHWINGER_256
+    U, srcs = wl.draw(4)
+    rng = synth.rng_for(wl.seed + 7000)
+    starts = np.stack([synth.gaussian_complex(rng, (wl.V * 2,)) for _ in range(8)])
+    g = dw.make_geom(wl.dims, wl.Ls)
+    h = dw.mg_setup(g, _dev(U), wl.M5, wl.mf, {"setup_mass": -0.3}, _dev(starts))
+    B = np.stack([s.reshape(-1) for s in srcs])
+    X = torch.empty(B.size, dtype=torch.complex128, device="cuda")
+    stats, status = dw.mg_solve_batched(h, _dev(B), X, 4, tol=1e-10)
+    assert status == 0
+    D = dirac.dwf_matrix(U, wl.dims, wl.Ls, wl.M5, wl.mf)
+    x = X.cpu().numpy().reshape(4, -1)
+    for r in range(4):
+        assert np.linalg.norm(B[r] - D @ x[r]) / np.linalg.norm(B[r]) <= 1e-10
+    h.close()
