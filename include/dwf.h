@@ -283,8 +283,9 @@ DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, d
  * cores: in / out hold nrhs coarse vectors back to back ([rhs][s][site][dof],
  * complex64).  Per coarse site the stencil is a dense contraction over the
  * nrhs * Ls_c columns, evaluated with mma.sync TF32 products of FP32 data split
- * into high and low parts (FP32-level accuracy), FP32 accumulation.  2-d, 16
- * coarse dof. */
+ * into high and low parts (FP32-level accuracy), FP32 accumulation.  The
+ * blocks are the handle's coarse block storage (coarse_block_prec), as for
+ * mg_coarse_apply.  2-d, 16 coarse dof. */
 DWF_API dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
                                          int dagger, void* stream);
 

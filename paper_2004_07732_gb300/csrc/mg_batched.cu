@@ -33,12 +33,20 @@ constexpr int BMDOT_BLOCKS = 152;     // blocks per (right-hand side, basis vect
 constexpr int CROW = (RED_GROUPS + 1) * RED_CSTRIDE;   // unsigneds of completion counters per row
 constexpr int PROW = RED_MAX * RED_BLOCKS;             // doubles of partial sums per row
 
-struct BGcr {                          // Krylov scalars of one right-hand side
-    double coef[BK_MAX][2];
-    double nrm[BK_MAX];
-    double alpha[2];
-    double rr2;
+// Krylov scalars of one right-hand side.  The GCR iterations keep only the
+// orthogonalised images w_k = A p'_k and the residual up to date; the search
+// directions are p'_k = p_k - sum_{j<k} C[k][j] p'_j of the stored raw
+// directions p_k, so the solution update sum_k A[k] p'_k is assembled once per
+// cycle as sum_j y_j p_j with (I + C)^T y = A (back substitution): every step
+// then reads and writes the raw basis only once.
+struct BGcr {
+    double coef[BK_MAX][2];          // projection coefficients of the current pass
+    double nrm[BK_MAX];              // |w_k|^2
+    double alpha[2];                 // alpha of the current step
+    double rr2;                      // |r|^2 after the current step
     double pad;
+    double C[BK_MAX][BK_MAX][2];     // C[k][j], j < k: summed over the Gram-Schmidt passes of step k
+    double A[BK_MAX][2];             // alpha of step k
 };
 
 __device__ __forceinline__ RedScratch row_scratch(RedScratch base, int r) {
@@ -55,6 +63,11 @@ __device__ __forceinline__ void csub4(float4& x, const float4 a, const float2 c)
     x.z -= c.x * a.z - c.y * a.w; x.w -= c.x * a.w + c.y * a.z;
 }
 
+__device__ __forceinline__ void cadd4(float4& x, const float4 a, const float2 c) {
+    x.x += c.x * a.x - c.y * a.y; x.y += c.x * a.y + c.y * a.x;
+    x.z += c.x * a.z - c.y * a.w; x.w += c.x * a.w + c.y * a.z;
+}
+
 #define ROW_LOOP(i, n2) for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n2); i += (long long)gridDim.x * blockDim.x)
 
 // ---- element-wise kernels; n = complex values per right-hand side (even) ----
@@ -64,13 +77,6 @@ __global__ void k_bcopy(float2* __restrict__ out, const float2* __restrict__ in,
     const float4* a = reinterpret_cast<const float4*>(in + r * n);
     float4* o = reinterpret_cast<float4*>(out + r * n);
     ROW_LOOP(i, n >> 1) o[i] = a[i];
-}
-
-__global__ void k_bzero(float2* __restrict__ out, long long n, const int* skip) {
-    const int r = blockIdx.y;
-    if (skip && skip[r]) return;
-    float4* o = reinterpret_cast<float4*>(out + r * n);
-    ROW_LOOP(i, n >> 1) o[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void k_bsub32(float2* __restrict__ out, const float2* __restrict__ a, const float2* __restrict__ b,
@@ -104,16 +110,6 @@ __global__ void k_bd2f_scale(float2* __restrict__ out, const double2* __restrict
     ROW_LOOP(i, n) { const double2 u = a[i]; out[i] = make_float2((float)(u.x * s), (float)(u.y * s)); }
 }
 
-// x (FP64) += s[r] * e (FP32)
-__global__ void k_baxpy_64_32(double2* __restrict__ x, const float2* __restrict__ e, const double* s, long long n,
-                              const int* skip) {
-    const int r = blockIdx.y;
-    if (skip && skip[r]) return;
-    const double a = s[r];
-    x += r * n; e += r * n;
-    ROW_LOOP(i, n) { double2 v = x[i]; const float2 d = e[i]; v.x += a * d.x; v.y += a * d.y; x[i] = v; }
-}
-
 // out[r] = |x_r|^2.  FP64 data: every product in FP64; FP32 data: per-thread
 // FP32 partials over a few elements, FP64 across threads.
 __global__ void __launch_bounds__(RED_THREADS) k_bnorm2_64(const double2* __restrict__ x, long long n, RedScratch rs,
@@ -137,31 +133,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_bnorm2_32(const float2* __restr
     grid_reduce<1>(v, row_scratch(rs, r), [=] __device__(double* t) { out[r] = t[0]; });
 }
 
-// x += alpha z, r -= alpha w, rr2 = |r|^2 per right-hand side.  With `done`:
-// iters[r] += 1 and done[r] = 1 once rr2 <= tol2 * ref2[r] or iters[r] >= maxit.
-// `skip` and `done` may be the same array: every block of a row reads the flag
-// before the row's last block (the only writer) runs its finaliser.
-__global__ void __launch_bounds__(RED_THREADS) k_bgcr_update(float2* __restrict__ x, float2* __restrict__ res,
-                                                             const float2* __restrict__ z, const float2* __restrict__ w,
-                                                             BGcr* g, long long n, RedScratch rs, const int* skip,
-                                                             int* done, const double* ref2, double tol2, int* iters,
-                                                             int maxit) {
+// rout = rin - alpha w, rr2 = |rout|^2 per right-hand side (rout may be rin).
+// With `done`: iters[r] += 1 and done[r] = 1 once rr2 <= tol2 * ref2[r] or
+// iters[r] >= maxit.  `skip` and `done` may be the same array: every block of a
+// row reads the flag before the row's last block (the only writer) runs its
+// finaliser.
+__global__ void __launch_bounds__(RED_THREADS) k_bres_update(const float2* rin, float2* rout,
+                                                             const float2* __restrict__ w, BGcr* g, long long n,
+                                                             RedScratch rs, const int* skip, int* done,
+                                                             const double* ref2, double tol2, int* iters, int maxit) {
     const int r = blockIdx.y;
     if (skip && skip[r]) return;
     const float ar = (float)g[r].alpha[0], ai = (float)g[r].alpha[1];
-    float4* x4 = reinterpret_cast<float4*>(x + r * n);
-    float4* r4 = reinterpret_cast<float4*>(res + r * n);
-    const float4* z4 = reinterpret_cast<const float4*>(z + r * n);
+    const float4* a4 = reinterpret_cast<const float4*>(rin + r * n);
+    float4* o4 = reinterpret_cast<float4*>(rout + r * n);
     const float4* w4 = reinterpret_cast<const float4*>(w + r * n);
     float acc = 0.f;
     ROW_LOOP(i, n >> 1) {
-        const float4 zi = z4[i], wi = w4[i];
-        float4 xi = x4[i], ri = r4[i];
-        xi.x += ar * zi.x - ai * zi.y; xi.y += ar * zi.y + ai * zi.x;
-        xi.z += ar * zi.z - ai * zi.w; xi.w += ar * zi.w + ai * zi.z;
+        const float4 wi = w4[i];
+        float4 ri = a4[i];
         ri.x -= ar * wi.x - ai * wi.y; ri.y -= ar * wi.y + ai * wi.x;
         ri.z -= ar * wi.z - ai * wi.w; ri.w -= ar * wi.w + ai * wi.z;
-        x4[i] = xi; r4[i] = ri;
+        o4[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
     }
     double v[1] = {acc};
@@ -174,11 +167,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_bgcr_update(float2* __restrict_
     });
 }
 
-// Classical Gram-Schmidt dots: coef[j] = <W_j, w> / nrm[j] for j < k, per
-// right-hand side.  Grid (B, k, nrhs); W: device array of basis block pointers.
+// Classical Gram-Schmidt dots: coef[j] = <W_j, w> / nrm[j] for j < k (k =
+// gridDim.y), per right-hand side, also summed into C[k][j] (set on the first
+// pass).  Grid (B, k, nrhs); W: device array of basis block pointers.
 __global__ void __launch_bounds__(RED_THREADS) k_bmdot(float2* const* __restrict__ W, const float2* __restrict__ w,
                                                        long long n, double* __restrict__ part, unsigned* counters,
-                                                       BGcr* g, const int* skip) {
+                                                       BGcr* g, int first, const int* skip) {
     const int r = blockIdx.z, j = blockIdx.y;
     if (skip && skip[r]) return;
     const float4* Wj = reinterpret_cast<const float4*>(W[j] + r * n);
@@ -211,44 +205,42 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmdot(float2* const* __restrict
     block_sum<2>(w2);
     if (threadIdx.x == 0) {
         const double nn = g[r].nrm[j];
-        g[r].coef[j][0] = nn > 0 ? w2[0] / nn : 0.0;
-        g[r].coef[j][1] = nn > 0 ? w2[1] / nn : 0.0;
+        const double cr = nn > 0 ? w2[0] / nn : 0.0, ci = nn > 0 ? w2[1] / nn : 0.0;
+        const int k = gridDim.y;
+        g[r].coef[j][0] = cr;
+        g[r].coef[j][1] = ci;
+        g[r].C[k][j][0] = first ? cr : g[r].C[k][j][0] + cr;
+        g[r].C[k][j][1] = first ? ci : g[r].C[k][j][1] + ci;
     }
 }
 
-// w -= sum_j c_j W_j, z -= sum_j c_j Z_j per right-hand side.  FINAL: also
-// nrm[k] = |w|^2 and alpha = <w, res> / |w|^2.
+// w -= sum_{j<k} coef_j W_j per right-hand side.  FINAL: also nrm[k] = |w|^2,
+// alpha = A[k] = <w, res> / |w|^2, and steps[r] = k + 1 (steps may be null).
 template <bool FINAL>
-__global__ void __launch_bounds__(RED_THREADS) k_bmaxpy(float2* __restrict__ w, float2* __restrict__ z,
-                                                        float2* const* __restrict__ W, float2* const* __restrict__ Z,
-                                                        BGcr* g, int k, const float2* __restrict__ res, long long n,
-                                                        RedScratch rs, const int* skip) {
+__global__ void __launch_bounds__(RED_THREADS) k_bmaxpy(float2* __restrict__ w, float2* const* __restrict__ W, BGcr* g,
+                                                        int k, const float2* __restrict__ res, long long n,
+                                                        RedScratch rs, int* steps, const int* skip) {
     const int r = blockIdx.y;
     if (skip && skip[r]) return;
     __shared__ float2 c[BK_MAX];
     __shared__ const float4* Wp[BK_MAX];
-    __shared__ const float4* Zp[BK_MAX];
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         c[j] = make_float2((float)g[r].coef[j][0], (float)g[r].coef[j][1]);
         Wp[j] = reinterpret_cast<const float4*>(W[j] + r * n);
-        Zp[j] = reinterpret_cast<const float4*>(Z[j] + r * n);
     }
     __syncthreads();
     float4* w4 = reinterpret_cast<float4*>(w + r * n);
-    float4* z4 = reinterpret_cast<float4*>(z + r * n);
     const float4* r4 = reinterpret_cast<const float4*>(res + r * n);
     float f0 = 0.f, f1 = 0.f, f2 = 0.f;
     ROW_LOOP(i, n >> 1) {
-        float4 wi = w4[i], zi = k > 0 ? z4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 wi = w4[i];
         int j = 0;
         for (; j + 3 < k; j += 4) {
             const float4 a0 = Wp[j][i], a1 = Wp[j + 1][i], a2 = Wp[j + 2][i], a3 = Wp[j + 3][i];
-            const float4 b0 = Zp[j][i], b1 = Zp[j + 1][i], b2 = Zp[j + 2][i], b3 = Zp[j + 3][i];
             csub4(wi, a0, c[j]); csub4(wi, a1, c[j + 1]); csub4(wi, a2, c[j + 2]); csub4(wi, a3, c[j + 3]);
-            csub4(zi, b0, c[j]); csub4(zi, b1, c[j + 1]); csub4(zi, b2, c[j + 2]); csub4(zi, b3, c[j + 3]);
         }
-        for (; j < k; ++j) { csub4(wi, Wp[j][i], c[j]); csub4(zi, Zp[j][i], c[j]); }
-        if (k > 0) { w4[i] = wi; z4[i] = zi; }
+        for (; j < k; ++j) csub4(wi, Wp[j][i], c[j]);
+        if (k > 0) w4[i] = wi;
         if (FINAL) {
             f0 += wi.x * wi.x + wi.y * wi.y + wi.z * wi.z + wi.w * wi.w;
             cdot4(wi, r4[i], f1, f2);
@@ -257,10 +249,82 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmaxpy(float2* __restrict__ w, 
     if (FINAL) {
         double v[3] = {f0, f1, f2};
         grid_reduce<3>(v, row_scratch(rs, r), [=] __device__(double* t) {
+            const double ar = t[0] > 0 ? t[1] / t[0] : 0.0, ai = t[0] > 0 ? t[2] / t[0] : 0.0;
             g[r].nrm[k] = t[0];
-            g[r].alpha[0] = t[0] > 0 ? t[1] / t[0] : 0.0;
-            g[r].alpha[1] = t[0] > 0 ? t[2] / t[0] : 0.0;
+            g[r].alpha[0] = ar; g[r].alpha[1] = ai;
+            g[r].A[k][0] = ar; g[r].A[k][1] = ai;
+            if (steps) steps[r] = k + 1;
         });
+    }
+}
+
+// y of the deferred solution update for the first m steps: (I + C)^T y = A,
+// y_j = A_j - sum_{k>j} C[k][j] y_k (one thread, FP64)
+__device__ __forceinline__ void back_substitute(const BGcr& g, int m, float2* y) {
+    double yr[BK_MAX], yi[BK_MAX];
+    for (int j = m - 1; j >= 0; --j) {
+        double a = g.A[j][0], b = g.A[j][1];
+        for (int k = j + 1; k < m; ++k) {
+            const double cr = g.C[k][j][0], ci = g.C[k][j][1];
+            a -= cr * yr[k] - ci * yi[k];
+            b -= cr * yi[k] + ci * yr[k];
+        }
+        yr[j] = a; yi[j] = b;
+        y[j] = make_float2((float)a, (float)b);
+    }
+}
+
+// out += sum_{j<m} y_j P_j (FP32), m = nsteps[r] or m_fixed when nsteps is
+// null; rows with m == 0 are left alone.  With wout: also wout = ra - rb.
+__global__ void __launch_bounds__(RED_THREADS) k_bcombine32(float2* __restrict__ out, float2* const* __restrict__ P,
+                                                            const BGcr* g, const int* nsteps, int m_fixed, long long n,
+                                                            const float2* __restrict__ ra, const float2* __restrict__ rb,
+                                                            float2* __restrict__ wout, const int* skip) {
+    const int r = blockIdx.y;
+    if (skip && skip[r]) return;
+    const int m = nsteps ? nsteps[r] : m_fixed;
+    __shared__ float2 y[BK_MAX];
+    __shared__ const float4* Pp[BK_MAX];
+    if (threadIdx.x == 0 && m > 0) back_substitute(g[r], m, y);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) Pp[j] = reinterpret_cast<const float4*>(P[j] + r * n);
+    __syncthreads();
+    float4* o4 = reinterpret_cast<float4*>(out + r * n);
+    const float4* a4 = wout ? reinterpret_cast<const float4*>(ra + r * n) : nullptr;
+    const float4* b4 = wout ? reinterpret_cast<const float4*>(rb + r * n) : nullptr;
+    float4* w4 = wout ? reinterpret_cast<float4*>(wout + r * n) : nullptr;
+    ROW_LOOP(i, n >> 1) {
+        if (m > 0) {
+            float4 x = o4[i];
+            for (int j = 0; j < m; ++j) cadd4(x, Pp[j][i], y[j]);
+            o4[i] = x;
+        }
+        if (wout) {
+            const float4 u = a4[i], v = b4[i];
+            w4[i] = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
+        }
+    }
+}
+
+// X (FP64) += s[r] * sum_{j<m} y_j Z_j, m = nsteps[r]; rows with m == 0 are left alone
+__global__ void __launch_bounds__(RED_THREADS) k_bcombine64(double2* __restrict__ X, float2* const* __restrict__ Z,
+                                                            const BGcr* g, const int* nsteps, const double* s,
+                                                            long long n) {
+    const int r = blockIdx.y;
+    const int m = nsteps[r];
+    if (m <= 0) return;
+    __shared__ float2 y[BK_MAX];
+    __shared__ const float4* Zp[BK_MAX];
+    if (threadIdx.x == 0) back_substitute(g[r], m, y);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) Zp[j] = reinterpret_cast<const float4*>(Z[j] + r * n);
+    __syncthreads();
+    const double sc = s[r];
+    double2* x2 = X + r * n;
+    ROW_LOOP(i, n >> 1) {
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < m; ++j) cadd4(e, Zp[j][i], y[j]);
+        double2 a = x2[2 * i], b = x2[2 * i + 1];
+        a.x += sc * e.x; a.y += sc * e.y; b.x += sc * e.z; b.y += sc * e.w;
+        x2[2 * i] = a; x2[2 * i + 1] = b;
     }
 }
 
@@ -270,7 +334,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmaxpy(float2* __restrict__ w, 
 struct BView {
     int nrhs;
     long long nf, nc;
-    float2 *rA, *r, *e, *tmp, *rs_, *ps;
+    float2 *rA, *r, *tmp, *rs_, *ps;
     float2 *Z[BK_MAX], *W[BK_MAX], *Ps[BK_MAX], *Qs[BK_MAX];
     float2 *rc, *ec, *crr, *ct;
     float2 *Zc[BK_MAX], *Wc[BK_MAX];
@@ -281,7 +345,7 @@ struct BView {
     RedScratch red;           // reductions: [nrhs][PROW] partials, [nrhs][CROW] counters
     BGcr *outer, *smooth, *cgcr;
     double *bn2, *rn2, *rA2, *ref2, *cref2, *scale, *rn;
-    int *odone, *idone, *cdone, *iters, *citers;
+    int *odone, *idone, *cdone, *iters, *citers, *csteps;
 };
 
 struct Carver {
@@ -303,7 +367,7 @@ static void carve(const dwf_mg* h, int nrhs, char* base, BView& v, size_t* total
     v.nf = fine_len(h);
     v.nc = coarse_len(h);
     const size_t F = (size_t)nrhs * v.nf, C = (size_t)nrhs * v.nc;
-    v.rA = c.take<float2>(F); v.r = c.take<float2>(F); v.e = c.take<float2>(F);
+    v.rA = c.take<float2>(F); v.r = c.take<float2>(F);
     v.tmp = c.take<float2>(F); v.rs_ = c.take<float2>(F); v.ps = c.take<float2>(F);
     for (int k = 0; k < BK_MAX; ++k) {
         v.Z[k] = k < K ? c.take<float2>(F) : nullptr;
@@ -330,7 +394,7 @@ static void carve(const dwf_mg* h, int nrhs, char* base, BView& v, size_t* total
     v.mcount = c.take<unsigned>((size_t)nrhs * BK_MAX * CROW);
     v.red.counter = c.take<unsigned>((size_t)nrhs * CROW);
     v.odone = c.take<int>(nrhs); v.idone = c.take<int>(nrhs); v.cdone = c.take<int>(nrhs);
-    v.iters = c.take<int>(nrhs); v.citers = c.take<int>(nrhs);
+    v.iters = c.take<int>(nrhs); v.citers = c.take<int>(nrhs); v.csteps = c.take<int>(nrhs);
     *zero_end = c.off;
     *total = c.off;
 }
@@ -431,8 +495,10 @@ static dwf_status bapply_A(BSolver& s, const float2* in, float2* out, const int*
     return DWF_OK;
 }
 
-static dwf_status borthogonalise(BSolver& s, BGcr* g, float2* const* Zb, float2* const* Wb, int k, const float2* res,
-                                 long long n, float2* const* dZ, float2* const* dW, const int* skip) {
+// Orthogonalise Wb[k] against Wb[0..k-1] (classical Gram-Schmidt, cgs_passes
+// passes), then nrm[k], alpha = A[k] = <w, res> / |w|^2; steps[r] = k + 1.
+static dwf_status borthogonalise(BSolver& s, BGcr* g, float2* const* Wb, int k, const float2* res, long long n,
+                                 float2* const* dW, int* steps, const int* skip) {
     BView& v = *s.v;
     const int rg = red_grid4(n);
     const dim3 rgrid((unsigned)rg, (unsigned)s.nrhs);
@@ -441,20 +507,24 @@ static dwf_status borthogonalise(BSolver& s, BGcr* g, float2* const* Zb, float2*
         const dim3 egrid = row_grid(n >> 1, s.nrhs, 152 * 16);
         const int passes = s.h->prm.cgs_passes;
         for (int pass = 0; pass < passes; ++pass) {
-            k_bmdot<<<mgrid, RED_THREADS, 0, s.st>>>(dW, Wb[k], n, v.mpart, v.mcount, g, skip);
+            k_bmdot<<<mgrid, RED_THREADS, 0, s.st>>>(dW, Wb[k], n, v.mpart, v.mcount, g, pass == 0, skip);
             if (pass + 1 < passes)
-                k_bmaxpy<false><<<egrid, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], dW, dZ, g, k, res, n, v.red, skip);
+                k_bmaxpy<false><<<egrid, RED_THREADS, 0, s.st>>>(Wb[k], dW, g, k, res, n, v.red, steps, skip);
             else
-                k_bmaxpy<true><<<rgrid, RED_THREADS, 0, s.st>>>(Wb[k], Zb[k], dW, dZ, g, k, res, n, v.red, skip);
+                k_bmaxpy<true><<<rgrid, RED_THREADS, 0, s.st>>>(Wb[k], dW, g, k, res, n, v.red, steps, skip);
         }
     } else {
-        k_bmaxpy<true><<<rgrid, RED_THREADS, 0, s.st>>>(Wb[0], Zb[0], dW, dZ, g, 0, res, n, v.red, skip);
+        k_bmaxpy<true><<<rgrid, RED_THREADS, 0, s.st>>>(Wb[0], dW, g, 0, res, n, v.red, steps, skip);
     }
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }
 
-// coarse GCR on every right-hand side with idone == 0 (cdone starts as a copy of idone)
+// Coarse GCR on every right-hand side with idone == 0 (cdone starts as a copy
+// of idone).  The residual at the start of a restart cycle is crr; step k
+// keeps its residual in Zc[k] (the raw direction of step k) and writes the
+// next one to Zc[k + 1], or to crr after the last step; the cycle ends with
+// ec += sum_j y_j Zc[j] over the csteps[r] steps that right-hand side took.
 static dwf_status bcoarse_prologue(BSolver& s) {
     BView& v = *s.v;
     const long long n = v.nc;
@@ -476,16 +546,21 @@ static dwf_status bcoarse_cycle(BSolver& s) {
     const double tol2 = h->prm.coarse_tol * h->prm.coarse_tol;
     const dim3 eg = row_grid(n >> 1, s.nrhs);
     const dim3 rg((unsigned)red_grid4(n), (unsigned)s.nrhs);
+    DWF_CHECK_CUDA(cudaMemsetAsync(v.csteps, 0, s.nrhs * sizeof(int), s.st));
+    k_bcopy<<<eg, 256, 0, s.st>>>(v.Zc[0], v.crr, n, v.cdone);
+    DWF_CHECK_LAUNCH();
     for (int k = 0; k < KC; ++k) {
-        k_bcopy<<<eg, 256, 0, s.st>>>(v.Zc[k], v.crr, n, v.cdone);
-        DWF_CHECK_LAUNCH();
         DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.Zc[k], v.ct, h->mf, false, v.cdone, s.st));
         DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.ct, v.Wc[k], 1.0, true, v.cdone, s.st));
-        DWF_TRY(borthogonalise(s, v.cgcr, v.Zc, v.Wc, k, v.crr, n, v.dptr + 4 * BK_MAX, v.dptr + 5 * BK_MAX, v.cdone));
-        k_bgcr_update<<<rg, RED_THREADS, 0, s.st>>>(v.ec, v.crr, v.Zc[k], v.Wc[k], v.cgcr, n, v.red, v.cdone, v.cdone,
-                                                    v.cref2, tol2, v.citers, h->prm.coarse_maxiter);
+        DWF_TRY(borthogonalise(s, v.cgcr, v.Wc, k, v.Zc[k], n, v.dptr + 5 * BK_MAX, v.csteps, v.cdone));
+        k_bres_update<<<rg, RED_THREADS, 0, s.st>>>(v.Zc[k], k + 1 < KC ? v.Zc[k + 1] : v.crr, v.Wc[k], v.cgcr, n,
+                                                    v.red, v.cdone, v.cdone, v.cref2, tol2, v.citers,
+                                                    h->prm.coarse_maxiter);
         DWF_CHECK_LAUNCH();
     }
+    k_bcombine32<<<eg, RED_THREADS, 0, s.st>>>(v.ec, v.dptr + 4 * BK_MAX, v.cgcr, v.csteps, 0, n, nullptr, nullptr,
+                                               nullptr, nullptr);
+    DWF_CHECK_LAUNCH();
     return DWF_OK;
 }
 
@@ -535,7 +610,10 @@ static dwf_status bcoarse_solve(BSolver& s, int* citers_out) {
     return DWF_OK;
 }
 
-// z = M(r) and w = A z for every right-hand side with idone == 0
+// z = M(r) and w = A z for every right-hand side with idone == 0.  The
+// smoother's step j keeps its residual in Ps[j] and writes the next one to
+// Ps[j + 1] (rs_ after the last step); z += sum_j y_j Ps[j] and w = r - rs_
+// come out of one final pass.
 static dwf_status bprecondition(BSolver& s, const float2* res, float2* zout, float2* wout, int* citers_out) {
     dwf_mg* h = s.h;
     BView& v = *s.v;
@@ -547,20 +625,18 @@ static dwf_status bprecondition(BSolver& s, const float2* res, float2* zout, flo
     const int S = h->prm.post_smooth;
     if (S == 0) return bapply_A(s, zout, wout, v.idone);
     DWF_TRY(bapply_A(s, zout, v.ps, v.idone));
-    k_bsub32<<<eg, 256, 0, s.st>>>(v.rs_, res, v.ps, n, v.idone);
+    k_bsub32<<<eg, 256, 0, s.st>>>(v.Ps[0], res, v.ps, n, v.idone);
     DWF_CHECK_LAUNCH();
     const dim3 rg((unsigned)red_grid4(n), (unsigned)s.nrhs);
     for (int j = 0; j < S; ++j) {
-        k_bcopy<<<eg, 256, 0, s.st>>>(v.Ps[j], v.rs_, n, v.idone);
-        DWF_CHECK_LAUNCH();
         DWF_TRY(bapply_A(s, v.Ps[j], v.Qs[j], v.idone));
-        DWF_TRY(borthogonalise(s, v.smooth, v.Ps, v.Qs, j, v.rs_, n, v.dptr + 2 * BK_MAX, v.dptr + 3 * BK_MAX,
-                               v.idone));
-        k_bgcr_update<<<rg, RED_THREADS, 0, s.st>>>(zout, v.rs_, v.Ps[j], v.Qs[j], v.smooth, n, v.red, v.idone,
-                                                    nullptr, nullptr, 0.0, nullptr, 0);
+        DWF_TRY(borthogonalise(s, v.smooth, v.Qs, j, v.Ps[j], n, v.dptr + 3 * BK_MAX, nullptr, v.idone));
+        k_bres_update<<<rg, RED_THREADS, 0, s.st>>>(v.Ps[j], j + 1 < S ? v.Ps[j + 1] : v.rs_, v.Qs[j], v.smooth, n,
+                                                    v.red, v.idone, nullptr, nullptr, 0.0, nullptr, 0);
         DWF_CHECK_LAUNCH();
     }
-    k_bsub32<<<eg, 256, 0, s.st>>>(wout, res, v.rs_, n, v.idone);
+    k_bcombine32<<<eg, RED_THREADS, 0, s.st>>>(zout, v.dptr + 2 * BK_MAX, v.smooth, nullptr, S, n, res, v.rs_, wout,
+                                               v.idone);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }
@@ -669,7 +745,6 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
         DWF_CHECK_LAUNCH();
         DWF_TRY(fine_apply_2d_multi(h->G, h->Ulo, v.ps, v.rA, h->M5, 1.0, true, h->prm.fine_prec, nrhs, v.idone, s.st));
         k_bcopy<<<eg32, 256, 0, s.st>>>(v.r, v.rA, n, v.idone);
-        k_bzero<<<eg32, 256, 0, s.st>>>(v.e, n, v.idone);
         k_bnorm2_32<<<rg32, RED_THREADS, 0, s.st>>>(v.rA, n, v.red, v.rA2, v.idone);
         DWF_CHECK_LAUNCH();
         DWF_CHECK_CUDA(cudaMemcpyAsync(hrA2, v.rA2, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s.st));
@@ -691,8 +766,8 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
             DWF_TRY(bprecondition(s, v.r, v.Z[k], v.W[k], hci));
             for (int r = 0; r < nrhs; ++r)
                 if (!hid[r]) { coarse_it[r] += hci[r]; coarse_solves[r] += 1; fine[r] += 2 + 2 * S; outer[r] += 1; }
-            DWF_TRY(borthogonalise(s, v.outer, v.Z, v.W, k, v.r, n, v.dptr + 0 * BK_MAX, v.dptr + 1 * BK_MAX, v.idone));
-            k_bgcr_update<<<rg, RED_THREADS, 0, s.st>>>(v.e, v.r, v.Z[k], v.W[k], v.outer, n, v.red, v.idone, v.idone,
+            DWF_TRY(borthogonalise(s, v.outer, v.W, k, v.r, n, v.dptr + 1 * BK_MAX, nullptr, v.idone));
+            k_bres_update<<<rg, RED_THREADS, 0, s.st>>>(v.r, v.r, v.W[k], v.outer, n, v.red, v.idone, v.idone,
                                                         v.ref2, 1.0, v.iters, K);
             DWF_CHECK_LAUNCH();
             DWF_CHECK_CUDA(cudaMemcpyAsync(hid, v.idone, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s.st));
@@ -701,7 +776,9 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
                 if (!hod[r] && outer[r] >= maxiter) hid[r] = 1;    // iteration cap: leave the cycle
             DWF_CHECK_CUDA(cudaMemcpyAsync(v.idone, hid, nrhs * sizeof(int), cudaMemcpyHostToDevice, s.st));
         }
-        k_baxpy_64_32<<<eg64, 256, 0, s.st>>>(X, v.e, v.rn, n, v.odone);
+        // x += |r| sum_k y_k Z_k over the iters[r] steps of this cycle
+        k_bcombine64<<<row_grid(n >> 1, nrhs), RED_THREADS, 0, s.st>>>(X, v.dptr + 0 * BK_MAX, v.outer, v.iters, v.rn,
+                                                                        n);
         DWF_CHECK_LAUNCH();
     }
     (void)hit;

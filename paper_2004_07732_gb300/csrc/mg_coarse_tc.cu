@@ -57,10 +57,17 @@ __device__ __forceinline__ long long nbr2d(const TcParams& p, long long xc, int 
 // The k dimension is walked in two halves (input components j = t + {0, 4} and
 // j = 8 + t + {0, 4}); each half covers the real and the imaginary k-tile of the
 // same input values, so every input value is loaded and split once.
-template <int NT>
-__global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__ Y, const float2* __restrict__ in,
+__device__ __forceinline__ float2 block_val(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 block_val(const __half2* p) { return __half22float2(__ldg(p)); }
+
+// BT = float2: FP32 blocks, split into TF32 high and low parts (three products
+// per term).  BT = __half2: FP16 blocks, exact in TF32 (same 11-bit
+// significand), so only the vectors are split (two products per term).
+template <int NT, class BT>
+__global__ void __launch_bounds__(256, 2) k_coarse_tc(const BT* __restrict__ Y, const float2* __restrict__ in,
                                                       float2* __restrict__ out, TcParams p,
                                                       const int* __restrict__ skip_rhs) {
+    constexpr bool SPLIT_A = sizeof(BT) == sizeof(float2);
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int ngroup = (p.ncols + 8 * NT - 1) / (8 * NT);
@@ -93,7 +100,7 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
 #pragma unroll 1
     for (int dir = 0; dir < 5; ++dir) {
         const long long nb = nbr2d(p, xc, dir);
-        const float2* Yb = Y + (xc * 5 + dir) * 256;
+        const BT* Yb = Y + (xc * 5 + dir) * 256;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             // block entries Y[i][j], i = g + 8h, j = 8 half + t + 4 w (column-major: j * 16 + i)
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int w = 0; w < 2; ++w) y[h][w] = __ldg(Yb + (8 * half + t + 4 * w) * 16 + g + 8 * h);
+                for (int w = 0; w < 2; ++w) y[h][w] = block_val(Yb + (8 * half + t + 4 * w) * 16 + g + 8 * h);
             // A fragments of [[Yr, -Yi], [Yi, Yr]] for m-tile mt (real / imaginary output rows) and the
             // real (ri = 0) or imaginary (ri = 1) input k-tile: a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
             uint32_t ah[2][2][4], al[2][2][4];
@@ -113,7 +120,8 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
                     for (int u = 0; u < 4; ++u) {
                         const float2 yy = y[u & 1][u >> 1];
                         const float e = mt == 0 ? (ri == 0 ? yy.x : -yy.y) : (ri == 0 ? yy.y : yy.x);
-                        split_tf32(e, ah[mt][ri][u], al[mt][ri][u]);
+                        if (SPLIT_A) split_tf32(e, ah[mt][ri][u], al[mt][ri][u]);
+                        else { ah[mt][ri][u] = __float_as_uint(e); al[mt][ri][u] = 0u; }
                     }
 #pragma unroll
             for (int k = 0; k < NT; ++k) {
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const float2* __restrict__
                     for (int ri = 0; ri < 2; ++ri) {
                         mma_tf32(acc[k][mt], ah[mt][ri], bh[ri]);
                         mma_tf32(acc[k][mt], ah[mt][ri], bl[ri]);
-                        mma_tf32(acc[k][mt], al[mt][ri], bh[ri]);
+                        if (SPLIT_A) mma_tf32(acc[k][mt], al[mt][ri], bh[ri]);
                     }
             }
         }
@@ -191,7 +199,10 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
     const long long warps = p.Vc * ((p.ncols + 8 * NT - 1) / (8 * NT));
     const long long blocks = (warps * 32 + 255) / 256;
     if (blocks > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
-    k_coarse_tc<NT><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip_rhs);
+    if (h->ytile_half)
+        k_coarse_tc<NT, __half2><<<(unsigned)blocks, 256, 0, st>>>((const __half2*)h->Ytile, in, out, p, skip_rhs);
+    else
+        k_coarse_tc<NT, float2><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip_rhs);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }

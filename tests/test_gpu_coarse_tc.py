@@ -88,3 +88,26 @@ def test_coarse_multi_rejects_bad_arguments(dw):
     with pytest.raises(dw.DwfError):
         dw.mg_coarse_apply_multi(h, vd, vd, 2, 0.1)
     h.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 6, 16])
+def test_coarse_multi_f16_blocks_match_single(dw, nrhs):
+    """FP16 coarse blocks (the default storage): each column of the tensor-core result agrees with
+    the one-vector stencil reading the same FP16 blocks, to FP32 accuracy."""
+    rng0 = synth.rng_for(90 + nrhs)
+    dims = (64, 32)
+    U = synth.u1_links(synth.u1_angles(rng0, dims, 0.6))
+    starts = np.stack([synth.gaussian_complex(rng0, (int(np.prod(dims)) * 2,)) for _ in range(8)])
+    g = dw.make_geom(dims, 8)
+    h = dw.mg_setup(g, _dev(U), 1.0, 0.01, {"setup_maxiter": 10, "setup_mass": -0.19, "Ls_c": 4}, _dev(starts))
+    nc = h.coarse_size
+    v = synth.gaussian_complex(np.random.default_rng(nrhs), (nrhs, nc)).astype(np.complex64)
+    vd = _dev(v, torch.complex64).reshape(nrhs, nc)
+    out = torch.empty_like(vd)
+    one = torch.empty(nc, dtype=torch.complex64, device="cuda")
+    for m, dag in ((0.01, False), (1.0, True), (0.01, True)):
+        dw.mg_coarse_apply_multi(h, vd, out, nrhs, m, dagger=dag)
+        for r in range(nrhs):
+            dw.mg_coarse_apply(h, vd[r].contiguous(), one, m, dagger=dag)
+            assert (torch.linalg.norm(out[r] - one) / torch.linalg.norm(one)).item() < 1e-5
+    h.close()
