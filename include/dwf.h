@@ -208,7 +208,10 @@ typedef struct {
     int fine_prec;        /* storage of the fine links in the inner solve (DWF_F32_L16)        */
     double inner_tol;     /* floor of the residual reduction of one reliable-update cycle      */
     int max_restarts;     /* reliable-update cycles before giving up                          */
-    int coarse_persistent;/* 1: the coarsest CGNR runs as one cooperative persistent launch    */
+    int coarse_persistent;/* 1: the coarsest CGNR runs as one cooperative persistent launch;
+                             2: the coarse GCR too (one launch per coarse solve; measured
+                             slower than the graph-launched GCR at 64^2 x 4, so not the
+                             default); 0: launched kernels throughout (default 1)         */
     int coarse_solver;    /* 0: CGNR on the coarse normal operator (Table kcycle, coarsest
                              level); 1: restarted GCR on Dhat_PV^dag Dhat_DW (the paper's
                              level-2 solver; valid by the right-half-plane property, App. B) */

@@ -98,6 +98,15 @@ dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec,
 // releases the batched solver's workspace of a handle
 void batched_state_free(dwf_mg* h);
 
+// One cooperative launch running a whole coarse GCR solve (restart
+// coarse_restart): S = coarse_restart + 1 residual slots, W = coarse_restart
+// vectors, t = one vector, partials = (2 + 2 * 16 + 3) * grid doubles, bar = 16
+// bytes of barrier state.  out_iters accumulates the steps over calls.
+bool coarse_gcr_persistent_ok(const dwf_mg* h);
+dwf_status coarse_gcr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* S, float2* const* W,
+                                 float2* t, double* partials, void* bar, int* out_iters, double* out_rr2,
+                                 cudaStream_t st);
+
 inline long long fine_len(const dwf_mg* h) { return h->G.V * h->G.Ls * site_dof(h->G); }
 inline long long coarse_len(const dwf_mg* h) { return h->mg.Vc * h->mg.Ls_c * h->mg.ncd; }
 

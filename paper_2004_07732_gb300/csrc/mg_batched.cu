@@ -346,6 +346,10 @@ struct BView {
     BGcr *outer, *smooth, *cgcr;
     double *bn2, *rn2, *rA2, *ref2, *cref2, *scale, *rn;
     int *odone, *idone, *cdone, *iters, *citers, *csteps;
+    double* pg_part;          // persistent coarse GCR (one right-hand side): partial sums
+    unsigned* pg_bar;         // its grid barrier state (count, gen, error, pad)
+    int* pg_iters;            // its step counter
+    double* pg_rr2;
 };
 
 struct Carver {
@@ -388,6 +392,8 @@ static void carve(const dwf_mg* h, int nrhs, char* base, BView& v, size_t* total
     v.bn2 = c.take<double>(nrhs); v.rn2 = c.take<double>(nrhs); v.rA2 = c.take<double>(nrhs);
     v.ref2 = c.take<double>(nrhs); v.cref2 = c.take<double>(nrhs); v.scale = c.take<double>(nrhs);
     v.rn = c.take<double>(nrhs);
+    v.pg_part = c.take<double>(64 * 1024);
+    v.pg_rr2 = c.take<double>(1);
     // from here on the arena is zeroed once at allocation (counters must start at 0)
     c.off = (c.off + 255) & ~(size_t)255;
     *zero_begin = c.off;
@@ -395,6 +401,8 @@ static void carve(const dwf_mg* h, int nrhs, char* base, BView& v, size_t* total
     v.red.counter = c.take<unsigned>((size_t)nrhs * CROW);
     v.odone = c.take<int>(nrhs); v.idone = c.take<int>(nrhs); v.cdone = c.take<int>(nrhs);
     v.iters = c.take<int>(nrhs); v.citers = c.take<int>(nrhs); v.csteps = c.take<int>(nrhs);
+    v.pg_bar = c.take<unsigned>(4);
+    v.pg_iters = c.take<int>(1);
     *zero_end = c.off;
     *total = c.off;
 }
@@ -403,7 +411,7 @@ struct BatchedState {
     void* arena = nullptr;
     int cap = 0;
     BView v{};
-    int* hflags = nullptr;            // pinned: odone, idone, cdone, iters, citers [5][cap]
+    int* hflags = nullptr;            // pinned: odone, idone, cdone, iters, citers [5][cap], + 2 spare
     double* hvals = nullptr;          // pinned: bn2, rn2, rA2, ref2, scale, rn [6][cap]
     cudaGraphExec_t gfirst = nullptr, gcycle = nullptr;
     int gnrhs = 0;                    // right-hand sides the graphs were captured for
@@ -444,7 +452,7 @@ static dwf_status ensure_batched(dwf_mg* h, int nrhs) {
         }
         carve(h, nrhs, (char*)n->arena, n->v, &total, &z0, &z1);
         if (cudaMemset((char*)n->arena + z0, 0, z1 - z0) != cudaSuccess ||
-            cudaMallocHost((void**)&n->hflags, 5 * sizeof(int) * nrhs) != cudaSuccess ||
+            cudaMallocHost((void**)&n->hflags, (5 * nrhs + 2) * sizeof(int)) != cudaSuccess ||
             cudaMallocHost((void**)&n->hvals, 6 * sizeof(double) * nrhs) != cudaSuccess) {
             delete n;
             set_error("batched solver workspace setup failed");
@@ -550,8 +558,14 @@ static dwf_status bcoarse_cycle(BSolver& s) {
     k_bcopy<<<eg, 256, 0, s.st>>>(v.Zc[0], v.crr, n, v.cdone);
     DWF_CHECK_LAUNCH();
     for (int k = 0; k < KC; ++k) {
-        DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.Zc[k], v.ct, h->mf, false, v.cdone, s.st));
-        DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.ct, v.Wc[k], 1.0, true, v.cdone, s.st));
+        if (s.nrhs == 1) {
+            // one column: the shared-memory tile stencil has the shorter latency
+            DWF_TRY(coarse_dwf_apply(h, v.Zc[k], v.ct, h->mf, false, v.cdone, s.st));
+            DWF_TRY(coarse_dwf_apply(h, v.ct, v.Wc[k], 1.0, true, v.cdone, s.st));
+        } else {
+            DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.Zc[k], v.ct, h->mf, false, v.cdone, s.st));
+            DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.ct, v.Wc[k], 1.0, true, v.cdone, s.st));
+        }
         DWF_TRY(borthogonalise(s, v.cgcr, v.Wc, k, v.Zc[k], n, v.dptr + 5 * BK_MAX, v.csteps, v.cdone));
         k_bres_update<<<rg, RED_THREADS, 0, s.st>>>(v.Zc[k], k + 1 < KC ? v.Zc[k + 1] : v.crr, v.Wc[k], v.cgcr, n,
                                                     v.red, v.cdone, v.cdone, v.cref2, tol2, v.citers,
@@ -589,6 +603,22 @@ static dwf_status bcoarse_solve(BSolver& s, int* citers_out) {
     dwf_mg* h = s.h;
     BatchedState* bs = s.bs;
     BView& v = *s.v;
+    if (s.nrhs == 1 && h->prm.coarse_persistent == 2 && coarse_gcr_persistent_ok(h)) {
+        // one right-hand side: the whole coarse GCR in one cooperative launch
+        const int KC = h->prm.coarse_restart;
+        float2* S[BK_MAX + 1];
+        for (int k = 0; k < KC; ++k) S[k] = v.Zc[k];
+        S[KC] = v.crr;
+        DWF_CHECK_CUDA(cudaMemsetAsync(v.pg_iters, 0, sizeof(int), s.st));
+        DWF_TRY(coarse_gcr_persistent(h, v.rc, v.ec, S, v.Wc, v.ct, v.pg_part, v.pg_bar, v.pg_iters, v.pg_rr2,
+                                      s.st));
+        unsigned* hb = reinterpret_cast<unsigned*>(bs->hflags + 5 * bs->cap);   // spare slot
+        DWF_CHECK_CUDA(cudaMemcpyAsync(citers_out, v.pg_iters, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaMemcpyAsync(hb, v.pg_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
+        if (*hb != 0u) { set_error("persistent coarse GCR: a grid barrier or bulk copy timed out"); return DWF_ERR_TIMEOUT; }
+        return DWF_OK;
+    }
     if (!bs->gfirst) {
         DWF_TRY(bcapture(s, true, &bs->gfirst));
         DWF_TRY(bcapture(s, false, &bs->gcycle));
@@ -782,6 +812,15 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
         DWF_CHECK_LAUNCH();
     }
     (void)hit;
+    {
+        int st1 = 0;    // bounded bulk-copy waits of the tile stencil (one-column coarse solves)
+        DWF_CHECK_CUDA(cudaMemcpyAsync(&st1, h->status + 1, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+        DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
+        if (st1 != 0) {
+            set_error("coarse stencil: a bulk copy wait timed out");
+            return DWF_ERR_TIMEOUT;
+        }
+    }
     int nconv = 0;
     for (int r = 0; r < nrhs; ++r) nconv += conv[r];
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -273,9 +273,14 @@ __device__ __forceinline__ void tile_issue_blocks(TileSmemT<BT>& sm, const BT* _
 // preserving prolongator gives Dhat_W^dag = sigma_3 Dhat_W sigma_3 (P^dag gamma_5
 // D_W gamma_5 P), so the same blocks serve with sign flips on the chirality -
 // components of input and output (2 nvec = 16: components 8..15).
-template <class BT>
+// optional epilogue of tile_site: called with (index, value) of every output written
+struct NoEpilogue {
+    __device__ __forceinline__ void operator()(long long, float2) const {}
+};
+
+template <class BT, class Epi = NoEpilogue>
 __device__ __forceinline__ double tile_site(const TileSmemT<BT>& sm, float2* __restrict__ out, const CoarseParams& p,
-                                            int x0, int y0, float mf, bool dag) {
+                                            int x0, int y0, float mf, bool dag, Epi epi = Epi()) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = warp % TILE_X, ty = warp / TILE_X;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -336,6 +341,7 @@ __device__ __forceinline__ double tile_site(const TileSmemT<BT>& sm, float2* __r
         acc.x = hop.x + self.x + sc * hv.x;
         acc.y = hop.y + self.y + sc * hv.y;
         out[s * slice + xc * 16 + i] = acc;
+        epi(s * slice + xc * 16 + i, acc);
         nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
     }
     return nrm;
@@ -892,6 +898,474 @@ dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec,
     DWF_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_cgnr_persistent, dim3(grid), dim3(PCG_THREADS), args,
                                                sizeof(TileSmemT<float2>), st));
     return DWF_OK;
+}
+
+
+// ===========================================================================
+// Persistent coarse GCR: one cooperative launch per coarse solve.
+//
+// Restarted GCR(KC) on B e = r_c, B = Dhat_PV^dag Dhat_DW (the level-2 solver
+// type), to |r| <= coarse_tol |r_c| or maxiter steps.  Per step three bounded
+// grid barriers separate the phases:
+//   A. r_k = r_{k-1} - alpha_{k-1} w_{k-1} is formed while the tiles and their
+//      halos are staged (each tile stores its own sites of r_k), and
+//      t = Dhat_DW r_k is applied; partial |r_k|^2.          -> barrier
+//      Stop if |r_k|^2 <= tol^2 |r_c|^2.
+//   B. w = Dhat_PV^dag t, with the classical Gram-Schmidt dots <w_j, w>,
+//      j < k, accumulated in the stencil's epilogue.         -> barrier
+//   C. w_k = w - sum_j c_j w_j; partial |w_k|^2, <w_k, r_k>. -> barrier
+//      alpha_k = <w_k, r_k> / |w_k|^2.
+// The solution is not updated per step: the residuals r_j of a cycle are the
+// raw search directions, and e += sum_j y_j r_j with (I + C)^T y = alpha is
+// added once per cycle (during phase A of the next cycle's first step, or at
+// the end).  The residual slots rotate over KC + 1 vectors so that the new
+// cycle's first residual never overwrites a direction still being combined.
+// Every block computes the same scalars from the same partials in the same
+// order; barrier waits and bulk-copy waits are bounded (%globaltimer) and end
+// in an error flag that the host reports as DWF_ERR_TIMEOUT.
+// ===========================================================================
+constexpr int PG_MAXK = 16;
+constexpr int PGCR_BLOCKS_PER_SM = 2;     // resident blocks per SM used by the persistent GCR
+constexpr int PG_NQ = 1 + 2 * PG_MAXK + 3;     // partial quantities: |r|^2 | dots | |w|^2, <w, r>
+
+struct PgcrArgs {
+    CoarseParams cp;
+    const void* Y;          // Galerkin blocks (column-major, FP32 or FP16)
+    const float2* rc;
+    float2* e;
+    float2* S[PG_MAXK + 1]; // residual slots
+    float2* W[PG_MAXK];     // orthogonalised images
+    float2* t;
+    double* partials;       // [PG_NQ][gridDim.x]
+    PcgBarrier* bar;
+    int* out_iters;         // running total of steps over solves
+    double* out_rr2;        // final |r|^2 / |r_c|^2
+    double tol2;
+    int maxiter;
+    int KC;
+    unsigned long long timeout_ns;
+};
+
+struct PgcrShared {
+    double C[PG_MAXK][PG_MAXK][2];
+    double A[PG_MAXK][2];
+    double nrm[PG_MAXK];
+    float2 coef[PG_MAXK];
+    float2 y[PG_MAXK];
+    double tot[PG_NQ];
+};
+
+// totals of nq partial quantities (layout [q][gridDim.x], gridDim.x <= 2 *
+// blockDim.x) into out[q0 + q]: thread t adds partials t and t + blockDim.x of
+// every quantity (all loads issued together), then a fixed-order block tree, so
+// every block obtains bitwise identical totals after one round trip to L2
+constexpr int PG_TOT_MAX = 36;
+constexpr int PG_TOT_CHUNK = 8;      // quantities whose loads are in flight together
+__device__ void pg_totals(const double* part, int q0, int nq, double* out) {
+    __shared__ double sh[PG_TOT_CHUNK][TILE_THREADS / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned b0 = threadIdx.x, b1 = threadIdx.x + blockDim.x;
+    for (int c0 = 0; c0 < nq; c0 += PG_TOT_CHUNK) {
+        double v[PG_TOT_CHUNK];
+#pragma unroll
+        for (int q = 0; q < PG_TOT_CHUNK; ++q) {
+            v[q] = 0.0;
+            if (c0 + q < nq) {
+                const double* pq = part + (size_t)(q0 + c0 + q) * gridDim.x;
+                const double x0 = b0 < gridDim.x ? __ldcg(pq + b0) : 0.0;
+                const double x1 = b1 < gridDim.x ? __ldcg(pq + b1) : 0.0;
+                v[q] = x0 + x1;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PG_TOT_CHUNK; ++q) {
+            if (c0 + q < nq) {
+                double d = v[q];
+                for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+                if (lane == 0) sh[q][warp] = d;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < PG_TOT_CHUNK && c0 + (int)threadIdx.x < nq) {
+            double sum = 0.0;
+            for (int w = 0; w < TILE_THREADS / 32; ++w) sum += sh[threadIdx.x][w];
+            out[q0 + c0 + threadIdx.x] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// block partials of NQ per-thread FP32 values (first nq used) into part[(q0 + q) * grid + block]
+template <int NQ>
+__device__ void pg_partials(const float (&v)[NQ], int nq, double* part, int q0) {
+    __shared__ double sh[NQ][TILE_THREADS / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (q < nq) {
+            double d = v[q];
+            for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+            if (lane == 0) sh[q][warp] = d;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) sum += sh[q][w];
+        part[(size_t)(q0 + q) * gridDim.x + blockIdx.x] = sum;
+    }
+    __syncthreads();
+}
+
+// stage r = a - alpha b (b may be null) for the tile and its halo; the tile's
+// own sites of r are stored to rout and their |r|^2 added to *nrm.  At most
+// PG_STAGE elements per thread: all loads are issued before any use.
+constexpr int PG_STAGE = (4 * TILE_HY * TILE_HX * 16 + TILE_THREADS - 1) / TILE_THREADS;
+template <class BT>
+__device__ __forceinline__ void pg_stage_axpy(TileSmemT<BT>& sm, const float2* a, const float2* b, float2 alpha,
+                                              float2* rout, const CoarseParams& p, int x0, int y0, float& nrm) {
+    const int L0 = p.Lc[0], L1 = p.Lc[1];
+    const long long slice = p.Vc * 16;
+    const int total = p.Ls_c * TILE_HY * TILE_HX * 16;
+    long long idx[PG_STAGE];
+    float2 va[PG_STAGE], vb[PG_STAGE];
+#pragma unroll
+    for (int u = 0; u < PG_STAGE; ++u) {
+        const int e = threadIdx.x + u * TILE_THREADS;
+        idx[u] = -1;
+        if (e < total) {
+            const int j = e & 15;
+            const int h = (e >> 4) % (TILE_HY * TILE_HX);
+            const int s = (e >> 4) / (TILE_HY * TILE_HX);
+            const int hx = h % TILE_HX, hy = h / TILE_HX;
+            const int gx = ((x0 + hx - 1) % L0 + L0) % L0, gy = ((y0 + hy - 1) % L1 + L1) % L1;
+            idx[u] = s * slice + ((long long)gy * L0 + gx) * 16 + j;
+            va[u] = __ldcg(a + idx[u]);
+            vb[u] = b ? __ldcg(b + idx[u]) : make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PG_STAGE; ++u) {
+        const int e = threadIdx.x + u * TILE_THREADS;
+        if (e < total) {
+            const int j = e & 15;
+            const int h = (e >> 4) % (TILE_HY * TILE_HX);
+            const int s = (e >> 4) / (TILE_HY * TILE_HX);
+            const int hx = h % TILE_HX, hy = h / TILE_HX;
+            float2 v = va[u];
+            v.x -= alpha.x * vb[u].x - alpha.y * vb[u].y;
+            v.y -= alpha.x * vb[u].y + alpha.y * vb[u].x;
+            sm.v[s][hy][hx][j] = v;
+            const bool own = hx >= 1 && hx <= TILE_X && hy >= 1 && hy <= TILE_Y && x0 + hx - 1 < L0 && y0 + hy - 1 < L1;
+            if (own) {
+                rout[idx[u]] = v;
+                nrm += v.x * v.x + v.y * v.y;
+            }
+        }
+    }
+}
+
+// stage the tile and its halo of `in` (all loads issued before any use)
+template <class BT>
+__device__ __forceinline__ void pg_stage(TileSmemT<BT>& sm, const float2* in, const CoarseParams& p, int x0, int y0) {
+    const int L0 = p.Lc[0], L1 = p.Lc[1];
+    const long long slice = p.Vc * 16;
+    const int total = p.Ls_c * TILE_HY * TILE_HX * 16;
+    float2 va[PG_STAGE];
+#pragma unroll
+    for (int u = 0; u < PG_STAGE; ++u) {
+        const int e = threadIdx.x + u * TILE_THREADS;
+        if (e < total) {
+            const int j = e & 15;
+            const int h = (e >> 4) % (TILE_HY * TILE_HX);
+            const int s = (e >> 4) / (TILE_HY * TILE_HX);
+            const int hx = h % TILE_HX, hy = h / TILE_HX;
+            const int gx = ((x0 + hx - 1) % L0 + L0) % L0, gy = ((y0 + hy - 1) % L1 + L1) % L1;
+            va[u] = __ldcg(in + s * slice + ((long long)gy * L0 + gx) * 16 + j);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PG_STAGE; ++u) {
+        const int e = threadIdx.x + u * TILE_THREADS;
+        if (e < total) {
+            const int j = e & 15;
+            const int h = (e >> 4) % (TILE_HY * TILE_HX);
+            const int s = (e >> 4) / (TILE_HY * TILE_HX);
+            sm.v[s][h / TILE_HX][h % TILE_HX][j] = va[u];
+        }
+    }
+}
+
+// e += sum_{j<m} y_j S[(base + j) mod (KC + 1)] (grid-stride; y in shared memory)
+__device__ __forceinline__ void pg_combine(const PgcrArgs& a, const PgcrShared& sh, int base, int m, long long n) {
+    if (m <= 0) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        float2 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) if (i0 + u * stride < n) x[u] = a.e[i0 + u * stride];
+        for (int j = 0; j < m; ++j) {
+            const float2* Sj = a.S[(base + j) % (a.KC + 1)];
+            const float2 y = sh.y[j];
+            float2 r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) if (i0 + u * stride < n) r[u] = __ldcg(Sj + i0 + u * stride);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u].x += y.x * r[u].x - y.y * r[u].y;
+                x[u].y += y.x * r[u].y + y.y * r[u].x;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) if (i0 + u * stride < n) a.e[i0 + u * stride] = x[u];
+    }
+}
+
+// y of the deferred update over m steps: (I + C)^T y = A (thread 0, FP64)
+__device__ __forceinline__ void pg_back_substitute(PgcrShared& sh, int m) {
+    if (threadIdx.x == 0) {
+        double yr[PG_MAXK], yi[PG_MAXK];
+        for (int j = m - 1; j >= 0; --j) {
+            double ar = sh.A[j][0], ai = sh.A[j][1];
+            for (int k = j + 1; k < m; ++k) {
+                ar -= sh.C[k][j][0] * yr[k] - sh.C[k][j][1] * yi[k];
+                ai -= sh.C[k][j][0] * yi[k] + sh.C[k][j][1] * yr[k];
+            }
+            yr[j] = ar; yi[j] = ai;
+            sh.y[j] = make_float2((float)ar, (float)ai);
+        }
+    }
+    __syncthreads();
+}
+
+template <class BT>
+__global__ void __launch_bounds__(TILE_THREADS, 2) k_coarse_gcr_persistent(PgcrArgs a) {
+    extern __shared__ __align__(128) unsigned char pg_raw[];
+    TileSmemT<BT>& sm = *reinterpret_cast<TileSmemT<BT>*>(pg_raw);
+    __shared__ PgcrShared sh;
+    const CoarseParams& p = a.cp;
+    const BT* Y = reinterpret_cast<const BT*>(a.Y);
+    const long long n = p.Vc * p.Ls_c * 16;
+    const int KC = a.KC;
+    const unsigned long long deadline = global_ns() + a.timeout_ns;
+    const int ntx = (p.Lc[0] + TILE_X - 1) / TILE_X;
+    const int ntiles = ntx * ((p.Lc[1] + TILE_Y - 1) / TILE_Y);
+    double* partA = a.partials;                                   // quantity 0
+    unsigned phase = 0;
+    bool ok = true;
+    if (threadIdx.x == 0) mbar_init(&sm.mbar, 1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a.e[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    int base = 0, m = 0, it = 0;
+    const float2* prevR = a.rc;          // r_{k-1} (or r_c before the first step)
+    const float2* prevW = nullptr;       // w_{k-1}
+    float2 prevA = make_float2(0.f, 0.f);
+    double bn2 = 0.0, rr2 = 0.0;
+    for (;;) {
+        // ---- phase A: r_k and t = Dhat_DW r_k ----
+        const bool roll = m == KC;
+        if (roll) pg_back_substitute(sh, KC);                     // y of the cycle that just ended
+        const int slot = (base + m) % (KC + 1);
+        float2* Rk = a.S[slot];
+        float nrA = 0.f;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int x0 = (tile % ntx) * TILE_X, y0 = (tile / ntx) * TILE_Y;
+            __syncthreads();
+            tile_issue_blocks(sm, Y, p, x0, y0);
+            pg_stage_axpy(sm, prevR, prevW, prevA, Rk, p, x0, y0, nrA);
+            __syncthreads();
+            if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
+                mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
+                ok = false;
+                break;
+            }
+            phase ^= 1u;
+            tile_site(sm, a.t, p, x0, y0, p.mf, false);
+        }
+        if (roll) {                                               // e += sum_j y_j r_j of the ended cycle
+            pg_combine(a, sh, base, KC, n);
+            base = slot;
+            m = 0;
+        }
+        {
+            float v[1] = {nrA};
+            pg_partials<1>(v, 1, partA, 0);
+        }
+        if (!pcg_sync(a.bar, deadline, ok)) return;
+        pg_totals(a.partials, 0, 1, sh.tot);
+        rr2 = sh.tot[0];
+        if (it == 0) bn2 = rr2;
+        if (bn2 == 0.0 || rr2 <= a.tol2 * bn2 || it >= a.maxiter) break;
+        // ---- phase B: w = Dhat_PV^dag t with the dots <w_j, w>, j < m ----
+        float dots[2 * (PG_MAXK - 1)];
+#pragma unroll
+        for (int q = 0; q < 2 * (PG_MAXK - 1); ++q) dots[q] = 0.f;
+        float2* Wm = a.W[m];
+        const int mm = m;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int x0 = (tile % ntx) * TILE_X, y0 = (tile / ntx) * TILE_Y;
+            __syncthreads();
+            tile_issue_blocks(sm, Y, p, x0, y0);
+            pg_stage(sm, a.t, p, x0, y0);
+            __syncthreads();
+            if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
+                mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
+                ok = false;
+                break;
+            }
+            phase ^= 1u;
+            tile_site(sm, Wm, p, x0, y0, 1.0f, true, [&](long long idx, float2 w) {
+#pragma unroll
+                for (int j = 0; j < PG_MAXK - 1; ++j) {
+                    if (j < mm) {
+                        const float2 u = __ldcg(a.W[j] + idx);
+                        dots[2 * j] += u.x * w.x + u.y * w.y;
+                        dots[2 * j + 1] += u.x * w.y - u.y * w.x;
+                    }
+                }
+            });
+        }
+        pg_partials<2 * (PG_MAXK - 1)>(dots, 2 * m, a.partials, 1);
+        if (!pcg_sync(a.bar, deadline, ok)) return;
+        if (m > 0) pg_totals(a.partials, 1, 2 * m, sh.tot);
+        if (threadIdx.x < m) {
+            const int j = threadIdx.x;
+            const double nn = sh.nrm[j];
+            const double cr = nn > 0 ? sh.tot[1 + 2 * j] / nn : 0.0, ci = nn > 0 ? sh.tot[2 + 2 * j] / nn : 0.0;
+            sh.C[m][j][0] = cr;
+            sh.C[m][j][1] = ci;
+            sh.coef[j] = make_float2((float)cr, (float)ci);
+        }
+        __syncthreads();
+        // ---- phase C: w_m = w - sum_j c_j w_j; |w_m|^2, <w_m, r_m> ----
+        float vc[3] = {0.f, 0.f, 0.f};
+        {
+            const long long stride = (long long)gridDim.x * blockDim.x;
+            for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+                float2 w[4], r[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long i = i0 + u * stride;
+                    if (i < n) { w[u] = __ldcg(Wm + i); r[u] = __ldcg(Rk + i); }
+                }
+                for (int j = 0; j < m; ++j) {
+                    const float2 c = sh.coef[j];
+                    float2 q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long i = i0 + u * stride;
+                        if (i < n) q[u] = __ldcg(a.W[j] + i);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        w[u].x -= c.x * q[u].x - c.y * q[u].y;
+                        w[u].y -= c.x * q[u].y + c.y * q[u].x;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long i = i0 + u * stride;
+                    if (i < n) {
+                        if (m > 0) Wm[i] = w[u];
+                        vc[0] += w[u].x * w[u].x + w[u].y * w[u].y;
+                        vc[1] += w[u].x * r[u].x + w[u].y * r[u].y;
+                        vc[2] += w[u].x * r[u].y - w[u].y * r[u].x;
+                    }
+                }
+            }
+        }
+        pg_partials<3>(vc, 3, a.partials, 1 + 2 * PG_MAXK);
+        if (!pcg_sync(a.bar, deadline, ok)) return;
+        pg_totals(a.partials, 1 + 2 * PG_MAXK, 3, sh.tot);
+        {
+            const double ww = sh.tot[1 + 2 * PG_MAXK];
+            const double ar = ww > 0 ? sh.tot[2 + 2 * PG_MAXK] / ww : 0.0;
+            const double ai = ww > 0 ? sh.tot[3 + 2 * PG_MAXK] / ww : 0.0;
+            if (threadIdx.x == 0) {
+                sh.nrm[m] = ww;
+                sh.A[m][0] = ar;
+                sh.A[m][1] = ai;
+            }
+            prevA = make_float2((float)ar, (float)ai);
+        }
+        __syncthreads();
+        prevR = Rk;
+        prevW = Wm;
+        ++m;
+        ++it;
+    }
+    // final update with the steps of the current cycle
+    pg_back_substitute(sh, m);
+    pg_combine(a, sh, base, m, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.out_iters += it;
+        *a.out_rr2 = bn2 > 0 ? rr2 / bn2 : 0.0;
+    }
+}
+
+template <class BT>
+static dwf_status launch_pgcr(PgcrArgs& a, int nsm, cudaStream_t st) {
+    static int per_sm[2] = {0, 0};
+    const int which = sizeof(BT) == sizeof(float2) ? 0 : 1;
+    const size_t smem = sizeof(TileSmemT<BT>);
+    if (per_sm[which] == 0) {
+        int per = 0;
+        DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_gcr_persistent<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        DWF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_gcr_persistent<BT>, TILE_THREADS,
+                                                                     smem));
+        if (per < 1) { set_error("persistent coarse GCR cannot be resident"); return DWF_ERR_UNSUPPORTED; }
+        per_sm[which] = per < PGCR_BLOCKS_PER_SM ? per : PGCR_BLOCKS_PER_SM;
+    }
+    const int ntiles = ((a.cp.Lc[0] + TILE_X - 1) / TILE_X) * ((a.cp.Lc[1] + TILE_Y - 1) / TILE_Y);
+    int grid = nsm * per_sm[which];
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    void* args[] = {&a};
+    DWF_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gcr_persistent<BT>, dim3(grid), dim3(TILE_THREADS),
+                                               args, smem, st));
+    return DWF_OK;
+}
+
+bool coarse_gcr_persistent_ok(const dwf_mg* h) {
+    return h->mg.nd == 2 && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->prm.coarse_restart <= PG_MAXK &&
+           h->prm.coarse_restart >= 1;
+}
+
+dwf_status coarse_gcr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* S, float2* const* W,
+                                 float2* t, double* partials, void* bar, int* out_iters, double* out_rr2,
+                                 cudaStream_t st) {
+    if (!coarse_gcr_persistent_ok(h)) {
+        set_error("persistent coarse GCR supports 2-d, 16 coarse dof, Ls_c <= 4 and coarse_restart <= %d", PG_MAXK);
+        return DWF_ERR_UNSUPPORTED;
+    }
+    int dev = 0, nsm = 0;
+    DWF_CHECK_CUDA(cudaGetDevice(&dev));
+    DWF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    PgcrArgs a;
+    a.cp = coarse_params(h, h->mf);
+    a.rc = rc;
+    a.e = ec;
+    const int KC = h->prm.coarse_restart;
+    for (int k = 0; k <= PG_MAXK; ++k) a.S[k] = k <= KC ? S[k] : nullptr;
+    for (int k = 0; k < PG_MAXK; ++k) a.W[k] = k < KC ? W[k] : nullptr;
+    a.t = t;
+    a.partials = partials;
+    a.bar = (PcgBarrier*)bar;
+    a.out_iters = out_iters;
+    a.out_rr2 = out_rr2;
+    a.tol2 = h->prm.coarse_tol * h->prm.coarse_tol;
+    a.maxiter = h->prm.coarse_maxiter;
+    a.KC = KC;
+    a.timeout_ns = 5000000000ULL;   // 5 s per solve
+    DWF_CHECK_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));   // count, gen; the error flag persists
+    if (h->ytile_half) {
+        a.Y = h->Ytile;
+        return launch_pgcr<__half2>(a, nsm, st);
+    }
+    a.Y = h->Y32;
+    return launch_pgcr<float2>(a, nsm, st);
 }
 
 }  // namespace dwf

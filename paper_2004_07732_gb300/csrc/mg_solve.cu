@@ -375,7 +375,7 @@ static dwf_status ensure_workspace(dwf_mg* h) {
     const int KC = h->prm.coarse_restart;
     for (int k = 0; k < 9 + 2 * KC; ++k) {   // 8 coarse vectors, persistent-solver partials, coarse GCR basis
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, k == 8 ? 3 * 4096 * sizeof(double) : nc * sizeof(float2) + 256);
+        cudaError_t e = cudaMalloc(&p, k == 8 ? 64 * 1024 * sizeof(double) : nc * sizeof(float2) + 256);
         if (e != cudaSuccess) { set_error("coarse vectors: %s", cudaGetErrorString(e)); return DWF_ERR_OOM; }
         h->coarse_vecs.push_back(p);
     }
@@ -555,10 +555,27 @@ static dwf_status coarse_solve_gcr(Solver& s) {
 }
 
 // Coarse solve: CGNR on B^dag B e = B^dag r, B = Dhat_PV^dag Dhat_DW.
+static bool persistent_coarse(const dwf_mg* h) {
+    if (!h->prm.coarse_persistent) return false;
+    if (h->prm.coarse_solver == 1) return h->prm.coarse_persistent == 2 && coarse_gcr_persistent_ok(h);
+    return h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2;
+}
+
 static dwf_status coarse_solve(Solver& s) {
     dwf_mg* h = s.h;
+    if (h->prm.coarse_solver == 1 && persistent_coarse(h)) {
+        // one cooperative launch per coarse solve; residual slots Zc[0..KC-1] and crr
+        float2* S[GCR_MAXK + 1];
+        const int KC = h->prm.coarse_restart;
+        for (int k = 0; k < KC; ++k) S[k] = s.Zc[k];
+        S[KC] = s.crr;
+        DWF_TRY(coarse_gcr_persistent(h, s.rc, s.ec, S, s.Wc, s.ct, s.partials, s.d->bar, &s.d->pcg_iters,
+                                      &s.d->pcg_rr2, s.st));
+        s.coarse_solves += 1;
+        return DWF_OK;
+    }
     if (h->prm.coarse_solver == 1) return coarse_solve_gcr(s);
-    if (h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
+    if (persistent_coarse(h)) {
         float2* v6[6] = {s.crr, s.cr, s.cp, s.cq, s.ct, s.cw};
         DWF_TRY(coarse_cgnr_persistent(h, s.rc, s.ec, v6, s.partials, s.d->bar, &s.d->pcg_iters, &s.d->pcg_rr2, s.st));
         s.coarse_solves += 1;
@@ -727,12 +744,13 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
         k_axpy_64_32<<<s.eg, 256, 0, s.st>>>(X, s.e, rn, n);
         DWF_CHECK_LAUNCH();
     }
-    if (h->prm.coarse_solver == 0 && h->prm.coarse_persistent && h->mg.ncd == 16 && h->mg.Ls_c <= 4 && h->mg.nd == 2) {
+    if (persistent_coarse(h)) {
         DWF_CHECK_CUDA(cudaMemcpyAsync(&s.hs->pcg_iters, &s.d->pcg_iters, sizeof(int), cudaMemcpyDeviceToHost, s.st));
         DWF_CHECK_CUDA(cudaMemcpyAsync(s.hs->bar, s.d->bar, sizeof(s.d->bar), cudaMemcpyDeviceToHost, s.st));
         DWF_CHECK_CUDA(cudaStreamSynchronize(s.st));
         s.coarse_iters = s.hs->pcg_iters;
-        s.coarse_applies = 2 * s.coarse_solves + 4LL * s.coarse_iters;
+        s.coarse_applies = h->prm.coarse_solver == 1 ? 2LL * s.coarse_iters + s.coarse_solves
+                                                     : 2 * s.coarse_solves + 4LL * s.coarse_iters;
         if (s.hs->bar[2] != 0u) {
             set_error("persistent coarse solver: a grid barrier or bulk copy timed out");
             status = DWF_ERR_TIMEOUT;

@@ -36,11 +36,13 @@ def _hierarchy(dw, dims, Ls, sigma, seed, M5=1.0, mf=0.01, mset=-0.19, extra=Non
     return h, U, rng
 
 
-@pytest.mark.parametrize("dims,Ls,sigma,mset,nrhs", [((32, 32), 8, 0.5, -0.19, 3), ((16, 16), 8, 0.3, -0.08, 5),
-                                                     ((24, 16), 6, 0.5, -0.19, 1)])
-def test_batched_solve_reaches_tolerance(dw, dims, Ls, sigma, mset, nrhs):
+@pytest.mark.parametrize("dims,Ls,sigma,mset,nrhs,extra", [((32, 32), 8, 0.5, -0.19, 3, None),
+                                                           ((16, 16), 8, 0.3, -0.08, 5, None),
+                                                           ((24, 16), 6, 0.5, -0.19, 1, None),
+                                                           ((24, 16), 6, 0.5, -0.19, 1, {"coarse_persistent": 2})])
+def test_batched_solve_reaches_tolerance(dw, dims, Ls, sigma, mset, nrhs, extra):
     M5, mf = 1.0, 0.01
-    h, U, rng = _hierarchy(dw, dims, Ls, sigma, 50 + nrhs, M5, mf, mset)
+    h, U, rng = _hierarchy(dw, dims, Ls, sigma, 50 + nrhs, M5, mf, mset, extra)
     V = int(np.prod(dims))
     B = np.stack([synth.gaussian_spinor(rng, dims, Ls).reshape(-1) for _ in range(nrhs)])
     X = torch.empty(nrhs * V * Ls * 2, dtype=torch.complex128, device="cuda")
