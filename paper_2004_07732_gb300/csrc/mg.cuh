@@ -95,6 +95,9 @@ dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine,
 dwf_status coarse_cgnr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* vec6, double* partials,
                                   void* bar, int* out_iters, double* out_rr2, cudaStream_t st);
 
+// the batched K-cycle on nrhs right-hand sides stored back to back (mg_batched.cu)
+dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2* X, double tol, int maxiter,
+                                 dwf_solve_stats* stats);
 // releases the batched solver's workspace of a handle
 void batched_state_free(dwf_mg* h);
 

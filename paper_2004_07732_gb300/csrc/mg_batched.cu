@@ -687,8 +687,9 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
     if (!h || !B || !X) { set_error("NULL argument"); return DWF_ERR_ARG; }
     if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
     if (!(tol > 0.0)) { set_error("tol must be > 0"); return DWF_ERR_ARG; }
-    if (h->mg.nd != 2 || h->mg.ncd != 16) {
-        set_error("the batched solver supports 2-d lattices with nvec = 8"); return DWF_ERR_UNSUPPORTED;
+    if (h->mg.nd != 2 || (nrhs > 1 && h->mg.ncd != 16)) {
+        set_error("the batched solver supports 2-d lattices, with nvec = 8 for more than one right-hand side");
+        return DWF_ERR_UNSUPPORTED;
     }
     if (h->prm.gcr_restart < 1 || h->prm.gcr_restart > BK_MAX || h->prm.post_smooth > BK_MAX ||
         h->prm.coarse_restart < 1 || h->prm.coarse_restart > BK_MAX) {
