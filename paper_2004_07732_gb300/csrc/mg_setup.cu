@@ -275,6 +275,157 @@ __global__ void k_galerkin_2d(const double2* __restrict__ U, const double2* __re
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3'. Galerkin kernel Dhat_W = P^dag D_W P, 4-d SU(3), FP32 arithmetic
+// ---------------------------------------------------------------------------
+// gamma_mu in the chiral basis: [[0, A_mu], [A_mu^dag, 0]] with A = -i sigma_1,
+// -i sigma_2, -i sigma_3, 1 (the basis of the fine 4-d operator)
+__device__ __forceinline__ float2 amat(int mu, int r, int c) {   // A_mu[r][c], r, c in {0, 1}
+    if (mu == 0) return r != c ? make_float2(0.f, -1.f) : make_float2(0.f, 0.f);          // -i sigma_1
+    if (mu == 1) return (r == 0 && c == 1) ? make_float2(-1.f, 0.f)
+                        : (r == 1 && c == 0) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);  // -i sigma_2
+    if (mu == 2) return r != c ? make_float2(0.f, 0.f) : make_float2(0.f, r == 0 ? -1.f : 1.f); // -i sigma_3
+    return r == c ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ float2 gamma4(int mu, int a, int b) {
+    if (a < 2 && b >= 2) return amat(mu, a, b - 2);
+    if (a >= 2 && b < 2) { const float2 A = amat(mu, b, a - 2); return make_float2(A.x, -A.y); }
+    return make_float2(0.f, 0.f);
+}
+
+constexpr int GAL4_THREADS = 256;
+constexpr int GAL4_MAXE = 16;           // Y entries per thread: ncd^2 <= 16 * 256 (ncd <= 64)
+
+// One block per (coarse site, direction): Y_dir = sum_x P(x)^dag Q(x) with
+// Q(x) = sum over the hops from x that land in the aggregate of xc + dir (and
+// the diagonal for dir 0) of D_W(x, y) P(y).  P(x) is 12 x ncd, block diagonal
+// in chirality (rows of spins 2c, 2c+1 feed columns c*nvec ...).
+__global__ void __launch_bounds__(GAL4_THREADS) k_galerkin_4d(const double2* __restrict__ U,
+                                                              const float2* __restrict__ P, double2* __restrict__ Y,
+                                                              AggIndex ai, int nvec, long long V, float diag,
+                                                              int4 anti) {
+    extern __shared__ float2 g4sm[];
+    const int ncd = 2 * nvec;
+    float2* Py = g4sm;                  // [12][nvec]: rows of the fine dof, columns of that row's chirality
+    float2* Px = Py + 12 * nvec;        // [12][nvec]
+    float2* Q = Px + 12 * nvec;         // [12][ncd]
+    __shared__ float Ul[9][2];
+    const long long xc = blockIdx.x;
+    const int dir = blockIdx.y;
+    const int nb = ai.b[0] * ai.b[1] * ai.b[2] * ai.b[3];
+    const int nent = ncd * ncd;
+    float2 acc[GAL4_MAXE];
+#pragma unroll
+    for (int u = 0; u < GAL4_MAXE; ++u) acc[u] = make_float2(0.f, 0.f);
+    const int anti_[4] = {anti.x, anti.y, anti.z, anti.w};
+    for (int l = 0; l < nb; ++l) {
+        const long long x = ai.fine_site(xc, l);
+        int xcrd[4];
+        {
+            long long rem = x;
+            for (int mu = 0; mu < 4; ++mu) { xcrd[mu] = (int)(rem % ai.L[mu]); rem /= ai.L[mu]; }
+        }
+        for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) Q[e] = make_float2(0.f, 0.f);
+        bool any = false;
+        for (int term = 0; term < 9; ++term) {
+            long long y = x;
+            int mu = 0, fwd = 1;
+            float ph = 1.f;
+            if (term == 0) {
+                if (dir != 0) continue;
+            } else {
+                mu = (term - 1) / 2;
+                fwd = ((term - 1) % 2) == 0;
+                const int lc = xcrd[mu] % ai.b[mu];
+                const bool crosses = fwd ? (lc == ai.b[mu] - 1) : (lc == 0);
+                const int want = crosses ? (1 + 2 * mu + (fwd ? 0 : 1)) : 0;
+                if (want != dir) continue;
+                int ycrd[4] = {xcrd[0], xcrd[1], xcrd[2], xcrd[3]};
+                ycrd[mu] += fwd ? 1 : -1;
+                const bool wrap = ycrd[mu] < 0 || ycrd[mu] >= ai.L[mu];
+                ycrd[mu] = (ycrd[mu] + ai.L[mu]) % ai.L[mu];
+                y = 0;
+                long long st = 1;
+                for (int nu = 0; nu < 4; ++nu) { y += ycrd[nu] * st; st *= ai.L[nu]; }
+                if (wrap && anti_[mu]) ph = -1.f;
+            }
+            any = true;
+            __syncthreads();                       // previous term's Py / Ul fully used
+            for (int e = threadIdx.x; e < 12 * nvec; e += blockDim.x) {
+                const int d = e / nvec, k = e % nvec;
+                const int sp = d / 3, c = sp / 2, lch = (sp % 2) * 3 + d % 3;
+                Py[e] = P[((y * 2 + c) * 6 + lch) * nvec + k];
+            }
+            if (term > 0 && threadIdx.x < 9) {
+                const int a = threadIdx.x / 3, b = threadIdx.x % 3;
+                // forward: U_mu(x)[a][b]; backward: U_mu(y)^dag[a][b] = conj(U_mu(y)[b][a])
+                const double2 u = fwd ? U[((long long)mu * V + x) * 9 + a * 3 + b] : U[((long long)mu * V + y) * 9 + b * 3 + a];
+                Ul[threadIdx.x][0] = (float)u.x;
+                Ul[threadIdx.x][1] = fwd ? (float)u.y : -(float)u.y;
+            }
+            __syncthreads();
+            // Q[a][j] += sum_{b: chirality of column j} D[a][b] Py[b][kj]
+            for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                const int a = e / ncd, j = e % ncd;
+                const int cj = j / nvec, kj = j % nvec;
+                const int sa = a / 3, ca = a % 3;
+                float2 q = Q[e];
+                for (int bl = 0; bl < 6; ++bl) {
+                    const int sb = 2 * cj + bl / 3, cb = bl % 3, b = sb * 3 + cb;
+                    float2 dab;
+                    if (term == 0) {
+                        if (b != a) continue;
+                        dab = make_float2(diag, 0.f);
+                    } else {
+                        // -1/2 ph (1 -+ gamma_mu)[sa][sb] U[ca][cb]   (- for forward)
+                        float2 sg = gamma4(mu, sa, sb);
+                        const float sgn = fwd ? -1.f : 1.f;
+                        float2 spin = make_float2((sa == sb ? 1.f : 0.f) + sgn * sg.x, sgn * sg.y);
+                        if (spin.x == 0.f && spin.y == 0.f) continue;
+                        const float ur = Ul[ca * 3 + cb][0], ui = Ul[ca * 3 + cb][1];
+                        dab = make_float2(-0.5f * ph * (spin.x * ur - spin.y * ui), -0.5f * ph * (spin.x * ui + spin.y * ur));
+                    }
+                    const float2 pv = Py[b * nvec + kj];
+                    q.x += dab.x * pv.x - dab.y * pv.y;
+                    q.y += dab.x * pv.y + dab.y * pv.x;
+                }
+                Q[e] = q;
+            }
+        }
+        if (!any) continue;                        // uniform over the block
+        __syncthreads();
+        for (int e = threadIdx.x; e < 12 * nvec; e += blockDim.x) {
+            const int d = e / nvec, k = e % nvec;
+            const int sp = d / 3, c = sp / 2, lch = (sp % 2) * 3 + d % 3;
+            Px[e] = P[((x * 2 + c) * 6 + lch) * nvec + k];
+        }
+        __syncthreads();
+        // Y[i][j] += sum_{a in chirality ci} conj(Px[a][ki]) Q[a][j]
+#pragma unroll
+        for (int u = 0; u < GAL4_MAXE; ++u) {
+            const int e = threadIdx.x + u * GAL4_THREADS;
+            if (e < nent) {
+                const int i = e / ncd, j = e % ncd;
+                const int ci = i / nvec, ki = i % nvec;
+                float2 s = acc[u];
+                for (int al = 0; al < 6; ++al) {
+                    const int a = (2 * ci + al / 3) * 3 + al % 3;
+                    const float2 pv = Px[a * nvec + ki], qv = Q[a * ncd + j];
+                    s.x += pv.x * qv.x + pv.y * qv.y;
+                    s.y += pv.x * qv.y - pv.y * qv.x;
+                }
+                acc[u] = s;
+            }
+        }
+        __syncthreads();                           // Q and Px are rewritten by the next site
+    }
+#pragma unroll
+    for (int u = 0; u < GAL4_MAXE; ++u) {
+        const int e = threadIdx.x + u * GAL4_THREADS;
+        if (e < nent) Y[((long long)xc * 9 + dir) * nent + e] = make_double2(acc[u].x, acc[u].y);
+    }
+}
+
 __global__ void k_blocks_to_f32(const double2* __restrict__ Y, float2* __restrict__ Y32, long long nblocks, int ncd) {
     const long long n = nblocks * ncd * ncd;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -380,8 +531,16 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
                                              (double)G.nd - h->M5, G.anti[0], G.anti[1]);
         DWF_CHECK_LAUNCH();
     } else {
-        set_error("4-d multigrid setup not built yet");
-        return DWF_ERR_UNSUPPORTED;
+        if (G.group != DWF_SU3 || m.ncd > 64 || m.nchd != 6) {
+            set_error("4-d multigrid setup supports SU(3) with nvec <= 32");
+            return DWF_ERR_UNSUPPORTED;
+        }
+        const size_t sh = (size_t)(12 * m.nvec * 2 + 12 * m.ncd) * sizeof(float2);
+        dim3 grid((unsigned)m.Vc, 9);
+        k_galerkin_4d<<<grid, GAL4_THREADS, sh, st>>>((const double2*)h->U64, h->P32, h->Y64, ai, m.nvec, G.V,
+                                                      (float)((double)G.nd - h->M5),
+                                                      make_int4(G.anti[0], G.anti[1], G.anti[2], G.anti[3]));
+        DWF_CHECK_LAUNCH();
     }
     k_blocks_to_f32<<<ew_grid(nblk * m.ncd * m.ncd), 256, 0, st>>>(h->Y64, h->Y32, nblk, m.ncd);
     DWF_CHECK_LAUNCH();
