@@ -43,6 +43,9 @@ SOLVE_WL = synth.SCHWINGER_256
 # smallest real part of spec D_W(U, 0), estimated once offline on 64^2 samples
 # of each link-angle width (0.31-0.39 for sigma 0.7, 0.19-0.20 for 0.5).
 SETUP_MASS = {0.7: -0.3, 0.5: -0.19, 0.214: -0.035}
+# 4-d SU(3), eps 0.3: the smallest real part of spec D_W(U, 0) is 0.443 (scipy on 6^4 and 8^4
+# samples of the same ensemble), so the setup relaxes at m_s = -0.42, just above critical
+SETUP_MASS_SU3 = -0.42
 # algorithmic bytes per 5-d site of the FP32-spinor / FP16-link 2-d apply:
 # read psi (2 complex64 = 16 B) + write out (16 B) + 2 links x 4 B shared by Ls slices
 def apply_bytes(V, Ls, spinor_b=16, link_b=4):
@@ -299,6 +302,9 @@ def run_ours(args):
     su3 = None
     if not args.skip_su3:
         su3 = time_su3_apply(dw, dev, stream, args)
+    su3_solve = None
+    if not args.skip_su3 and not args.skip_solve and not args.skip_mg:
+        su3_solve = time_su3_solves(dw, dev)
 
     # ---------------- batched multi-RHS apply: 64 sources, mixed lattices ----------------
     batched = None
@@ -342,10 +348,52 @@ def run_ours(args):
                 "e2e": {"value": world * nbytes / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "gpu_launches": launches, "su3_apply": su3, "batched_apply": batched, "solve": solve,
+                "gpu_launches": launches, "su3_apply": su3, "su3_solve": su3_solve, "batched_apply": batched,
+                "solve": solve,
                 "batched_solve": batched_solve, "coarse_multi_rhs": coarse_multi}
         print(json.dumps(line), flush=True)
     ranks.close()
+
+
+def time_su3_solves(dw, dev):
+    """16^3 x 32 x Ls=16 SU(3) (eps 0.3, M5 1.8, m 0.01) to 1e-10: the two-level MG
+    (2^4 aggregates, Nvec = 24, FP16 coarse blocks) against FP64 CGNE, same source."""
+    import torch
+    wl = synth.SU3_16x32
+    U, srcs = wl.draw(1)
+    g = dw.make_geom(wl.dims, wl.Ls, group="su3")
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    b = torch.from_numpy(srcs[0].reshape(-1)).to(dev)
+    x = torch.empty_like(b)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st, status = dw.cgne_solve(g, U64, b, x, wl.M5, wl.mf, tol=1e-10, maxiter=200000, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    t_cg = time.perf_counter() - t0
+    nvec = 24
+    rng = synth.rng_for(wl.seed + 7000)
+    starts = np.stack([synth.gaussian_complex(rng, (wl.V * 12,)) for _ in range(nvec)])
+    params = {"nvec": nvec, "block": [2, 2, 2, 2], "setup_mass": SETUP_MASS_SU3}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    mg = dw.mg_setup(g, U64, wl.M5, wl.mf, params, torch.from_numpy(starts.reshape(-1)).to(dev))
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t0
+    y = torch.empty_like(b)
+    dw.mg_solve(mg, b, y, tol=1e-10, maxiter=2, raise_noconv=False)      # warm (workspace, graphs)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sm, mstatus = dw.mg_solve(mg, b, y, tol=1e-10, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    t_mg = time.perf_counter() - t0
+    dw.mg_destroy(mg)
+    return {"workload": f"{wl.name}: D_DW x = b to 1e-10, M5 {wl.M5}, m {wl.mf}",
+            "cgne_fp64": {"seconds": t_cg, "iterations": st["iterations"], "true_residual": st["true_residual"],
+                          "status": status},
+            "mg": {"seconds": t_mg, "setup_seconds": t_setup, "outer_iterations": sm["iterations"],
+                   "fine_applies": sm["fine_applies"], "coarse_avg_iters": sm["coarse_avg_iters"],
+                   "true_residual": sm["true_residual"], "status": mstatus},
+            "mg_speedup_vs_cgne": t_cg / t_mg if t_mg > 0 else None}
 
 
 def time_su3_apply(dw, dev, stream, args):

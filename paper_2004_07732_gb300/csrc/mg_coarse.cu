@@ -373,12 +373,14 @@ __global__ void __launch_bounds__(TILE_THREADS) k_coarse_tile(const BT* __restri
 
 static bool tile_ok(const CoarseParams& p) { return p.nd == 2 && p.ncd == 16 && p.Ls_c <= 4; }
 
+static dwf_status site_init_attributes();
+
 dwf_status coarse_init_attributes() {
     DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tile<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(TileSmemT<float2>)));
     DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tile<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(TileSmemT<__half2>)));
-    return DWF_OK;
+    return site_init_attributes();
 }
 
 template <int NCD>
@@ -389,6 +391,228 @@ __global__ void __launch_bounds__(256) k_coarse_dwf(const float2* __restrict__ B
     if (xc >= p.Vc) return;
     if (NCD == 16 && p.Ls_c <= 4) warp_site16<false>(B, in, out, p, xc, p.mf, dag, threadIdx.x & 31);
     else warp_site_apply<NCD, false>(B, in, out, p, xc, p.mf, dag, threadIdx.x & 31);
+}
+
+// ---------------------------------------------------------------------------
+// Per-site kernel for wide coarse blocks (4-d: 9 directions, 2 nvec = 48 dof).
+// One block per coarse site: the site's ndir blocks (contiguous, 83 KB in FP16
+// at 48 dof) arrive in shared memory by one cp.async.bulk on an mbarrier while
+// the threads stage the neighbours' inputs; thread (i, s) then forms output row
+// i of slice s from shared memory only.  At one right-hand side the blocks are
+// read once per apply, so the kernel is bound by their HBM traffic.  The
+// adjoint uses sigma_3 (Dhat_W^dag = sigma_3 Dhat_W sigma_3), so the same blocks
+// serve both.
+// ---------------------------------------------------------------------------
+// neighbour of coarse site xc in direction dir (0 self, 1 + 2 mu forward, 2 + 2 mu
+// backward) with 32-bit index arithmetic (coarse lattices have < 2^31 sites)
+__device__ __forceinline__ int coarse_nb32(const CoarseParams& p, int xc, int dir) {
+    if (dir == 0) return xc;
+    const int mu = (dir - 1) >> 1;
+    const int L0 = p.Lc[0], L1 = p.Lc[1], L2 = p.Lc[2], L3 = p.Lc[3];
+    const int Lm = mu == 0 ? L0 : mu == 1 ? L1 : mu == 2 ? L2 : L3;
+    const int stride = mu == 0 ? 1 : mu == 1 ? L0 : mu == 2 ? L0 * L1 : L0 * L1 * L2;
+    const int c = (xc / stride) % Lm;
+    const int cn = ((dir - 1) & 1) ? (c == 0 ? Lm - 1 : c - 1) : (c == Lm - 1 ? 0 : c + 1);
+    return xc + (cn - c) * stride;
+}
+
+template <class BT>
+__host__ __device__ constexpr size_t site_smem_bytes(int ndir, int ncd, int Ls_c) {
+    return ((size_t)ndir * ncd * ncd * sizeof(BT) + 15) / 16 * 16 + (size_t)ndir * Ls_c * ncd * sizeof(float2) + 16;
+}
+
+template <class BT>
+__global__ void __launch_bounds__(512) k_coarse_site(const BT* __restrict__ B, const float2* __restrict__ in,
+                                                     float2* __restrict__ out, CoarseParams p, bool dag,
+                                                     const int* skip, int* status) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(128) unsigned char site_raw[];
+    const int ncd = p.ncd, ndir = p.ndir, Ls_c = p.Ls_c;
+    const size_t yb_bytes = ((size_t)ndir * ncd * ncd * sizeof(BT) + 15) / 16 * 16;
+    BT* yb = reinterpret_cast<BT*>(site_raw);
+    float2* vs = reinterpret_cast<float2*>(site_raw + yb_bytes);                 // [dir][s][j]
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(site_raw + yb_bytes +
+                                                                     (size_t)ndir * Ls_c * ncd * sizeof(float2));
+    const long long xc = blockIdx.x;
+    const long long slice = p.Vc * ncd;
+    const unsigned bytes = (unsigned)((size_t)ndir * ncd * ncd * sizeof(BT));
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(mbar, bytes);
+        bulk_g2s(yb, B + xc * (long long)ndir * ncd * ncd, bytes, mbar);
+    }
+    __shared__ int nbs[MG_MAX_DIRS];
+    if (threadIdx.x < ndir) nbs[threadIdx.x] = coarse_nb32(p, (int)xc, threadIdx.x);
+    __syncthreads();
+    const int nv = ndir * Ls_c * ncd;
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+        const int j = e % ncd, s = (e / ncd) % Ls_c, dir = e / (ncd * Ls_c);
+        vs[e] = __ldg(in + s * slice + (long long)nbs[dir] * ncd + j);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(mbar, 0, TILE_WAIT_NS)) {
+        if (threadIdx.x == 0) atomicExch(status, 2);
+        mbar_wait_bounded(mbar, 0, TILE_WAIT_NS);          // let the copy land before the block exits
+        return;
+    }
+    const int i = threadIdx.x % ncd, s = threadIdx.x / ncd;
+    if (s >= Ls_c) return;
+    const int nvec = p.nvec;
+    float2 a_lo = make_float2(0.f, 0.f), a_hi = make_float2(0.f, 0.f);    // inputs j < nvec / j >= nvec
+    for (int dir = 0; dir < ndir; ++dir) {
+        const BT* yd = yb + (size_t)dir * ncd * ncd + i;
+        const float2* v = vs + (dir * Ls_c + s) * ncd;
+#pragma unroll 4
+        for (int j = 0; j < nvec; ++j) a_lo = cfma(to_f2(yd[j * ncd]), v[j], a_lo);
+#pragma unroll 4
+        for (int j = nvec; j < ncd; ++j) a_hi = cfma(to_f2(yd[j * ncd]), v[j], a_hi);
+    }
+    const float sj = dag ? -1.f : 1.f;                   // sigma_3 on the inputs
+    const float si = (dag && i >= nvec) ? -1.f : 1.f;    // sigma_3 on the output
+    float2 acc = make_float2(si * (a_lo.x + sj * a_hi.x), si * (a_lo.y + sj * a_hi.y));
+    const float2* v0 = vs;                               // dir 0 = the site itself
+    const float2 self = v0[s * ncd + i];
+    const int c = i / nvec;
+    const bool from_below = dag ? (c == 1) : (c == 0);
+    int sh;
+    float sc = 1.f;
+    if (from_below) { if (s > 0) sh = s - 1; else { sh = Ls_c - 1; sc = -p.mf; } }
+    else            { if (s < Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
+    const float2 hv = v0[sh * ncd + i];
+    acc.x += self.x + sc * hv.x;
+    acc.y += self.y + sc * hv.y;
+    out[s * slice + xc * ncd + i] = acc;
+}
+
+// Persistent, double-buffered variant for 48 coarse dof and FP16 blocks (the
+// 4-d workload): one block per SM walks the coarse sites; while site k is
+// multiplied, the bulk copies of site k + 1's blocks (83 KB) and of its
+// neighbours' inputs (one 384-byte run per direction and slice) are in flight
+// on the other buffer's mbarrier, so the HBM stream of blocks never stops.
+// Thread (i, g): row i of direction g (all slices); the nine direction
+// partials of each (row, slice) are summed in shared memory.
+constexpr int SDB_NCD = 48, SDB_NDIR = 9, SDB_LS = 4, SDB_GROUPS = SDB_NDIR;
+constexpr int SDB_THREADS = SDB_NCD * SDB_GROUPS;
+struct SiteDbSmem {
+    __half2 yb[2][SDB_NDIR * SDB_NCD * SDB_NCD];
+    float2 vs[2][SDB_NDIR][SDB_LS][SDB_NCD];
+    float2 part[SDB_GROUPS][SDB_LS][SDB_NCD];
+    unsigned long long mbar[2];
+};
+
+// warp 0 only: lane 0 expects the bytes and copies the blocks; lane d < ndir copies
+// direction d's neighbour inputs, all on the buffer's mbarrier
+__device__ __forceinline__ void sdb_issue(SiteDbSmem& sm, int buf, const __half2* __restrict__ B,
+                                          const float2* __restrict__ in, const CoarseParams& p, int xc) {
+    constexpr unsigned YB = SDB_NDIR * SDB_NCD * SDB_NCD * sizeof(__half2);
+    constexpr unsigned VB = SDB_NCD * sizeof(float2);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        const unsigned bytes = YB + (unsigned)(SDB_NDIR * p.Ls_c) * VB;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&sm.mbar[buf], bytes);
+        bulk_g2s(sm.yb[buf], B + (long long)xc * SDB_NDIR * SDB_NCD * SDB_NCD, YB, &sm.mbar[buf]);
+    }
+    __syncwarp();
+    if (lane < SDB_NDIR) {
+        const long long slice = p.Vc * SDB_NCD;
+        const int nb = coarse_nb32(p, xc, lane);
+        for (int s = 0; s < p.Ls_c; ++s)
+            bulk_g2s(&sm.vs[buf][lane][s][0], in + s * slice + (long long)nb * SDB_NCD, VB, &sm.mbar[buf]);
+    }
+}
+
+__global__ void __launch_bounds__(SDB_THREADS, 1) k_coarse_site_db(const __half2* __restrict__ B,
+                                                                   const float2* __restrict__ in,
+                                                                   float2* __restrict__ out, CoarseParams p, bool dag,
+                                                                   const int* skip, int* status) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(128) unsigned char sdb_raw[];
+    SiteDbSmem& sm = *reinterpret_cast<SiteDbSmem*>(sdb_raw);
+    const int Ls_c = p.Ls_c, nvec = p.nvec;
+    const long long slice = p.Vc * SDB_NCD;
+    const int i = threadIdx.x % SDB_NCD, grp = threadIdx.x / SDB_NCD;   // grp = direction
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.mbar[0], 1);
+        mbar_init(&sm.mbar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && blockIdx.x < p.Vc) sdb_issue(sm, 0, B, in, p, blockIdx.x);
+    int k = 0;
+    for (long long xc = blockIdx.x; xc < p.Vc; xc += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const long long nxt = xc + gridDim.x;
+        if (threadIdx.x < 32 && nxt < p.Vc) sdb_issue(sm, buf ^ 1, B, in, p, (int)nxt);
+        if (!mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS)) {
+            if (threadIdx.x == 0) atomicExch(status, 2);
+            // let the copies in flight land before the block exits
+            mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS);
+            if (nxt < p.Vc) mbar_wait_bounded(&sm.mbar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1), TILE_WAIT_NS);
+            return;
+        }
+        float2 a_lo[SDB_LS], a_hi[SDB_LS];
+#pragma unroll
+        for (int s = 0; s < SDB_LS; ++s) { a_lo[s] = make_float2(0.f, 0.f); a_hi[s] = make_float2(0.f, 0.f); }
+        {
+            const int dir = grp;
+            const __half2* yd = sm.yb[buf] + dir * SDB_NCD * SDB_NCD + i;
+#pragma unroll 4
+            for (int j = 0; j < SDB_NCD; ++j) {
+                const float2 y = __half22float2(yd[j * SDB_NCD]);
+#pragma unroll
+                for (int s = 0; s < SDB_LS; ++s) {
+                    if (s < Ls_c) {
+                        const float2 v = sm.vs[buf][dir][s][j];
+                        if (j < nvec) a_lo[s] = cfma(y, v, a_lo[s]);
+                        else          a_hi[s] = cfma(y, v, a_hi[s]);
+                    }
+                }
+            }
+        }
+        const float sj = dag ? -1.f : 1.f;                 // sigma_3 on the inputs
+#pragma unroll
+        for (int s = 0; s < SDB_LS; ++s)
+            if (s < Ls_c) sm.part[grp][s][i] = make_float2(a_lo[s].x + sj * a_hi[s].x, a_lo[s].y + sj * a_hi[s].y);
+        __syncthreads();
+        // epilogue: thread t < 48 * Ls_c forms output (row, slice)
+        if (threadIdx.x < SDB_NCD * Ls_c) {
+            const int r = threadIdx.x % SDB_NCD, s = threadIdx.x / SDB_NCD;
+            float2 hsum = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int g = 0; g < SDB_GROUPS; ++g) { hsum.x += sm.part[g][s][r].x; hsum.y += sm.part[g][s][r].y; }
+            const float si = (dag && r >= nvec) ? -1.f : 1.f;
+            const float2 self = sm.vs[buf][0][s][r];
+            const int c = r / nvec;
+            const bool from_below = dag ? (c == 1) : (c == 0);
+            int sh;
+            float sc = 1.f;
+            if (from_below) { if (s > 0) sh = s - 1; else { sh = Ls_c - 1; sc = -p.mf; } }
+            else            { if (s < Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
+            const float2 hv = sm.vs[buf][0][sh][r];
+            out[s * slice + xc * SDB_NCD + r] =
+                make_float2(si * hsum.x + self.x + sc * hv.x, si * hsum.y + self.y + sc * hv.y);
+        }
+        __syncthreads();                                   // buffer buf and the partials are free again
+    }
+}
+
+constexpr size_t SITE_SMEM_MAX = 200 * 1024;
+static dwf_status site_init_attributes() {
+    DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_site_db, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(SiteDbSmem)));
+    DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_site<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SITE_SMEM_MAX));
+    DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_site<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SITE_SMEM_MAX));
+    return DWF_OK;
+}
+
+// the per-site kernel: 4-d blocks (or wide 2-d ones) whose shared-memory copy fits in a block
+static bool site_ok(const CoarseParams& p, int half) {
+    if (p.ncd < 24 || p.ncd * p.Ls_c > 512) return false;
+    const size_t b = half ? site_smem_bytes<__half2>(p.ndir, p.ncd, p.Ls_c) : site_smem_bytes<float2>(p.ndir, p.ncd, p.Ls_c);
+    return b <= SITE_SMEM_MAX;
 }
 
 static CoarseParams coarse_params(const dwf_mg* h, double mf) {
@@ -418,6 +642,24 @@ dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, doub
                 (const __half2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
         else
             k_coarse_tile<float2><<<ntiles, TILE_THREADS, sizeof(TileSmemT<float2>), st>>>(
+                (const float2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
+    } else if (h->ytile_half && p.ncd == SDB_NCD && p.ndir == SDB_NDIR && p.Ls_c <= SDB_LS) {
+        static int nsm = 0;
+        if (nsm == 0) {
+            int dev = 0;
+            DWF_CHECK_CUDA(cudaGetDevice(&dev));
+            DWF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        }
+        const long long grid1 = p.Vc < nsm ? p.Vc : nsm;
+        k_coarse_site_db<<<(unsigned)grid1, SDB_THREADS, sizeof(SiteDbSmem), st>>>((const __half2*)h->Ytile, in, out, p,
+                                                                                  dagger, skip, h->status + 1);
+    } else if (site_ok(p, h->ytile_half)) {
+        const int threads = p.ncd * p.Ls_c;
+        if (h->ytile_half)
+            k_coarse_site<__half2><<<(unsigned)p.Vc, threads, site_smem_bytes<__half2>(p.ndir, p.ncd, p.Ls_c), st>>>(
+                (const __half2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
+        else
+            k_coarse_site<float2><<<(unsigned)p.Vc, threads, site_smem_bytes<float2>(p.ndir, p.ncd, p.Ls_c), st>>>(
                 (const float2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
     } else if (p.ncd == 16) k_coarse_dwf<16><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
     else             k_coarse_dwf<0><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
