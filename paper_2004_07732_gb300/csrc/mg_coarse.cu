@@ -490,10 +490,12 @@ __global__ void __launch_bounds__(512) k_coarse_site(const BT* __restrict__ B, c
 // multiplied, the bulk copies of site k + 1's blocks (83 KB) and of its
 // neighbours' inputs (one 384-byte run per direction and slice) are in flight
 // on the other buffer's mbarrier, so the HBM stream of blocks never stops.
-// Thread (i, g): row i of direction g (all slices); the nine direction
-// partials of each (row, slice) are summed in shared memory.
-constexpr int SDB_NCD = 48, SDB_NDIR = 9, SDB_LS = 4, SDB_GROUPS = SDB_NDIR;
-constexpr int SDB_THREADS = SDB_NCD * SDB_GROUPS;
+// Thread (i, g): rows i and i + 24 of group g = (direction, half of the
+// columns), all slices, so every block value and input pair loaded from shared
+// memory feeds 8 or 16 complex multiply-adds; the 18 group partials of each
+// (row, slice) are summed in shared memory.
+constexpr int SDB_NCD = 48, SDB_NDIR = 9, SDB_LS = 4, SDB_GROUPS = 2 * SDB_NDIR;
+constexpr int SDB_THREADS = (SDB_NCD / 2) * SDB_GROUPS;
 struct SiteDbSmem {
     __half2 yb[2][SDB_NDIR * SDB_NCD * SDB_NCD];
     float2 vs[2][SDB_NDIR][SDB_LS][SDB_NCD];
@@ -532,7 +534,8 @@ __global__ void __launch_bounds__(SDB_THREADS, 1) k_coarse_site_db(const __half2
     SiteDbSmem& sm = *reinterpret_cast<SiteDbSmem*>(sdb_raw);
     const int Ls_c = p.Ls_c, nvec = p.nvec;
     const long long slice = p.Vc * SDB_NCD;
-    const int i = threadIdx.x % SDB_NCD, grp = threadIdx.x / SDB_NCD;   // grp = direction
+    const int i = threadIdx.x % (SDB_NCD / 2), grp = threadIdx.x / (SDB_NCD / 2);
+    const int dir = grp >> 1, jh = grp & 1;            // direction; columns [24 jh, 24 jh + 24)
     if (threadIdx.x == 0) {
         mbar_init(&sm.mbar[0], 1);
         mbar_init(&sm.mbar[1], 1);
@@ -551,29 +554,40 @@ __global__ void __launch_bounds__(SDB_THREADS, 1) k_coarse_site_db(const __half2
             if (nxt < p.Vc) mbar_wait_bounded(&sm.mbar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1), TILE_WAIT_NS);
             return;
         }
-        float2 a_lo[SDB_LS], a_hi[SDB_LS];
+        // acc[r][s]: row i + 24 r, slice s
+        float2 acc[2][SDB_LS];
 #pragma unroll
-        for (int s = 0; s < SDB_LS; ++s) { a_lo[s] = make_float2(0.f, 0.f); a_hi[s] = make_float2(0.f, 0.f); }
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int s = 0; s < SDB_LS; ++s) acc[r][s] = make_float2(0.f, 0.f);
         {
-            const int dir = grp;
             const __half2* yd = sm.yb[buf] + dir * SDB_NCD * SDB_NCD + i;
-#pragma unroll 4
-            for (int j = 0; j < SDB_NCD; ++j) {
-                const float2 y = __half22float2(yd[j * SDB_NCD]);
+            const int j0 = jh * (SDB_NCD / 2);
+#pragma unroll 2
+            for (int jj = 0; jj < SDB_NCD / 2; jj += 2) {
+                const int j = j0 + jj;
+                const float2 y00 = __half22float2(yd[j * SDB_NCD]);
+                const float2 y10 = __half22float2(yd[j * SDB_NCD + SDB_NCD / 2]);
+                const float2 y01 = __half22float2(yd[(j + 1) * SDB_NCD]);
+                const float2 y11 = __half22float2(yd[(j + 1) * SDB_NCD + SDB_NCD / 2]);
 #pragma unroll
                 for (int s = 0; s < SDB_LS; ++s) {
                     if (s < Ls_c) {
-                        const float2 v = sm.vs[buf][dir][s][j];
-                        if (j < nvec) a_lo[s] = cfma(y, v, a_lo[s]);
-                        else          a_hi[s] = cfma(y, v, a_hi[s]);
+                        const float4 v = *reinterpret_cast<const float4*>(&sm.vs[buf][dir][s][j]);
+                        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+                        acc[0][s] = cfma(y01, v1, cfma(y00, v0, acc[0][s]));
+                        acc[1][s] = cfma(y11, v1, cfma(y10, v0, acc[1][s]));
                     }
                 }
             }
         }
-        const float sj = dag ? -1.f : 1.f;                 // sigma_3 on the inputs
+        // sigma_3 on the inputs: the column half jh = 1 holds the chirality - inputs (nvec = 24)
+        const float sj = (dag && jh == 1) ? -1.f : 1.f;
 #pragma unroll
-        for (int s = 0; s < SDB_LS; ++s)
-            if (s < Ls_c) sm.part[grp][s][i] = make_float2(a_lo[s].x + sj * a_hi[s].x, a_lo[s].y + sj * a_hi[s].y);
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int s = 0; s < SDB_LS; ++s)
+                if (s < Ls_c) sm.part[grp][s][i + r * (SDB_NCD / 2)] = make_float2(sj * acc[r][s].x, sj * acc[r][s].y);
         __syncthreads();
         // epilogue: thread t < 48 * Ls_c forms output (row, slice)
         if (threadIdx.x < SDB_NCD * Ls_c) {
