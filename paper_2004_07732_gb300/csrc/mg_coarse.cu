@@ -7,6 +7,7 @@
 //   * truncated wall restriction / prolongation (Eq. TruncProjectInterpolate).
 // Coarse vectors are [s][coarse site][chirality][vec], complex64.
 #include "mg.cuh"
+#include "async_copy.cuh"
 
 namespace dwf {
 
@@ -192,39 +193,6 @@ template <class BT> __host__ __device__ constexpr unsigned site_block_bytes() { 
 
 __device__ __forceinline__ float2 to_f2(float2 a) { return a; }
 __device__ __forceinline__ float2 to_f2(__half2 a) { return __half22float2(a); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait on phase `parity`; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long budget_ns) {
-    const unsigned long long t0 = now_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (now_ns() - t0 > budget_ns) return false;
-    }
-    return true;
-}
 
 template <bool CG, class BT>
 __device__ __forceinline__ void tile_stage(TileSmemT<BT>& sm, const float2* __restrict__ in, const CoarseParams& p,
@@ -547,7 +515,8 @@ __global__ void __launch_bounds__(SDB_THREADS, 1) k_coarse_site_db(const __half2
         const int buf = k & 1;
         const long long nxt = xc + gridDim.x;
         if (threadIdx.x < 32 && nxt < p.Vc) sdb_issue(sm, buf ^ 1, B, in, p, (int)nxt);
-        if (!mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS)) {
+        const bool okw = mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS);
+        if (__syncthreads_or(!okw)) {                      // the whole block leaves together
             if (threadIdx.x == 0) atomicExch(status, 2);
             // let the copies in flight land before the block exits
             mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS);
@@ -1009,7 +978,8 @@ __device__ double pcg_apply(const PcgArgs& a, TileSmemT<float2>& sm, unsigned& p
         tile_issue_blocks(sm, B, p, x0, y0);
         tile_stage<true, float2>(sm, in, p, x0, y0);
         __syncthreads();
-        if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
+        const bool okw = mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
+        if (__syncthreads_or(!okw)) {                      // the whole block leaves together
             mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
             *ok = false;
             return nrm;
@@ -1431,7 +1401,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k_coarse_gcr_persistent(PgcrA
             tile_issue_blocks(sm, Y, p, x0, y0);
             pg_stage_axpy(sm, prevR, prevW, prevA, Rk, p, x0, y0, nrA);
             __syncthreads();
-            if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
+            const bool okw = mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
+            if (__syncthreads_or(!okw)) {                  // the whole block leaves together
                 mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
                 ok = false;
                 break;
@@ -1465,7 +1436,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k_coarse_gcr_persistent(PgcrA
             tile_issue_blocks(sm, Y, p, x0, y0);
             pg_stage(sm, a.t, p, x0, y0);
             __syncthreads();
-            if (!mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS)) {
+            const bool okw = mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
+            if (__syncthreads_or(!okw)) {                  // the whole block leaves together
                 mbar_wait_bounded(&sm.mbar, phase, TILE_WAIT_NS);
                 ok = false;
                 break;
