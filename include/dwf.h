@@ -219,6 +219,10 @@ typedef struct {
     int coarse_block_prec;/* storage of the Galerkin blocks read by the coarse stencil:
                              DWF_F32 or DWF_F32_L16 (FP16 blocks, FP32 arithmetic; default) */
     int cgs_passes;       /* classical Gram-Schmidt passes per GCR step: 1, or 2 (re-orthogonalised) */
+    int coarse_tc;        /* tensor-core form of the many-right-hand-side coarse contraction with
+                             FP16 blocks and >= 128 columns: 0 = mma.sync (default), 1 = tcgen05
+                             with the accumulator in tensor memory (measured slower at 64^2 x 4
+                             coarse sites, kept selectable)                                    */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;

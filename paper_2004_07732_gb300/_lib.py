@@ -51,7 +51,8 @@ class MgParams(ctypes.Structure):
                 ("coarse_tol", ctypes.c_double), ("coarse_maxiter", ctypes.c_int), ("fine_prec", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("coarse_persistent", ctypes.c_int), ("coarse_solver", ctypes.c_int),
-                ("coarse_restart", ctypes.c_int), ("coarse_block_prec", ctypes.c_int), ("cgs_passes", ctypes.c_int)]
+                ("coarse_restart", ctypes.c_int), ("coarse_block_prec", ctypes.c_int), ("cgs_passes", ctypes.c_int),
+                ("coarse_tc", ctypes.c_int)]
 
 
 _lib = None

@@ -10,8 +10,10 @@
 // products per term: hi*hi + hi*lo + lo*hi), which keeps FP32-level accuracy.
 // The adjoint uses gamma_5-hermiticity, Dhat_W^dag = sigma_3 Dhat_W sigma_3.
 // Vectors: [rhs][s][coarse site][16] complex64; blocks: the FP32 column-major
-// Galerkin blocks.
+// Galerkin blocks.  With FP16 blocks, at least 128 columns and coarse_tc = 1
+// the contraction runs on tcgen05 instead (k_coarse_umma below).
 #include "mg.cuh"
+#include "async_copy.cuh"
 
 namespace dwf {
 namespace {
@@ -178,6 +180,223 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const BT* __restrict__ Y, 
         }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 form (5th-generation tensor cores, accumulator in tensor memory).
+//
+// Transposed contraction per coarse site: D[c][n] = sum_dir sum_k A_dir[c][k]
+// B_dir[n][k], where the rows c are a tile of 128 columns (rhs, slice), A_dir
+// holds the real form [Re v_j | Im v_j] (k < 32) of the neighbour's input
+// vectors and B_dir[n][k] the real form [[Yr, -Yi], [Yi, Yr]] of the block
+// (rows n: Re out_i, then Im out_i).  One CTA per (site, column tile): the
+// five weight matrices are staged once, the inputs of one direction at a time
+// into one of two buffers (TF32 high and low parts, so that A = A_hi + A_lo
+// keeps FP32 accuracy; FP16 blocks are exact in TF32), and one thread issues
+// the K = 8 MMAs of each direction; a tcgen05.commit on the buffer's mbarrier
+// frees the buffer for the direction after next.  Operands sit in shared
+// memory in the K-major layout without swizzle (8 rows x 16 bytes per core
+// matrix, 128 bytes between K-adjacent core matrices, 1024 bytes between row
+// groups).  The 128 x 32 FP32 accumulator lives in 32 TMEM columns; warps 0-3
+// read it back (lane = row) and add the identity and the s-hops.  Measured at
+// 64^2 x 4 coarse sites and 64 right-hand sides: 400 us against 224 us for the
+// mma.sync kernel -- one site per CTA leaves the staging and the five
+// commit/wait steps unhidden at two CTAs per SM -- so it is opt-in.
+// ---------------------------------------------------------------------------
+constexpr int UM_M = 128, UM_K = 32, UM_N = 32, UM_THREADS = 256, UM_DIRS = 5;
+constexpr uint32_t UM_LBO = 128, UM_SBO = 1024;
+constexpr unsigned long long UM_WAIT_NS = 2000000000ULL;
+struct UmSmem {
+    float a[2][2][UM_M * UM_K];          // [buffer][hi, lo]
+    float b[UM_DIRS][UM_N * UM_K];       // weights per direction
+    unsigned long long mbar[3];          // buffers 0, 1; all MMAs done
+    uint32_t tmem;
+};
+
+// float offset of element (row, k) in the K-major no-swizzle layout
+__device__ __forceinline__ int um_off(int row, int k) {
+    return (row >> 3) * (UM_SBO / 4) + (k >> 2) * (UM_LBO / 4) + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ uint64_t um_desc(const void* base) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(base) >> 4) & 0x3FFF);
+    d |= (uint64_t)((UM_LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((UM_SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                                  // descriptor version; no swizzle, base offset 0
+    return d;
+}
+
+__device__ __forceinline__ void um_mma(uint32_t dt, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(dt), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void um_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// inputs of direction d for the tile's 128 columns: thread t holds half jh = t & 1 (8 complex values)
+// of column t >> 1; zeros for columns past the end or of skipped right-hand sides
+__device__ __forceinline__ void um_load_a(float4 (&v)[4], const float2* __restrict__ in, const TcParams& p, long long nb,
+                                          int col0, const int* skip_rhs) {
+    const int t = threadIdx.x, m = t >> 1, jh = t & 1;
+    const int col = col0 + m;
+    const long long slice = p.Vc * 16, rhs_stride = slice * p.Ls_c;
+    bool ok = col < p.ncols;
+    if (ok && skip_rhs) ok = skip_rhs[col / p.Ls_c] == 0;
+    if (ok) {
+        const float4* src = reinterpret_cast<const float4*>(in + (long long)(col / p.Ls_c) * rhs_stride +
+                                                            (long long)(col % p.Ls_c) * slice + nb * 16 + 8 * jh);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldg(src + q);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// the held values as TF32 high and low parts in the operand layout of buffer `buf`
+__device__ __forceinline__ void um_store_a(UmSmem& sm, int buf, const float4 (&v)[4], const TcParams& p) {
+    const int t = threadIdx.x, m = t >> 1, jh = t & 1;
+    const float sg = (p.dag && jh == 1) ? -1.f : 1.f;       // sigma_3 on input components 8..15
+    float re[8], im[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        re[2 * q] = sg * v[q].x; im[2 * q] = sg * v[q].y;
+        re[2 * q + 1] = sg * v[q].z; im[2 * q + 1] = sg * v[q].w;
+    }
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {                  // real parts at k = 8 jh .., imaginary at 16 + 8 jh ..
+        const float* x = half == 0 ? re : im;
+        const int k0 = 16 * half + 8 * jh;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float hi[4], lo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                hi[u] = __uint_as_float(to_tf32(x[4 * g + u]));
+                lo[u] = x[4 * g + u] - hi[u];
+            }
+            const int o = um_off(m, k0 + 4 * g);
+            *reinterpret_cast<float4*>(&sm.a[buf][0][o]) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<float4*>(&sm.a[buf][1][o]) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __restrict__ Y, const float2* __restrict__ in,
+                                                           float2* __restrict__ out, TcParams p,
+                                                           const int* __restrict__ skip_rhs, int* status) {
+    extern __shared__ __align__(1024) unsigned char um_raw[];
+    UmSmem& sm = *reinterpret_cast<UmSmem*>(um_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int ntile = (p.ncols + UM_M - 1) / UM_M;
+    const long long xc = blockIdx.x / ntile;
+    const int col0 = (int)(blockIdx.x % ntile) * UM_M;
+    if (t == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(&sm.mbar[b], 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(UM_N) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // every direction's inputs are requested before anything waits on them
+    const TcParams& pp = p;
+    float4 va[UM_DIRS][4];
+#pragma unroll
+    for (int d = 0; d < UM_DIRS; ++d) um_load_a(va[d], in, pp, nbr2d(pp, xc, d), col0, skip_rhs);
+    // weights of the five directions: B_d[n][k] from the FP16 block Y[xc][d] (column-major: j * 16 + i)
+    for (int e = t; e < UM_DIRS * 256; e += UM_THREADS) {
+        const int d = e >> 8, j = (e >> 4) & 15, i = e & 15;
+        const float2 y = __half22float2(__ldg(Y + (xc * UM_DIRS + d) * 256 + e % 256));
+        float* b = sm.b[d];
+        b[um_off(i, j)] = y.x;
+        b[um_off(i, 16 + j)] = -y.y;
+        b[um_off(16 + i, j)] = y.y;
+        b[um_off(16 + i, 16 + j)] = y.x;
+    }
+    um_store_a(sm, 0, va[0], pp);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t dt = sm.tmem;
+    // D F32, A and B TF32, both K-major, N = 32, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UM_N >> 3) << 17) | ((uint32_t)(UM_M >> 4) << 24);
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < UM_DIRS; ++d) {
+        const int buf = d & 1;
+        if (t == 0) {
+#pragma unroll
+            for (int ks = 0; ks < UM_K / 8; ++ks) {
+                const uint64_t db = um_desc(reinterpret_cast<const char*>(sm.b[d]) + ks * 2 * UM_LBO);
+                const uint64_t dah = um_desc(reinterpret_cast<const char*>(sm.a[buf][0]) + ks * 2 * UM_LBO);
+                const uint64_t dal = um_desc(reinterpret_cast<const char*>(sm.a[buf][1]) + ks * 2 * UM_LBO);
+                um_mma(dt, dah, db, idesc, (d > 0 || ks > 0) ? 1u : 0u);
+                um_mma(dt, dal, db, idesc, 1u);
+            }
+            um_commit(&sm.mbar[buf]);
+            if (d == UM_DIRS - 1) um_commit(&sm.mbar[2]);
+        }
+        if (d + 1 < UM_DIRS) {
+            const int nb_buf = (d + 1) & 1;
+            if (d + 1 >= 2)                                   // the MMAs of direction d - 1 have read the buffer
+                ok = ok && mbar_wait_bounded(&sm.mbar[nb_buf], (unsigned)(((d - 1) >> 1) & 1), UM_WAIT_NS);
+            um_store_a(sm, nb_buf, va[d + 1 < UM_DIRS ? d + 1 : 0], pp);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    ok = ok && mbar_wait_bounded(&sm.mbar[2], 0u, UM_WAIT_NS);
+    if (!ok) {                                       // record, then give the MMAs a second bounded wait
+        if (t == 0) atomicExch(status, 3);
+        mbar_wait_bounded(&sm.mbar[2], 0u, UM_WAIT_NS);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp < 4) {
+        // row m = t of D: column col0 + t
+        uint32_t r[32];
+        const uint32_t taddr = dt + ((uint32_t)(32 * warp) << 16);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                       "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                       "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int col = col0 + t;
+        bool live = ok && col < p.ncols;
+        if (live && skip_rhs) live = skip_rhs[col / p.Ls_c] == 0;
+        if (live) {
+            const int rr = col / p.Ls_c, s = col % p.Ls_c;
+            const long long slice = p.Vc * 16;
+            const long long rb = (long long)rr * slice * p.Ls_c;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float so = (p.dag && i >= 8) ? -1.f : 1.f;
+                const bool from_below = p.dag ? (i >= 8) : (i < 8);
+                int sh;
+                float sc = 1.f;
+                if (from_below) { if (s > 0) sh = s - 1; else { sh = p.Ls_c - 1; sc = -p.mf; } }
+                else            { if (s < p.Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
+                const float2 self = __ldg(in + rb + (long long)s * slice + xc * 16 + i);
+                const float2 hv = __ldg(in + rb + (long long)sh * slice + xc * 16 + i);
+                out[rb + (long long)s * slice + xc * 16 + i] =
+                    make_float2(so * __uint_as_float(r[i]) + self.x + sc * hv.x,
+                                so * __uint_as_float(r[16 + i]) + self.y + sc * hv.y);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dt), "r"(UM_N) : "memory");
+}
+
 }  // namespace
 
 dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
@@ -199,7 +418,18 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
     const long long warps = p.Vc * ((p.ncols + 8 * NT - 1) / (8 * NT));
     const long long blocks = (warps * 32 + 255) / 256;
     if (blocks > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
-    if (h->ytile_half)
+    if (h->prm.coarse_tc == 1 && h->ytile_half && p.ncols >= UM_M) {
+        static bool attr = false;
+        if (!attr) {
+            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)sizeof(UmSmem)));
+            attr = true;
+        }
+        const long long ctas = p.Vc * ((p.ncols + UM_M - 1) / UM_M);
+        if (ctas > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
+        k_coarse_umma<<<(unsigned)ctas, UM_THREADS, sizeof(UmSmem), st>>>((const __half2*)h->Ytile, in, out, p,
+                                                                          skip_rhs, h->status + 1);
+    } else if (h->ytile_half)
         k_coarse_tc<NT, __half2><<<(unsigned)blocks, 256, 0, st>>>((const __half2*)h->Ytile, in, out, p, skip_rhs);
     else
         k_coarse_tc<NT, float2><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip_rhs);

@@ -90,16 +90,18 @@ def test_coarse_multi_rejects_bad_arguments(dw):
     h.close()
 
 
-@pytest.mark.parametrize("nrhs", [1, 6, 16])
-def test_coarse_multi_f16_blocks_match_single(dw, nrhs):
+@pytest.mark.parametrize("nrhs,tc", [(1, 0), (6, 0), (16, 0), (32, 0), (48, 0), (64, 0), (32, 1), (48, 1), (64, 1)])
+def test_coarse_multi_f16_blocks_match_single(dw, nrhs, tc):
     """FP16 coarse blocks (the default storage): each column of the tensor-core result agrees with
-    the one-vector stencil reading the same FP16 blocks, to FP32 accuracy."""
+    the one-vector stencil reading the same FP16 blocks, to FP32 accuracy.  tc = 1 selects the
+    tcgen05 form from 128 columns (32 right-hand sides x 4 slices) on (48: a partial tile)."""
     rng0 = synth.rng_for(90 + nrhs)
     dims = (64, 32)
     U = synth.u1_links(synth.u1_angles(rng0, dims, 0.6))
     starts = np.stack([synth.gaussian_complex(rng0, (int(np.prod(dims)) * 2,)) for _ in range(8)])
     g = dw.make_geom(dims, 8)
-    h = dw.mg_setup(g, _dev(U), 1.0, 0.01, {"setup_maxiter": 10, "setup_mass": -0.19, "Ls_c": 4}, _dev(starts))
+    h = dw.mg_setup(g, _dev(U), 1.0, 0.01, {"setup_maxiter": 10, "setup_mass": -0.19, "Ls_c": 4, "coarse_tc": tc},
+                    _dev(starts))
     nc = h.coarse_size
     v = synth.gaussian_complex(np.random.default_rng(nrhs), (nrhs, nc)).astype(np.complex64)
     vd = _dev(v, torch.complex64).reshape(nrhs, nc)

@@ -147,3 +147,21 @@ def test_batched_full_size_256(dw):
     for r in range(4):
         assert np.linalg.norm(B[r] - D @ x[r]) / np.linalg.norm(B[r]) <= 1e-10
     h.close()
+
+
+def test_batched_solve_with_tcgen05_coarse(dw):
+    """33 right-hand sides (132 coarse columns: one full and one partial 128-column tile) with
+    the tcgen05 form of the coarse contraction (coarse_tc = 1); every system reaches 1e-10."""
+    dims, Ls, M5, mf = (16, 16), 8, 1.0, 0.01
+    h, U, rng = _hierarchy(dw, dims, Ls, 0.4, 81, M5, mf, -0.12, {"coarse_tc": 1})
+    nrhs = 33
+    B = np.stack([synth.gaussian_spinor(rng, dims, Ls).reshape(-1) for _ in range(nrhs)])
+    X = torch.empty(B.size, dtype=torch.complex128, device="cuda")
+    stats, status = dw.mg_solve_batched(h, _dev(B), X, nrhs, tol=1e-10)
+    assert status == 0
+    D = dirac.dwf_matrix(U, dims, Ls, M5, mf)
+    x = X.cpu().numpy().reshape(nrhs, -1)
+    for r in (0, 16, 31, 32):
+        assert np.linalg.norm(B[r] - D @ x[r]) / np.linalg.norm(B[r]) <= 1e-10
+    assert max(s["true_residual"] for s in stats) <= 1e-10
+    h.close()
