@@ -92,6 +92,20 @@ DWF_API dwf_status dwf_convert_links(const dwf_geom* g, const void* U64, void* U
 DWF_API dwf_status dwf_apply(const dwf_geom* g, const void* U, const void* psi, void* out,
                      double M5, double mf, int dagger, int prec, void* stream);
 
+/* D_DW(mf) psi (or its adjoint) for spinors that live in host memory (2-d).
+ * psi_host / out_host: host spinors in the canonical layout (pinned memory
+ * lets the copies overlap); U_host: links already in the storage of `prec`
+ * (as dwf_convert_links writes them).  U_dev, psi_dev, out_dev: caller-owned
+ * device buffers of the link and spinor sizes, used as staging.  The copy in,
+ * the apply and the copy back are pipelined over `nchunks` ranges of s-slices
+ * (<= 0: 4) on library streams; the call is ordered on `stream`: out_host is
+ * complete once `stream` reaches this point.  Same errors as dwf_apply;
+ * DWF_ERR_UNSUPPORTED for 4-d lattices.  Calls from several host threads on
+ * one device are serialised. */
+DWF_API dwf_status dwf_apply_host(const dwf_geom* g, const void* U_host, const void* psi_host, void* out_host,
+                                  void* U_dev, void* psi_dev, void* out_dev, double M5, double mf, int dagger,
+                                  int prec, int nchunks, void* stream);
+
 /* Batched apply: out_r = D_DW(mf) psi_r (or the adjoint) for nrhs right-hand
  * sides, each on its own 2-d U(1) lattice geoms[r] with links U[r] (pointers may
  * repeat), all in ONE persistent kernel launch over the concatenated site

@@ -93,6 +93,7 @@ def _setup_signatures(L):
         "dwf_apply_batched": [_I, ctypes.POINTER(Geom), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                               ctypes.POINTER(_VP), _D, _D, _I, _I, _VP],
         "dwf_check_wait_timeout": [_I, _D, _VP],
+        "dwf_apply_host": [G, _VP, _VP, _VP, _VP, _VP, _VP, _D, _D, _I, _I, _I, _VP],
         "dwf_links_from_angles": [G, _VP, _VP, _VP],
         "dwf_gamma5_reflect": [G, _VP, _VP, _I, _VP],
         "dwf_link_force": [G, _VP, _VP, _VP, _VP, _VP],
@@ -259,6 +260,24 @@ def dwf_apply_batched(geoms, Us, psis, outs, M5, mf, dagger=False, prec="f32_l16
     O = (_VP * n)(*[o.data_ptr() for o in outs])
     check(lib().dwf_apply_batched(n, G, U, P, O, float(M5), float(mf), int(bool(dagger)), PREC[prec], _stream(stream)))
     return outs
+
+
+def dwf_apply_host(geom, U_host, psi_host, out_host, U_dev, psi_dev, out_dev, M5, mf, dagger=False,
+                   prec="f32_l16", nchunks=0, stream=None):
+    """D_DW on host spinors: copies in, applies and copies back, pipelined over s-chunks.
+
+    U_host holds the links in the storage of `prec`; the *_dev tensors are device staging
+    buffers of the same sizes.  Returns once the work is ordered on `stream`."""
+    for t, nm in ((psi_host, "psi_host"), (out_host, "out_host")):
+        if t.is_cuda or not t.is_contiguous() or t.dtype != spinor_dtype(prec) or t.numel() != spinor_size(geom):
+            raise ValueError(f"{nm} must be a contiguous host tensor of the spinor size and precision")
+    _check_spinor(psi_dev, geom, prec, "psi_dev")
+    _check_spinor(out_dev, geom, prec, "out_dev")
+    if U_host.is_cuda or not U_dev.is_cuda or U_host.numel() * U_host.element_size() != U_dev.numel() * U_dev.element_size():
+        raise ValueError("U_host (host) and U_dev (device) must be link buffers of the same size")
+    check(lib().dwf_apply_host(ctypes.byref(geom), ctypes.c_void_p(U_host.data_ptr()), ctypes.c_void_p(psi_host.data_ptr()),
+                               ctypes.c_void_p(out_host.data_ptr()), _ptr(U_dev), _ptr(psi_dev), _ptr(out_dev),
+                               float(M5), float(mf), int(bool(dagger)), PREC[prec], int(nchunks), _stream(stream)))
 
 
 def check_wait_timeout(which=0, seconds=0.05, stream=None) -> int:

@@ -169,6 +169,8 @@ dwf_status dwf_apply_batched(int nrhs, const dwf_geom* geoms, const void* const*
             p.diag = (double)G.nd - M5 + 1.0;
             p.mf = mf;
             p.s_chunk = G.Ls;
+            p.s_base = 0;
+            p.s_end = G.Ls;
             args.d[k].U = U[r0 + k];
             args.d[k].psi = psi[r0 + k];
             args.d[k].out = out[r0 + k];

@@ -166,9 +166,9 @@ k_dwf2d(const typename LT::store* __restrict__ U, const Sp2<R>* __restrict__ psi
         Fine2dParams p) {
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.V) return;
-    const int s0 = blockIdx.y * p.s_chunk;
-    if (s0 >= p.Ls) return;
-    dwf2d_site<LT, R, DAG, PF>(U, psi, out, p, site, s0, min(s0 + p.s_chunk, p.Ls));
+    const int s0 = p.s_base + blockIdx.y * p.s_chunk;
+    if (s0 >= p.s_end) return;
+    dwf2d_site<LT, R, DAG, PF>(U, psi, out, p, site, s0, min(s0 + p.s_chunk, p.s_end));
 }
 
 // nrhs right-hand sides on the same lattice and links, stored back to back
@@ -244,11 +244,15 @@ dwf_status fine_apply_2d_batched(const BatchArgs2d& a, bool dagger, int prec, cu
     return DWF_OK;
 }
 
+dwf_status fine_apply_2d_range(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                               bool dagger, int prec, int s_lo, int s_hi, cudaStream_t st, int s_chunk);
+
 template <class LT, class R>
 static void launch2d(const void* U, const void* psi, void* out, const Fine2dParams& p, bool dagger,
                      cudaStream_t st) {
     const int threads = 256;
-    dim3 grid((unsigned)((p.V + threads - 1) / threads), (unsigned)((p.Ls + p.s_chunk - 1) / p.s_chunk));
+    dim3 grid((unsigned)((p.V + threads - 1) / threads),
+              (unsigned)((p.s_end - p.s_base + p.s_chunk - 1) / p.s_chunk));
     auto Ut = reinterpret_cast<const typename LT::store*>(U);
     auto pi = reinterpret_cast<const Sp2<R>*>(psi);
     auto po = reinterpret_cast<Sp2<R>*>(out);
@@ -272,7 +276,20 @@ int choose_s_chunk(long long V, int Ls) {
 
 dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                          bool dagger, int prec, int s_chunk, cudaStream_t st) {
+    return fine_apply_2d_range(g, U, psi, out, M5, mf, dagger, prec, 0, g.Ls, st, s_chunk);
+}
+
+dwf_status fine_apply_2d_range(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                               bool dagger, int prec, int s_lo, int s_hi, cudaStream_t st) {
+    return fine_apply_2d_range(g, U, psi, out, M5, mf, dagger, prec, s_lo, s_hi, st, 0);
+}
+
+dwf_status fine_apply_2d_range(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                               bool dagger, int prec, int s_lo, int s_hi, cudaStream_t st, int s_chunk) {
+    if (s_lo < 0 || s_hi > g.Ls || s_lo >= s_hi) { set_error("bad slice range [%d, %d)", s_lo, s_hi); return DWF_ERR_ARG; }
     Fine2dParams p;
+    p.s_base = s_lo;
+    p.s_end = s_hi;
     p.V = g.V;
     p.L0 = g.L[0];
     p.L1 = g.L[1];
@@ -281,7 +298,7 @@ dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* ou
     p.anti1 = g.anti[1];
     p.diag = (double)g.nd - M5 + 1.0;
     p.mf = mf;
-    p.s_chunk = s_chunk > 0 ? s_chunk : choose_s_chunk(g.V, g.Ls);
+    p.s_chunk = s_chunk > 0 ? s_chunk : choose_s_chunk(g.V, s_hi - s_lo);
     switch (prec) {
         case DWF_F64:      launch2d<LinkF64, double>(U, psi, out, p, dagger, st); break;
         case DWF_F32:      launch2d<LinkF32, float>(U, psi, out, p, dagger, st); break;
@@ -307,6 +324,8 @@ dwf_status fine_apply_2d_multi(const Geom& g, const void* U, const void* psi, vo
     p.diag = (double)g.nd - M5 + 1.0;
     p.mf = mf;
     p.s_chunk = choose_s_chunk(g.V * nrhs, g.Ls);
+    p.s_base = 0;
+    p.s_end = g.Ls;
     switch (prec) {
         case DWF_F64:       launch2d_multi<LinkF64, double>(U, psi, out, p, nrhs, skip, dagger, st); break;
         case DWF_F32:       launch2d_multi<LinkF32, float>(U, psi, out, p, nrhs, skip, dagger, st); break;

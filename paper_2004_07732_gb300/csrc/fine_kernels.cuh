@@ -12,6 +12,7 @@ struct Fine2dParams {
     double diag;   // d - M5 + 1
     double mf;
     int s_chunk;
+    int s_base, s_end;   // slices [s_base, s_end) written by k_dwf2d (0, Ls for the whole operator)
 };
 
 struct Fine4dParams {
@@ -54,6 +55,10 @@ dwf_status fine_apply_2d(const Geom& g, const void* U, const void* psi, void* ou
 // right-hand-side device flags (may be null), nonzero leaves that output untouched.
 dwf_status fine_apply_2d_multi(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                                bool dagger, int prec, int nrhs, const int* skip, cudaStream_t st);
+// out slices [s_lo, s_hi) of D_DW(mf) psi (psi must hold slices s_lo - 1 .. s_hi and, for the
+// walls, 0 and Ls - 1); 2-d only
+dwf_status fine_apply_2d_range(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                               bool dagger, int prec, int s_lo, int s_hi, cudaStream_t st);
 dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                          bool dagger, int prec, int s_chunk, cudaStream_t st);
 
