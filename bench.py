@@ -621,6 +621,7 @@ def time_coarse_multi(dw, dev, nrhs=64, reps=20):
         return a.elapsed_time(b) * 1e-3 / reps
 
     t_tc = timed(lambda: dw.mg_coarse_apply_multi(mg, vin, vout, nrhs, mf))
+    form = dw.mg_coarse_tc_form(mg, nrhs)
 
     def singles():
         for r in range(nrhs):
@@ -629,6 +630,8 @@ def time_coarse_multi(dw, dev, nrhs=64, reps=20):
     dw.mg_destroy(mg)
     return {"workload": f"{wl.name} hierarchy (default FP16 blocks), coarse D_DW(m) on {nrhs} vectors",
             "nrhs": nrhs, "coarse_sites": Vc, "Ls_c": Ls_c, "useful_flops": flops, "algorithmic_bytes": nbytes,
+            "autotuned_form": {1: "mma.sync, 1 tile/warp", 2: "mma.sync, 2 tiles/warp", 4: "mma.sync, 4 tiles/warp",
+                               256: "tcgen05"}.get(form, str(form)),
             "tensor_core_ms": t_tc * 1e3, "tensor_core_TFLOPs": flops / t_tc / 1e12,
             "tensor_core_GBps": nbytes / t_tc / 1e9, "per_vector_launches_ms": t_one * 1e3,
             "speedup": t_one / t_tc}

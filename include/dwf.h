@@ -233,10 +233,11 @@ typedef struct {
     int coarse_block_prec;/* storage of the Galerkin blocks read by the coarse stencil:
                              DWF_F32 or DWF_F32_L16 (FP16 blocks, FP32 arithmetic; default) */
     int cgs_passes;       /* classical Gram-Schmidt passes per GCR step: 1, or 2 (re-orthogonalised) */
-    int coarse_tc;        /* tensor-core form of the many-right-hand-side coarse contraction with
-                             FP16 blocks and >= 128 columns: 0 = mma.sync (default), 1 = tcgen05
-                             with the accumulator in tensor memory (measured slower at 64^2 x 4
-                             coarse sites, kept selectable)                                    */
+    int coarse_tc;        /* form of the many-right-hand-side coarse contraction: 0 (default) =
+                             autotuned -- the first use for a given nrhs times mma.sync with 1, 2
+                             and 4 column tiles per warp and, with FP16 blocks and >= 128
+                             columns, tcgen05 with the accumulator in tensor memory, and keeps
+                             the fastest; 1 = tcgen05 wherever eligible                        */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;
@@ -306,9 +307,16 @@ DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, d
  * nrhs * Ls_c columns, evaluated with mma.sync TF32 products of FP32 data split
  * into high and low parts (FP32-level accuracy), FP32 accumulation.  The
  * blocks are the handle's coarse block storage (coarse_block_prec), as for
- * mg_coarse_apply.  2-d, 16 coarse dof. */
+ * mg_coarse_apply.  With coarse_tc = 0 the first call for a new nrhs times the
+ * candidate forms (using in and out as scratch, synchronising `stream`) and
+ * keeps the fastest.  2-d, 16 coarse dof. */
 DWF_API dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
                                          int dagger, void* stream);
+
+/* The form the autotuner chose for nrhs right-hand sides: 1, 2 or 4 (mma.sync
+ * with that many 8-column tiles per warp) or 256 (tcgen05); 0 before the first
+ * tuned call for that nrhs. */
+DWF_API int mg_coarse_tc_form(const dwf_mg* h, int nrhs);
 
 /* Batched K-cycle: nrhs right-hand sides that share the hierarchy h (one
  * gauge field) solved together (the multi-right-hand-side form of the solve

@@ -110,6 +110,7 @@ def _setup_signatures(L):
         "mg_prolong": [_VP, _VP, _VP, _VP],
         "mg_coarse_apply": [_VP, _VP, _VP, _D, _I, _VP],
         "mg_coarse_apply_multi": [_VP, _I, _VP, _VP, _D, _I, _VP],
+        "mg_coarse_tc_form": [_VP, _I],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -491,3 +492,8 @@ def mg_coarse_apply_multi(mg: Multigrid, vin, vout, nrhs, mf, dagger=False, stre
     check(lib().mg_coarse_apply_multi(mg.ptr, int(nrhs), _ptr(vin), _ptr(vout), float(mf), int(bool(dagger)),
                                       _stream(stream)))
     return vout
+
+
+def mg_coarse_tc_form(mg: Multigrid, nrhs) -> int:
+    """Form of the coarse contraction the autotuner chose for nrhs (0: not tuned yet)."""
+    return int(lib().mg_coarse_tc_form(mg.ptr, int(nrhs)))

@@ -1,6 +1,7 @@
 // Internal structures of the two-level domain-wall multigrid (Sec. 2.3).
 #pragma once
 
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -65,6 +66,7 @@ struct dwf_mg {
     cudaGraphExec_t coarse_graph_cycle;   // captured coarse GCR: one restart cycle
     cudaStream_t cap_stream;              // private stream used only to record graphs
     void* batched;                        // workspace and graphs of the batched solver (mg_batched.cu)
+    mutable std::map<int, int> tc_choice; // autotuned form of the many-right-hand-side coarse contraction, by nrhs
 };
 
 namespace dwf {
@@ -80,6 +82,11 @@ dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st);
 // skip_rhs: per right-hand-side device flags (may be null)
 dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
                                  const int* skip_rhs, cudaStream_t st);
+// Autotuner of that contraction: times every eligible form (mma.sync with 1, 2 or 4
+// column tiles of 8 per warp; tcgen05 with FP16 blocks from 128 columns) on in -> out
+// (scratch: contents are overwritten) and keeps the fastest for nrhs.  Synchronises
+// `st`; must not run during stream capture.  No-op once nrhs is tuned.
+dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* out, cudaStream_t st);
 // one-time kernel attributes of the coarse stencil (outside any stream capture)
 dwf_status coarse_init_attributes();
 // Wall transfers (Eq. TruncProjectInterpolate) on nrhs vectors stored back to

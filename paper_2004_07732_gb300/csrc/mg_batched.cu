@@ -620,6 +620,8 @@ static dwf_status bcoarse_solve(BSolver& s, int* citers_out) {
         return DWF_OK;
     }
     if (!bs->gfirst) {
+        // the contraction's form is chosen by timing, before it is frozen into the graphs
+        if (s.nrhs > 1 && h->prm.coarse_tc == 0) DWF_TRY(coarse_tc_tune(h, s.nrhs, v.Zc[0], v.ct, s.st));
         DWF_TRY(bcapture(s, true, &bs->gfirst));
         DWF_TRY(bcapture(s, false, &bs->gcycle));
         bs->gnrhs = s.nrhs;

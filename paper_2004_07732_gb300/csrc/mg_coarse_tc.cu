@@ -382,26 +382,14 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
 
 }  // namespace
 
-dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
-                                 const int* skip_rhs, cudaStream_t st) {
-    if (h->mg.nd != 2 || h->mg.ncd != 16) {
-        set_error("the tensor-core coarse stencil supports 2-d lattices with 16 coarse dof");
-        return DWF_ERR_UNSUPPORTED;
-    }
-    TcParams p;
-    p.Vc = h->mg.Vc;
-    p.Lc0 = h->mg.Lc[0];
-    p.Lc1 = h->mg.Lc[1];
-    p.Ls_c = h->mg.Ls_c;
-    p.nrhs = nrhs;
-    p.ncols = nrhs * h->mg.Ls_c;
-    p.mf = (float)mf;
-    p.dag = dagger ? 1 : 0;
-    constexpr int NT = 4;
-    const long long warps = p.Vc * ((p.ncols + 8 * NT - 1) / (8 * NT));
-    const long long blocks = (warps * 32 + 255) / 256;
-    if (blocks > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
-    if (h->prm.coarse_tc == 1 && h->ytile_half && p.ncols >= UM_M) {
+// forms of the contraction: 1, 2, 4 = mma.sync with that many column tiles per warp; TC_UMMA = tcgen05
+constexpr int TC_UMMA = 0x100;
+
+static bool umma_eligible(const dwf_mg* h, int ncols) { return h->ytile_half && ncols >= UM_M; }
+
+static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, const float2* in, float2* out,
+                              const int* skip_rhs, cudaStream_t st) {
+    if (form == TC_UMMA) {
         static bool attr = false;
         if (!attr) {
             DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -412,12 +400,83 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
         if (ctas > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
         k_coarse_umma<<<(unsigned)ctas, UM_THREADS, sizeof(UmSmem), st>>>((const __half2*)h->Ytile, in, out, p,
                                                                           skip_rhs, h->status + 1);
-    } else if (h->ytile_half)
-        k_coarse_tc<NT, __half2><<<(unsigned)blocks, 256, 0, st>>>((const __half2*)h->Ytile, in, out, p, skip_rhs);
-    else
-        k_coarse_tc<NT, float2><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip_rhs);
+        DWF_CHECK_LAUNCH();
+        return DWF_OK;
+    }
+    const int NT = form;
+    const long long warps = p.Vc * ((p.ncols + 8 * NT - 1) / (8 * NT));
+    const long long blocks = (warps * 32 + 255) / 256;
+    if (blocks > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
+#define DWF_TC_LAUNCH(N)                                                                                              \
+    if (h->ytile_half)                                                                                                 \
+        k_coarse_tc<N, __half2><<<(unsigned)blocks, 256, 0, st>>>((const __half2*)h->Ytile, in, out, p, skip_rhs);   \
+    else                                                                                                               \
+        k_coarse_tc<N, float2><<<(unsigned)blocks, 256, 0, st>>>(h->Y32, in, out, p, skip_rhs);
+    if (NT == 1) { DWF_TC_LAUNCH(1) }
+    else if (NT == 2) { DWF_TC_LAUNCH(2) }
+    else { DWF_TC_LAUNCH(4) }
+#undef DWF_TC_LAUNCH
     DWF_CHECK_LAUNCH();
     return DWF_OK;
+}
+
+static TcParams tc_params(const dwf_mg* h, int nrhs, double mf, bool dagger) {
+    TcParams p;
+    p.Vc = h->mg.Vc;
+    p.Lc0 = h->mg.Lc[0];
+    p.Lc1 = h->mg.Lc[1];
+    p.Ls_c = h->mg.Ls_c;
+    p.nrhs = nrhs;
+    p.ncols = nrhs * h->mg.Ls_c;
+    p.mf = (float)mf;
+    p.dag = dagger ? 1 : 0;
+    return p;
+}
+
+dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* out, cudaStream_t st) {
+    if (h->mg.nd != 2 || h->mg.ncd != 16 || nrhs < 1) return DWF_OK;
+    if (h->tc_choice.count(nrhs)) return DWF_OK;
+    const TcParams p = tc_params(h, nrhs, h->mf, false);
+    int forms[4] = {1, 2, 4, 0};
+    int nforms = 3;
+    if (umma_eligible(h, p.ncols)) forms[nforms++] = TC_UMMA;
+    cudaEvent_t a, b;
+    DWF_CHECK_CUDA(cudaEventCreate(&a));
+    DWF_CHECK_CUDA(cudaEventCreate(&b));
+    int best = 4;
+    float best_ms = 1e30f;
+    dwf_status status = DWF_OK;
+    for (int f = 0; f < nforms && status == DWF_OK; ++f) {
+        for (int w = 0; w < 2 && status == DWF_OK; ++w) status = launch_form(h, forms[f], p, in, out, nullptr, st);
+        if (status != DWF_OK) break;
+        cudaEventRecord(a, st);
+        for (int r = 0; r < 5 && status == DWF_OK; ++r) status = launch_form(h, forms[f], p, in, out, nullptr, st);
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) { set_error("autotuner timing failed"); status = DWF_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) { best_ms = ms; best = forms[f]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (status == DWF_OK) h->tc_choice[nrhs] = best;
+    return status;
+}
+
+dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
+                                 const int* skip_rhs, cudaStream_t st) {
+    if (h->mg.nd != 2 || h->mg.ncd != 16) {
+        set_error("the tensor-core coarse stencil supports 2-d lattices with 16 coarse dof");
+        return DWF_ERR_UNSUPPORTED;
+    }
+    const TcParams p = tc_params(h, nrhs, mf, dagger);
+    int form = 4;
+    if (h->prm.coarse_tc == 1 && umma_eligible(h, p.ncols)) form = TC_UMMA;
+    else if (h->prm.coarse_tc == 0) {
+        auto it = h->tc_choice.find(nrhs);
+        if (it != h->tc_choice.end()) form = it->second;
+    }
+    return launch_form(h, form, p, in, out, skip_rhs, st);
 }
 
 }  // namespace dwf
@@ -430,5 +489,14 @@ extern "C" dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const voi
     if (!h || !in || !out) { set_error("NULL argument"); return DWF_ERR_ARG; }
     if (nrhs < 1) { set_error("nrhs must be >= 1"); return DWF_ERR_ARG; }
     if (in == out) { set_error("in and out must be distinct buffers"); return DWF_ERR_ARG; }
-    return coarse_apply_multi_tc(h, nrhs, (const float2*)in, (float2*)out, mf, dagger != 0, nullptr, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    // the first call for a new nrhs picks the fastest form of the contraction (using in / out as scratch)
+    if (h->prm.coarse_tc == 0) DWF_TRY(coarse_tc_tune(h, nrhs, (const float2*)in, (float2*)out, st));
+    return coarse_apply_multi_tc(h, nrhs, (const float2*)in, (float2*)out, mf, dagger != 0, nullptr, st);
+}
+
+extern "C" int mg_coarse_tc_form(const dwf_mg* h, int nrhs) {
+    if (!h) return 0;
+    auto it = h->tc_choice.find(nrhs);
+    return it == h->tc_choice.end() ? 0 : it->second;
 }

@@ -107,8 +107,11 @@ def test_coarse_multi_f16_blocks_match_single(dw, nrhs, tc):
     vd = _dev(v, torch.complex64).reshape(nrhs, nc)
     out = torch.empty_like(vd)
     one = torch.empty(nc, dtype=torch.complex64, device="cuda")
+    assert dw.mg_coarse_tc_form(h, nrhs) == 0
     for m, dag in ((0.01, False), (1.0, True), (0.01, True)):
         dw.mg_coarse_apply_multi(h, vd, out, nrhs, m, dagger=dag)
+        form = dw.mg_coarse_tc_form(h, nrhs)
+        assert form in ((1, 2, 4, 256) if tc == 0 else (0,)) and (form != 256 or nrhs * 4 >= 128)
         for r in range(nrhs):
             dw.mg_coarse_apply(h, vd[r].contiguous(), one, m, dagger=dag)
             assert (torch.linalg.norm(out[r] - one) / torch.linalg.norm(one)).item() < 1e-5
