@@ -174,6 +174,37 @@ def test_apply_host_pipelined(dw, dims, Ls, anti, prec, dagger, nchunks):
         assert torch.equal(out_h, want.cpu())
 
 
+def test_bench_size_apply_sampled(dw):
+    """The bench's workload (1024x1024 x Ls=16, FP32 spinors, FP16 links), both the device apply
+    and the host-spinor apply with 16 s-chunks as the bench calls them: point checks against the
+    definition, and the two paths bit for bit."""
+    wl = synth.SCHWINGER_1024
+    U, srcs = wl.draw(1)
+    psi = srcs[0]
+    g = dw.make_geom(wl.dims, wl.Ls)
+    Ud = dw.links_to(g, _dev(U), "f32_l16")
+    pd = _dev(psi, torch.complex64)
+    out = torch.empty_like(pd)
+    dw.dwf_apply(g, Ud, pd, out, wl.M5, wl.mf, prec="f32_l16")
+    psi_h = pd.cpu().pin_memory()
+    out_h = torch.empty_like(psi_h).pin_memory()
+    dw.dwf_apply_host(g, Ud.cpu().pin_memory(), psi_h, out_h, torch.empty_like(Ud), torch.empty_like(pd),
+                      torch.empty_like(pd), wl.M5, wl.mf, prec="f32_l16", nchunks=16)
+    torch.cuda.synchronize()
+    got = out.cpu()
+    assert torch.equal(out_h, got)
+    got = got.numpy().reshape(wl.Ls, wl.V, 2)
+    rng = np.random.default_rng(3)
+    L0 = wl.dims[0]
+    pts = [(int(rng.integers(0, wl.Ls)), int(rng.integers(0, wl.V))) for _ in range(150)]
+    pts += [(0, 0), (wl.Ls - 1, wl.V - 1), (0, wl.V - 1), (wl.Ls - 1, 0), (7, L0 - 1), (8, wl.V - L0)]
+    Uo = _rounded_links(U, "f32_l16")
+    ps = psi.astype(np.complex64).astype(np.complex128)
+    want = dirac.dwf_apply_points_2d(Uo, ps, wl.dims, wl.Ls, wl.M5, wl.mf, pts)
+    g_pts = np.array([got[s, site] for s, site in pts])
+    assert np.abs(g_pts - want).max() < 1e-5 * np.abs(want).max()
+
+
 def test_cgne_solve_reaches_tolerance(dw):
     """FP64 GPU CGNR on the 32x32 x Ls=8 workload reaches 1e-10 and the oracle's solution."""
     wl = synth.SCHWINGER_32

@@ -165,3 +165,32 @@ def test_batched_solve_with_tcgen05_coarse(dw):
         assert np.linalg.norm(B[r] - D @ x[r]) / np.linalg.norm(B[r]) <= 1e-10
     assert max(s["true_residual"] for s in stats) <= 1e-10
     h.close()
+
+
+def test_bench_batch_all_sources(dw):
+    """The bench's batched workload as the bench runs it: 64 sources over {64^2, 128^2, 256^2} x 16
+    (one hierarchy per size class, the classes solved concurrently); every source reaches 1e-10,
+    recomputed by the oracle."""
+    setup_mass = -0.3        # sigma 0.7
+    hs, Bs, Xs, ns, mats = [], [], [], [], []
+    for wl, nsrc in synth.batched_classes():
+        U, srcs = wl.draw(nsrc)
+        g = dw.make_geom(wl.dims, wl.Ls)
+        rng = synth.rng_for(wl.seed + 7000)
+        starts = np.stack([synth.gaussian_complex(rng, (wl.V * 2,)) for _ in range(8)])
+        hs.append(dw.mg_setup(g, _dev(U), wl.M5, wl.mf, {"setup_mass": setup_mass}, _dev(starts)))
+        B = np.stack([x.reshape(-1) for x in srcs])
+        Bs.append(B)
+        Xs.append(torch.empty(B.size, dtype=torch.complex128, device="cuda"))
+        ns.append(nsrc)
+        mats.append(dirac.dwf_matrix(U, wl.dims, wl.Ls, wl.M5, wl.mf))
+    stats, status = dw.mg_solve_groups(hs, [_dev(B) for B in Bs], Xs, ns, tol=1e-10)
+    assert status == 0 and sum(ns) == 64
+    for B, X, D, st in zip(Bs, Xs, mats, stats):
+        x = X.cpu().numpy().reshape(len(B), -1)
+        R = (B - (D @ x.T).T)
+        res = np.linalg.norm(R, axis=1) / np.linalg.norm(B, axis=1)
+        assert res.max() <= 1e-10
+        assert np.abs(res - np.array([s["true_residual"] for s in st])).max() < 1e-12
+    for h in hs:
+        h.close()
