@@ -112,3 +112,34 @@ def test_mg_solve_4d_reaches_tolerance(dw, nvec):
     res = np.linalg.norm(b - D @ x.cpu().numpy()) / np.linalg.norm(b)
     assert status == 0 and res <= 1e-10 and abs(res - stats["true_residual"]) < 1e-12
     h.close()
+
+
+def test_mg_solve_4d_bench_size(dw):
+    """The bench's 4-d workload (16^3 x 32 x Ls=16, eps 0.3, M5 1.8, m 0.01; Nvec 24 on 2^4 blocks,
+    16 post-smoothing steps, coarse tolerance 0.4) reaches 1e-10.  The residual b - D x is
+    recomputed with the FP64 GPU apply (itself held to the oracle at 1e-12) and, at sampled
+    points, with the oracle's point evaluator (each |r_p| <= ||r||_2 <= 1e-10 ||b||_2)."""
+    wl = synth.SU3_16x32
+    U, srcs = wl.draw(1)
+    b = srcs[0].reshape(-1)
+    g = dw.make_geom(wl.dims, wl.Ls, group="su3")
+    rng = synth.rng_for(wl.seed + 7000)
+    starts = np.stack([synth.gaussian_complex(rng, (wl.V * 12,)) for _ in range(24)])
+    h = dw.mg_setup(g, _dev(U), wl.M5, wl.mf, {"nvec": 24, "block": [2, 2, 2, 2], "setup_mass": -0.42,
+                                               "post_smooth": 16, "coarse_tol": 0.4}, _dev(starts))
+    bd = _dev(b)
+    x = torch.empty_like(bd)
+    stats, status = dw.mg_solve(h, bd, x, tol=1e-10)
+    assert status == 0 and stats["true_residual"] <= 1e-10
+    Dx = torch.empty_like(bd)
+    dw.dwf_apply(g, _dev(U), x, Dx, wl.M5, wl.mf, prec="f64")
+    bn = torch.linalg.norm(bd).item()
+    assert torch.linalg.norm(bd - Dx).item() <= 1e-10 * bn
+    xs = x.cpu().numpy().reshape(wl.Ls, wl.V, 4, 3)
+    prng = np.random.default_rng(9)
+    pts = [(int(prng.integers(0, wl.Ls)), int(prng.integers(0, wl.V))) for _ in range(40)] + [(0, 0), (wl.Ls - 1, wl.V - 1)]
+    Dx_p = dirac.dwf_apply_points(U, xs, wl.dims, wl.Ls, wl.M5, wl.mf, pts, group="su3")
+    bs = b.reshape(wl.Ls, wl.V, 4, 3)
+    r_p = np.array([bs[s, site] for s, site in pts]) - Dx_p
+    assert np.abs(r_p).max() <= 1e-10 * bn
+    h.close()
