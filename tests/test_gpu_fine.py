@@ -205,6 +205,44 @@ def test_bench_size_apply_sampled(dw):
     assert np.abs(g_pts - want).max() < 1e-5 * np.abs(want).max()
 
 
+def test_max_size_apply_sampled(dw):
+    """A 4096 x 4096 x Ls=16 lattice (268 M 5-d sites, 4.3 GB per FP32 spinor): the apply's
+    64-bit indexing and s-window at this size, checked point by point against the definition.
+    The source is drawn on the GPU from a seeded generator (the CPU copy is read only at the
+    sampled points' neighbourhoods)."""
+    dims, Ls, M5, mf = (4096, 4096), 16, 1.0, 0.005
+    V = dims[0] * dims[1]
+    rng = synth.rng_for(4096)
+    theta = synth.u1_angles(rng, dims, 0.7)
+    U = synth.u1_links(theta)
+    g = dw.make_geom(dims, Ls)
+    Ud = dw.links_to(g, _dev(U), "f32_l16")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4096)
+    pd = torch.randn(V * Ls * 2, dtype=torch.complex64, device="cuda", generator=gen)
+    out = torch.empty_like(pd)
+    dw.dwf_apply(g, Ud, pd, out, M5, mf, prec="f32_l16")
+    prng = np.random.default_rng(1)
+    pts = [(int(prng.integers(0, Ls)), int(prng.integers(0, V))) for _ in range(40)]
+    pts += [(0, 0), (Ls - 1, V - 1), (Ls - 1, 0), (0, V - 1)]
+    # psi restricted to what the sampled points read: all slices of each point's 5-site neighbourhood
+    L0, L1 = dims
+    sites = set()
+    for _, x in pts:
+        xx, yy = x % L0, x // L0
+        for dx, dy in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)):
+            sites.add(((yy + dy) % L1) * L0 + (xx + dx) % L0)
+    sites = sorted(sites)
+    idx = torch.tensor(sites, dtype=torch.long, device="cuda")
+    sub = pd.view(Ls, V, 2).index_select(1, idx).cpu().numpy().astype(np.complex128)
+    psi_full = np.zeros((Ls, V, 2), dtype=np.complex128)
+    psi_full[:, sites, :] = sub
+    want = dirac.dwf_apply_points_2d(_rounded_links(U, "f32_l16"), psi_full, dims, Ls, M5, mf, pts)
+    got = out.view(Ls, V, 2)
+    g_pts = np.array([got[s, x].cpu().numpy() for s, x in pts])
+    assert np.abs(g_pts - want).max() < 1e-5 * np.abs(want).max()
+
+
 def test_cgne_solve_reaches_tolerance(dw):
     """FP64 GPU CGNR on the 32x32 x Ls=8 workload reaches 1e-10 and the oracle's solution."""
     wl = synth.SCHWINGER_32
