@@ -413,32 +413,47 @@ def time_su3_solves(dw, dev):
 
 
 def time_su3_apply(dw, dev, stream, args):
-    """FP32/FP16-link 4-d SU(3) apply on 16^3 x 32 x Ls=16 (421 MB per apply)."""
+    """FP32/FP16-link 4-d SU(3) apply on 16^3 x 32 x Ls=16 (421 MB per apply), in the canonical layout
+    and in the packed layout (blocks of 32 sites, each piece of a spinor a 512-byte plane)."""
     import torch
     wl = synth.SU3_16x32
     U, srcs = wl.draw(1)
     g = dw.make_geom(wl.dims, wl.Ls, group="su3")
-    Ud = dw.links_to(g, torch.from_numpy(U.reshape(-1)).to(dev), "f32_l16")
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    Ud = dw.links_to(g, U64, "f32_l16")
+    Up = dw.pack_links(g, U64, "f32_l16")
     psi = torch.from_numpy(srcs[0].reshape(-1).astype(np.complex64)).to(dev)
     out = torch.empty_like(psi)
+    psi_p = dw.pack_spinor(g, psi)
+    out_p = torch.empty_like(psi_p)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     nbytes = wl.V * wl.Ls * 2 * 96 + 4 * wl.V * 36
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
-    torch.cuda.synchronize(dev)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for a, b in evs:
-        flush.fill_(1.0)
-        a.record(stream)
-        dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16")
-        b.record(stream)
-    torch.cuda.synchronize(dev)
-    t = float(np.mean([a.elapsed_time(b) * 1e-3 for a, b in evs]))
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            fn()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return float(np.mean([a.elapsed_time(b) * 1e-3 for a, b in evs]))
+
+    t = timed(lambda: dw.dwf_apply(g, Ud, psi, out, wl.M5, wl.mf, prec="f32_l16"))
+    tp = timed(lambda: dw.dwf_apply_packed(g, Up, psi_p, out_p, wl.M5, wl.mf, prec="f32_l16"))
+    tc = timed(lambda: dw.pack_spinor(g, psi, psi_p))
+    diff = float((dw.unpack_spinor(g, out_p) - out).abs().max() / out.abs().max())
     peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
     return {"workload": f"{wl.name}: 4-d SU(3) D_DW(m) apply, FP32 spinors, FP16 links, M5 {wl.M5}, m {wl.mf}",
             "algorithmic_bytes_per_launch": nbytes, "ms": t * 1e3, "GBps": nbytes / t / 1e9,
-            "frac_of_hbm": nbytes / t / 1e9 / float(peaks["hbm_gbs"])}
+            "frac_of_hbm": nbytes / t / 1e9 / hbm,
+            "packed": {"ms": tp * 1e3, "GBps": nbytes / tp / 1e9, "frac_of_hbm": nbytes / tp / 1e9 / hbm,
+                       "pack_ms": tc * 1e3, "max_rel_diff_vs_canonical": diff}}
 
 
 def time_batched_apply(dw, dev, stream, args):

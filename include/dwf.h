@@ -143,6 +143,39 @@ DWF_API dwf_status dwf_pvdag_apply(const dwf_geom* g, const void* U, const void*
 DWF_API dwf_status dwf_pvdag_apply_noalloc(const dwf_geom* g, const void* U, const void* psi, void* out,
                                    double M5, double mf, int prec, void* stream);
 
+/* Packed layout of 4-d SU(3) fields (FP32 spinors), a private alternative to
+ * the canonical layout with the same operator (Eq. DWoperator, Sec. 2).  The
+ * sites of a slice are taken in blocks of 32 consecutive canonical site
+ * indices (NB = ceil(V / 32) blocks; sites past V pad the last block).  A
+ * spinor block holds six planes of 32 float4: plane k, slot i is complex
+ * values 2k, 2k+1 (spin-major, colour fastest) of site 32 b + i, so the
+ * float4 of (s, site, k) sits at ((s NB + site / 32) 6 + k) 32 + site % 32.  A
+ * link block holds nine planes of 32 entries: entry j = 3 row + column of
+ * U_mu(site) at ((mu NB + site / 32) 9 + j) 32 + site % 32, in the storage of
+ * `prec` (complex64, half pairs or bfloat16 pairs).  A warp then reads each
+ * piece of 32 neighbour spinors as one contiguous run.  4-d lattices only
+ * (DWF_ERR_UNSUPPORTED otherwise).  Sizes are in complex values (0 for a bad
+ * or 2-d geometry). */
+DWF_API size_t dwf_packed_spinor_size(const dwf_geom* g);
+DWF_API size_t dwf_packed_link_size(const dwf_geom* g);
+
+/* FP64 canonical links -> packed links in the storage of prec (F32, F32_L16
+ * or F32_LBF16), rounded to nearest even; entries of padding sites are 0. */
+DWF_API dwf_status dwf_pack_links(const dwf_geom* g, const void* U64, void* U_packed, int prec, void* stream);
+
+/* FP32 canonical spinor (dwf_spinor_size complex64) -> packed spinor
+ * (dwf_packed_spinor_size complex64; padding sites written as 0), and back.
+ * Buffers are 16-byte aligned and distinct. */
+DWF_API dwf_status dwf_pack_spinor(const dwf_geom* g, const void* psi, void* packed, void* stream);
+DWF_API dwf_status dwf_unpack_spinor(const dwf_geom* g, const void* packed, void* psi, void* stream);
+
+/* out = D_DW(mf) psi (dagger != 0: D_DW(mf)^dag psi) with psi, out and U in
+ * the packed layout; the same operator as dwf_apply.  prec is F32, F32_L16 or
+ * F32_LBF16 and must match the links' storage.  Padding sites of out are not
+ * written.  psi and out are distinct, 16-byte aligned buffers. */
+DWF_API dwf_status dwf_apply_packed(const dwf_geom* g, const void* U_packed, const void* psi, void* out,
+                                    double M5, double mf, int dagger, int prec, void* stream);
+
 /* Inner product <x, y> = sum conj(x_i) y_i over n complex values (complex128
  * if prec == DWF_F64, complex64 otherwise), accumulated in FP64 by a
  * warp-shuffle / block / grid reduction with a fixed summation order (the

@@ -7,6 +7,7 @@ from ._lib import (  # noqa: F401
     DwfError, Geom, SolveStats, PREC, lib, make_geom, spinor_size, link_size, spinor_dtype,
     links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_pvdag_apply_noalloc, dwf_dot, cgne_solve,
     links_from_angles, gamma5_reflect, link_force, dwf_apply_batched, check_wait_timeout, dwf_apply_host,
+    packed_spinor_size, packed_link_size, pack_links, pack_spinor, unpack_spinor, dwf_apply_packed,
 )
 from ._lib import (  # noqa: F401
     MgParams, Multigrid, mg_default_params, mg_setup, mg_solve, mg_destroy, mg_get_prolongator,

@@ -68,6 +68,8 @@ def lib():
         L.dwf_last_error.restype = ctypes.c_char_p
         L.dwf_spinor_size.restype = ctypes.c_size_t
         L.dwf_link_size.restype = ctypes.c_size_t
+        L.dwf_packed_spinor_size.restype = ctypes.c_size_t
+        L.dwf_packed_link_size.restype = ctypes.c_size_t
         _setup_signatures(L)
         _lib = L
     return _lib
@@ -83,6 +85,12 @@ def _setup_signatures(L):
     sigs = {
         "dwf_spinor_size": [G],
         "dwf_link_size": [G],
+        "dwf_packed_spinor_size": [G],
+        "dwf_packed_link_size": [G],
+        "dwf_pack_links": [G, _VP, _VP, _I, _VP],
+        "dwf_pack_spinor": [G, _VP, _VP, _VP],
+        "dwf_unpack_spinor": [G, _VP, _VP, _VP],
+        "dwf_apply_packed": [G, _VP, _VP, _VP, _D, _D, _I, _I, _VP],
         "dwf_convert_links": [G, _VP, _VP, _I, _VP],
         "dwf_apply": [G, _VP, _VP, _VP, _D, _D, _I, _I, _VP],
         "pv_apply": [G, _VP, _VP, _VP, _D, _I, _I, _VP],
@@ -115,7 +123,7 @@ def _setup_signatures(L):
     for name, args in sigs.items():
         fn = getattr(L, name)
         fn.argtypes = args
-        if name not in ("dwf_spinor_size", "dwf_link_size"):
+        if name not in ("dwf_spinor_size", "dwf_link_size", "dwf_packed_spinor_size", "dwf_packed_link_size"):
             fn.restype = ctypes.c_int
     L.dwf_mg_default_params.argtypes = [ctypes.POINTER(MgParams)]
     L.dwf_mg_default_params.restype = None
@@ -190,6 +198,70 @@ def links_to(geom: Geom, U64: torch.Tensor, prec: str, stream=None) -> torch.Ten
     else:
         out = torch.empty(n, 2, dtype=torch.bfloat16, device=U64.device)
     check(lib().dwf_convert_links(ctypes.byref(geom), _ptr(U64), _ptr(out), PREC[prec], _stream(stream)))
+    return out
+
+
+def packed_spinor_size(geom: Geom) -> int:
+    return int(lib().dwf_packed_spinor_size(ctypes.byref(geom)))
+
+
+def packed_link_size(geom: Geom) -> int:
+    return int(lib().dwf_packed_link_size(ctypes.byref(geom)))
+
+
+def _check_packed(t, geom, name):
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if t.dtype != torch.complex64:
+        raise ValueError(f"{name} must be complex64 (packed spinors are FP32)")
+    if t.numel() != packed_spinor_size(geom):
+        raise ValueError(f"{name} has {t.numel()} complex values, the packed layout needs {packed_spinor_size(geom)}")
+
+
+def pack_links(geom: Geom, U64: torch.Tensor, prec: str, stream=None) -> torch.Tensor:
+    """complex128 canonical links -> packed links in the storage of `prec` (4-d)."""
+    n = packed_link_size(geom)
+    if U64.dtype != torch.complex128 or U64.numel() != link_size(geom) or not U64.is_cuda:
+        raise ValueError("U64 must be a CUDA complex128 tensor of the link size")
+    U64 = U64.contiguous()
+    if prec == "f32":
+        out = torch.empty(n, dtype=torch.complex64, device=U64.device)
+    elif prec == "f32_l16":
+        out = torch.empty(n, 2, dtype=torch.float16, device=U64.device)
+    elif prec == "f32_lbf16":
+        out = torch.empty(n, 2, dtype=torch.bfloat16, device=U64.device)
+    else:
+        raise ValueError("packed links take f32, f32_l16 or f32_lbf16")
+    check(lib().dwf_pack_links(ctypes.byref(geom), _ptr(U64), _ptr(out), PREC[prec], _stream(stream)))
+    return out
+
+
+def pack_spinor(geom: Geom, psi: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """FP32 canonical spinor -> packed layout (4-d)."""
+    _check_spinor(psi, geom, "f32", "psi")
+    if out is None:
+        out = torch.empty(packed_spinor_size(geom), dtype=torch.complex64, device=psi.device)
+    _check_packed(out, geom, "out")
+    check(lib().dwf_pack_spinor(ctypes.byref(geom), _ptr(psi), _ptr(out), _stream(stream)))
+    return out
+
+
+def unpack_spinor(geom: Geom, packed: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """Packed spinor -> FP32 canonical layout (4-d)."""
+    _check_packed(packed, geom, "packed")
+    if out is None:
+        out = torch.empty(spinor_size(geom), dtype=torch.complex64, device=packed.device)
+    _check_spinor(out, geom, "f32", "out")
+    check(lib().dwf_unpack_spinor(ctypes.byref(geom), _ptr(packed), _ptr(out), _stream(stream)))
+    return out
+
+
+def dwf_apply_packed(geom, U_packed, psi, out, M5, mf, dagger=False, prec="f32_l16", stream=None):
+    """D_DW(mf) (or its adjoint) on packed 4-d spinors with packed links."""
+    _check_packed(psi, geom, "psi")
+    _check_packed(out, geom, "out")
+    check(lib().dwf_apply_packed(ctypes.byref(geom), _ptr(U_packed), _ptr(psi), _ptr(out), float(M5), float(mf),
+                                 int(bool(dagger)), PREC[prec], _stream(stream)))
     return out
 
 

@@ -22,6 +22,7 @@ struct Fine4dParams {
     int anti[4];
     double diag;
     double mf;
+    float diag_f, mf_f;   // the same in FP32 for the FP32 kernels
     int s_chunk;
 };
 

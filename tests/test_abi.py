@@ -64,3 +64,21 @@ def test_sizes_and_host_side_argument_checks(dw):
     assert L.dwf_apply(ctypes.byref(empty), None, None, None, 1.0, 0.01, 0, 0, None) == 1   # L >= 1 required
     res = (ctypes.c_double * 2)()
     assert L.dwf_dot(None, None, 0, 0, res, None) == 0 and res[0] == 0.0
+
+
+def test_packed_layout_sizes_and_checks(dw):
+    g4 = dw.make_geom((3, 5, 2, 3), 4, group="su3")          # V = 90: three blocks of 32, the last padded
+    assert dw.packed_spinor_size(g4) == 4 * 96 * 12
+    assert dw.packed_link_size(g4) == 4 * 96 * 9
+    g2 = dw.make_geom((32, 32), 8)
+    assert dw.packed_spinor_size(g2) == 0 and dw.packed_link_size(g2) == 0
+    L = dw.lib()
+    fake, fake2 = ctypes.c_void_p(4096), ctypes.c_void_p(8192)
+    assert L.dwf_apply_packed(ctypes.byref(g2), fake, fake, fake2, 1.8, 0.01, 0, 2, None) == 6   # 2-d: unsupported
+    assert L.dwf_apply_packed(ctypes.byref(g4), None, None, None, 1.8, 0.01, 0, 2, None) == 1    # NULL pointers
+    assert L.dwf_apply_packed(ctypes.byref(g4), fake, fake, fake, 1.8, 0.01, 0, 2, None) == 1    # psi == out
+    assert L.dwf_apply_packed(ctypes.byref(g4), fake, ctypes.c_void_p(4100), fake2, 1.8, 0.01, 0, 2, None) == 1
+    assert b"aligned" in L.dwf_last_error()
+    assert L.dwf_pack_links(ctypes.byref(g4), fake, fake2, 0, None) == 1                        # F64 not packed
+    assert L.dwf_pack_spinor(ctypes.byref(g4), fake, fake, None) == 1
+    assert L.dwf_unpack_spinor(ctypes.byref(g2), fake, fake2, None) == 6

@@ -95,3 +95,85 @@ def test_dwf4d_adjoint_and_cgne(dw):
     D = dirac.dwf_matrix(U, dims, Ls, M5, mf, group="su3")
     res = np.linalg.norm(b - D @ x.cpu().numpy()) / np.linalg.norm(b)
     assert status == 0 and res <= 1e-10
+
+
+def _packed_positions(dims, Ls):
+    """Float4 index in the packed layout of every (s, site, piece) in canonical order."""
+    V = int(np.prod(dims))
+    NB = (V + 31) // 32
+    s, site, k = np.meshgrid(np.arange(Ls), np.arange(V), np.arange(6), indexing="ij")
+    return ((s * NB + site // 32) * 6 + k) * 32 + site % 32, NB
+
+
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 4), ((3, 5, 2, 3), 3), ((2, 2, 2, 2), 2)])
+def test_pack_unpack_layout(dw, dims, Ls):
+    """Packing places piece k of (s, site) at ((s NB + site/32) 6 + k) 32 + site%32; unpacking inverts it."""
+    rng = synth.rng_for(7)
+    psi = synth.gaussian_spinor(rng, dims, Ls, "su3")
+    g = dw.make_geom(dims, Ls, group="su3")
+    pd = _dev(psi, torch.complex64)
+    pk = dw.pack_spinor(g, pd)
+    pos, NB = _packed_positions(dims, Ls)
+    assert pk.numel() == Ls * NB * 32 * 12
+    f4 = pk.cpu().numpy().view(np.float32).reshape(-1, 4)
+    canon = pd.cpu().numpy().view(np.float32).reshape(-1, 4)
+    assert np.array_equal(f4[pos.reshape(-1)], canon)
+    pad = np.ones(f4.shape[0], bool)
+    pad[pos.reshape(-1)] = False
+    assert not f4[pad].any()                         # padding sites are zero
+    back = dw.unpack_spinor(g, pk)
+    assert torch.equal(back, pd)
+
+
+def test_pack_links_layout(dw):
+    dims = (3, 5, 2, 3)
+    V = int(np.prod(dims))
+    NB = (V + 31) // 32
+    rng = synth.rng_for(8)
+    U = synth.su3_links(rng, dims, 0.3).reshape(4, V, 9)
+    g = dw.make_geom(dims, 2, group="su3")
+    Up = dw.pack_links(g, _dev(U), "f32").cpu().numpy().reshape(4, NB, 9, 32)
+    want = np.zeros((4, NB * 32, 9), np.complex64)
+    want[:, :V] = U.astype(np.complex64)
+    assert np.array_equal(Up, want.reshape(4, NB, 32, 9).transpose(0, 1, 3, 2))
+
+
+@pytest.mark.parametrize("dims,Ls,anti", [((4, 4, 4, 4), 4, None), ((3, 5, 2, 3), 3, [0, 0, 0, 1]),
+                                          ((2, 2, 2, 2), 2, [1, 1, 1, 1]), ((6, 4, 4, 8), 5, None)])
+@pytest.mark.parametrize("prec", ["f32", "f32_l16", "f32_lbf16"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dwf4d_packed_apply_parity(dw, dims, Ls, anti, prec, dagger):
+    M5, mf = 1.8, 0.01
+    rng = synth.rng_for(hash((dims, Ls, 3)) % 997)
+    U = synth.su3_links(rng, dims, 0.3)
+    psi = synth.gaussian_spinor(rng, dims, Ls, "su3")
+    g = dw.make_geom(dims, Ls, group="su3", antiperiodic=anti)
+    Up = dw.pack_links(g, _dev(U), prec)
+    pk = dw.pack_spinor(g, _dev(psi, torch.complex64))
+    outp = torch.empty_like(pk)
+    dw.dwf_apply_packed(g, Up, pk, outp, M5, mf, dagger=dagger, prec=prec)
+    got = dw.unpack_spinor(g, outp).cpu().numpy().astype(np.complex128)
+    ps = psi.astype(np.complex64).astype(np.complex128)
+    want = dirac.dwf_apply(_rounded(U, prec), ps, dims, Ls, M5, mf, dagger_=dagger, group="su3",
+                           antiperiodic=anti).reshape(-1)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < TOL[prec]
+
+
+def test_dwf4d_packed_full_size_sampled(dw):
+    """The bench workload (16^3 x 32 x 16, FP16 links) in the packed layout, checked point by point."""
+    wl = synth.SU3_16x32
+    U, srcs = wl.draw(1)
+    psi = srcs[0]
+    g = dw.make_geom(wl.dims, wl.Ls, group="su3")
+    Up = dw.pack_links(g, _dev(U), "f32_l16")
+    pk = dw.pack_spinor(g, _dev(psi, torch.complex64))
+    outp = torch.empty_like(pk)
+    dw.dwf_apply_packed(g, Up, pk, outp, wl.M5, wl.mf, prec="f32_l16")
+    got = dw.unpack_spinor(g, outp).cpu().numpy().reshape(wl.Ls, wl.V, 4, 3)
+    rng = np.random.default_rng(2)
+    pts = [(int(rng.integers(0, wl.Ls)), int(rng.integers(0, wl.V))) for _ in range(120)]
+    pts += [(0, 0), (wl.Ls - 1, wl.V - 1), (0, wl.V - 1), (wl.Ls - 1, 0)]
+    want = dirac.dwf_apply_points(_rounded(U, "f32_l16"), psi.astype(np.complex64).astype(np.complex128),
+                                  wl.dims, wl.Ls, wl.M5, wl.mf, pts, group="su3")
+    g_pts = np.array([got[s, x] for s, x in pts])
+    assert np.abs(g_pts - want).max() < 1e-5 * np.abs(want).max()
