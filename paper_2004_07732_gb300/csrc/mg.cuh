@@ -50,6 +50,7 @@ struct dwf_mg {
     float2* Yd32;         // FP32 adjoint blocks Y[x+dir][-dir]^dag, column-major (generic stencil)
     void* Ytile;          // blocks read by the 2-d tile stencil: Y32, or an FP16 column-major copy
     int ytile_half;       // 1 when Ytile holds FP16 (half2) blocks
+    void* Ymma;           // FP16 blocks in tensor-core fragment order (48 dof, FP16 blocks), else nullptr
     int* status;          // device status word of the setup kernels
     std::vector<void*> allocs;
     // solver workspace (allocated on first solve)

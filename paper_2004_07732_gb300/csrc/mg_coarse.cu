@@ -8,6 +8,7 @@
 // Coarse vectors are [s][coarse site][chirality][vec], complex64.
 #include "mg.cuh"
 #include "async_copy.cuh"
+#include "mma_tf32.cuh"
 
 namespace dwf {
 
@@ -453,137 +454,101 @@ __global__ void __launch_bounds__(512) k_coarse_site(const BT* __restrict__ B, c
     out[s * slice + xc * ncd + i] = acc;
 }
 
-// Persistent, double-buffered variant for 48 coarse dof and FP16 blocks (the
-// 4-d workload): one block per SM walks the coarse sites; while site k is
-// multiplied, the bulk copies of site k + 1's blocks (83 KB) and of its
-// neighbours' inputs (one 384-byte run per direction and slice) are in flight
-// on the other buffer's mbarrier, so the HBM stream of blocks never stops.
-// Thread (i, g): rows i and i + 24 of group g = (direction, half of the
-// columns), all slices, so every block value and input pair loaded from shared
-// memory feeds 8 or 16 complex multiply-adds; the 18 group partials of each
-// (row, slice) are summed in shared memory.
-constexpr int SDB_NCD = 48, SDB_NDIR = 9, SDB_LS = 4, SDB_GROUPS = 2 * SDB_NDIR;
-constexpr int SDB_THREADS = (SDB_NCD / 2) * SDB_GROUPS;
-struct SiteDbSmem {
-    __half2 yb[2][SDB_NDIR * SDB_NCD * SDB_NCD];
-    float2 vs[2][SDB_NDIR][SDB_LS][SDB_NCD];
-    float2 part[SDB_GROUPS][SDB_LS][SDB_NCD];
-    unsigned long long mbar[2];
-};
-
-// warp 0 only: lane 0 expects the bytes and copies the blocks; lane d < ndir copies
-// direction d's neighbour inputs, all on the buffer's mbarrier
-__device__ __forceinline__ void sdb_issue(SiteDbSmem& sm, int buf, const __half2* __restrict__ B,
-                                          const float2* __restrict__ in, const CoarseParams& p, int xc) {
-    constexpr unsigned YB = SDB_NDIR * SDB_NCD * SDB_NCD * sizeof(__half2);
-    constexpr unsigned VB = SDB_NCD * sizeof(float2);
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        const unsigned bytes = YB + (unsigned)(SDB_NDIR * p.Ls_c) * VB;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&sm.mbar[buf], bytes);
-        bulk_g2s(sm.yb[buf], B + (long long)xc * SDB_NDIR * SDB_NCD * SDB_NCD, YB, &sm.mbar[buf]);
-    }
-    __syncwarp();
-    if (lane < SDB_NDIR) {
-        const long long slice = p.Vc * SDB_NCD;
-        const int nb = coarse_nb32(p, xc, lane);
-        for (int s = 0; s < p.Ls_c; ++s)
-            bulk_g2s(&sm.vs[buf][lane][s][0], in + s * slice + (long long)nb * SDB_NCD, VB, &sm.mbar[buf]);
-    }
+// ---------------------------------------------------------------------------
+// Tensor-core form of the 48-dof stencil (4-d, FP16 blocks, Ls_c <= 4).  One
+// warp per coarse site.  Per direction the complex product Y v over the Ls_c
+// slices is the real product of A = [Re Y; Im Y] (96 x 48, FP16, exact in
+// TF32) with B = [Re v | Im v] (48 x 2 Ls_c): C = A B holds Re Y Re v, Re Y Im v
+// (rows < 48) and Im Y Re v, Im Y Im v (rows >= 48), so
+// Re(Y v) = C[i][Re] - C[48 + i][Im] and Im(Y v) = C[48 + i][Re] + C[i][Im].
+// B column n = 4 part + s; the FP32 inputs are split into TF32 high and low
+// parts multiplied separately (FP32-level accuracy).  A streams from HBM in
+// fragment order (one coalesced 16-byte load per lane per row tile and column
+// tile pair, no shared-memory staging), so many warps per SM keep enough bytes
+// in flight; the products accumulate over the 9 directions in registers.
+// ---------------------------------------------------------------------------
+constexpr int CM_WARPS = 4;
+__device__ __forceinline__ uint32_t f16_bits_to_f32(uint32_t w, int hi) {
+    return __float_as_uint(__half2float(__ushort_as_half((unsigned short)(hi ? (w >> 16) : (w & 0xffffu)))));
 }
 
-__global__ void __launch_bounds__(SDB_THREADS, 1) k_coarse_site_db(const __half2* __restrict__ B,
-                                                                   const float2* __restrict__ in,
-                                                                   float2* __restrict__ out, CoarseParams p, bool dag,
-                                                                   const int* skip, int* status) {
+__global__ void __launch_bounds__(CM_WARPS * 32, 3) k_coarse_mma(const uint4* __restrict__ Ym,
+                                                                 const float2* __restrict__ in,
+                                                                 float2* __restrict__ out, CoarseParams p, bool dag,
+                                                                 const int* skip) {
     if (skip && *skip) return;
-    extern __shared__ __align__(128) unsigned char sdb_raw[];
-    SiteDbSmem& sm = *reinterpret_cast<SiteDbSmem*>(sdb_raw);
-    const int Ls_c = p.Ls_c, nvec = p.nvec;
-    const long long slice = p.Vc * SDB_NCD;
-    const int i = threadIdx.x % (SDB_NCD / 2), grp = threadIdx.x / (SDB_NCD / 2);
-    const int dir = grp >> 1, jh = grp & 1;            // direction; columns [24 jh, 24 jh + 24)
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.mbar[0], 1);
-        mbar_init(&sm.mbar[1], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32 && blockIdx.x < p.Vc) sdb_issue(sm, 0, B, in, p, blockIdx.x);
-    int k = 0;
-    for (long long xc = blockIdx.x; xc < p.Vc; xc += gridDim.x, ++k) {
-        const int buf = k & 1;
-        const long long nxt = xc + gridDim.x;
-        if (threadIdx.x < 32 && nxt < p.Vc) sdb_issue(sm, buf ^ 1, B, in, p, (int)nxt);
-        const bool okw = mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS);
-        if (__syncthreads_or(!okw)) {                      // the whole block leaves together
-            if (threadIdx.x == 0) atomicExch(status, 2);
-            // let the copies in flight land before the block exits
-            mbar_wait_bounded(&sm.mbar[buf], (unsigned)((k >> 1) & 1), TILE_WAIT_NS);
-            if (nxt < p.Vc) mbar_wait_bounded(&sm.mbar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1), TILE_WAIT_NS);
-            return;
-        }
-        // acc[r][s]: row i + 24 r, slice s
-        float2 acc[2][SDB_LS];
+    __shared__ float Ps[CM_WARPS][96][9];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int xc = blockIdx.x * CM_WARPS + warp;
+    if (xc >= p.Vc) return;                              // whole warps; no block-wide barrier below
+    const int Ls_c = p.Ls_c;
+    const long long slice = p.Vc * 48;
+    const int part = g >> 2, sB = g & 3;                 // B column n = g
+    const bool colv = sB < Ls_c;
+    float acc[6][2][4];
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+    for (int mt = 0; mt < 6; ++mt)
 #pragma unroll
-            for (int s = 0; s < SDB_LS; ++s) acc[r][s] = make_float2(0.f, 0.f);
-        {
-            const __half2* yd = sm.yb[buf] + dir * SDB_NCD * SDB_NCD + i;
-            const int j0 = jh * (SDB_NCD / 2);
-#pragma unroll 2
-            for (int jj = 0; jj < SDB_NCD / 2; jj += 2) {
-                const int j = j0 + jj;
-                const float2 y00 = __half22float2(yd[j * SDB_NCD]);
-                const float2 y10 = __half22float2(yd[j * SDB_NCD + SDB_NCD / 2]);
-                const float2 y01 = __half22float2(yd[(j + 1) * SDB_NCD]);
-                const float2 y11 = __half22float2(yd[(j + 1) * SDB_NCD + SDB_NCD / 2]);
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int s = 0; s < SDB_LS; ++s) {
-                    if (s < Ls_c) {
-                        const float4 v = *reinterpret_cast<const float4*>(&sm.vs[buf][dir][s][j]);
-                        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
-                        acc[0][s] = cfma(y01, v1, cfma(y00, v0, acc[0][s]));
-                        acc[1][s] = cfma(y11, v1, cfma(y10, v0, acc[1][s]));
-                    }
+            for (int q = 0; q < 4; ++q) acc[mt][h][q] = 0.f;
+    const uint4* A = Ym + (long long)xc * (9 * 3 * 6 * 32) + lane;
+#pragma unroll 1
+    for (int dir = 0; dir < 9; ++dir) {
+        const int nb = coarse_nb32(p, xc, dir);
+        const float* vin = reinterpret_cast<const float*>(in + (colv ? sB : 0) * slice + (long long)nb * 48) + part;
+#pragma unroll
+        for (int kp = 0; kp < 3; ++kp) {
+            uint4 a[6];
+#pragma unroll
+            for (int mt = 0; mt < 6; ++mt) a[mt] = __ldg(A + ((dir * 3 + kp) * 6 + mt) * 32);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kt = 2 * kp + h;                 // input dof 8 kt .. 8 kt + 7
+                float b0 = colv ? __ldg(vin + 2 * (8 * kt + t)) : 0.f;
+                float b1 = colv ? __ldg(vin + 2 * (8 * kt + t + 4)) : 0.f;
+                if (dag && kt >= 3) { b0 = -b0; b1 = -b1; }   // sigma_3 on the chirality - inputs
+                uint32_t bh[2], bl[2];
+                split_tf32(b0, bh[0], bl[0]);
+                split_tf32(b1, bh[1], bl[1]);
+#pragma unroll
+                for (int mt = 0; mt < 6; ++mt) {
+                    const uint32_t w0 = h ? a[mt].z : a[mt].x, w1 = h ? a[mt].w : a[mt].y;
+                    const uint32_t af[4] = {f16_bits_to_f32(w0, 0), f16_bits_to_f32(w0, 1), f16_bits_to_f32(w1, 0),
+                                            f16_bits_to_f32(w1, 1)};
+                    mma_tf32(acc[mt][0], af, bh);
+                    mma_tf32(acc[mt][1], af, bl);
                 }
             }
         }
-        // sigma_3 on the inputs: the column half jh = 1 holds the chirality - inputs (nvec = 24)
-        const float sj = (dag && jh == 1) ? -1.f : 1.f;
+    }
+    // C fragment: c0 (g, 2t), c1 (g, 2t + 1), c2 (g + 8, 2t), c3 (g + 8, 2t + 1)
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+    for (int mt = 0; mt < 6; ++mt)
 #pragma unroll
-            for (int s = 0; s < SDB_LS; ++s)
-                if (s < Ls_c) sm.part[grp][s][i + r * (SDB_NCD / 2)] = make_float2(sj * acc[r][s].x, sj * acc[r][s].y);
-        __syncthreads();
-        // epilogue: thread t < 48 * Ls_c forms output (row, slice)
-        if (threadIdx.x < SDB_NCD * Ls_c) {
-            const int r = threadIdx.x % SDB_NCD, s = threadIdx.x / SDB_NCD;
-            float2 hsum = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int g = 0; g < SDB_GROUPS; ++g) { hsum.x += sm.part[g][s][r].x; hsum.y += sm.part[g][s][r].y; }
-            const float si = (dag && r >= nvec) ? -1.f : 1.f;
-            const float2 self = sm.vs[buf][0][s][r];
-            const int c = r / nvec;
-            const bool from_below = dag ? (c == 1) : (c == 0);
-            int sh;
-            float sc = 1.f;
-            if (from_below) { if (s > 0) sh = s - 1; else { sh = Ls_c - 1; sc = -p.mf; } }
-            else            { if (s < Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
-            const float2 hv = sm.vs[buf][0][sh][r];
-            out[s * slice + xc * SDB_NCD + r] =
-                make_float2(si * hsum.x + self.x + sc * hv.x, si * hsum.y + self.y + sc * hv.y);
-        }
-        __syncthreads();                                   // buffer buf and the partials are free again
+        for (int q = 0; q < 4; ++q)
+            Ps[warp][mt * 16 + g + ((q & 2) ? 8 : 0)][2 * t + (q & 1)] = acc[mt][0][q] + acc[mt][1][q];
+    __syncwarp();
+    const int nvec = p.nvec;
+    for (int idx = lane; idx < 48 * Ls_c; idx += 32) {
+        const int s = idx / 48, r = idx % 48;
+        const float re = Ps[warp][r][s] - Ps[warp][48 + r][4 + s];
+        const float im = Ps[warp][48 + r][s] + Ps[warp][r][4 + s];
+        const float si = (dag && r >= nvec) ? -1.f : 1.f;  // sigma_3 on the output
+        const float2 self = __ldg(in + s * slice + (long long)xc * 48 + r);
+        const int c = r / nvec;
+        const bool from_below = dag ? (c == 1) : (c == 0);
+        int sh;
+        float sc = 1.f;
+        if (from_below) { if (s > 0) sh = s - 1; else { sh = Ls_c - 1; sc = -p.mf; } }
+        else            { if (s < Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
+        const float2 hv = __ldg(in + sh * slice + (long long)xc * 48 + r);
+        out[s * slice + (long long)xc * 48 + r] = make_float2(si * re + self.x + sc * hv.x, si * im + self.y + sc * hv.y);
     }
 }
 
 constexpr size_t SITE_SMEM_MAX = 200 * 1024;
 static dwf_status site_init_attributes() {
-    DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_site_db, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(SiteDbSmem)));
     DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_site<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SITE_SMEM_MAX));
     DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_site<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -626,16 +591,9 @@ dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, doub
         else
             k_coarse_tile<float2><<<ntiles, TILE_THREADS, sizeof(TileSmemT<float2>), st>>>(
                 (const float2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
-    } else if (h->ytile_half && p.ncd == SDB_NCD && p.ndir == SDB_NDIR && p.Ls_c <= SDB_LS) {
-        static int nsm = 0;
-        if (nsm == 0) {
-            int dev = 0;
-            DWF_CHECK_CUDA(cudaGetDevice(&dev));
-            DWF_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        }
-        const long long grid1 = p.Vc < nsm ? p.Vc : nsm;
-        k_coarse_site_db<<<(unsigned)grid1, SDB_THREADS, sizeof(SiteDbSmem), st>>>((const __half2*)h->Ytile, in, out, p,
-                                                                                  dagger, skip, h->status + 1);
+    } else if (h->Ymma && p.ncd == 48 && p.ndir == 9 && p.Ls_c <= 4) {
+        const unsigned grid1 = (unsigned)((p.Vc + CM_WARPS - 1) / CM_WARPS);
+        k_coarse_mma<<<grid1, CM_WARPS * 32, 0, st>>>((const uint4*)h->Ymma, in, out, p, dagger, skip);
     } else if (site_ok(p, h->ytile_half)) {
         const int threads = p.ncd * p.Ls_c;
         if (h->ytile_half)

@@ -448,6 +448,29 @@ __global__ void k_blocks_to_f16(const double2* __restrict__ Y, __half2* __restri
     }
 }
 
+// Blocks of the 48-dof coarse operator in the fragment order of k_coarse_mma:
+// the real form A = [Re Y; Im Y] (96 x 48) of each direction's block, cut in
+// 6 row tiles of 16 and 6 column tiles of 8.  Per coarse site, direction d,
+// column-tile pair kp and row tile mt, lane l = 4 g + t holds eight halves: the
+// m16n8k8 A fragment {A(g, t), A(g + 8, t), A(g, t + 4), A(g + 8, t + 4)} of
+// column tile 2 kp, then that of column tile 2 kp + 1.  FP16 rounding as in
+// k_blocks_to_f16.
+__global__ void k_blocks_to_mma(const double2* __restrict__ Y, __half* __restrict__ Ym, long long nsites) {
+    constexpr int per_site = 9 * 3 * 6 * 32 * 8;
+    const long long n = nsites * per_site;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long site = t / per_site;
+        const int r = (int)(t % per_site);
+        const int e = r & 7, lane = (r >> 3) & 31, f = r >> 8;     // f = (dir 3 + kp) 6 + mt
+        const int mt = f % 6, kp = (f / 6) % 3, dir = f / 18;
+        const int g = lane >> 2, tq = lane & 3, kt = 2 * kp + (e >> 2), q = e & 3;
+        const int row = mt * 16 + g + ((q & 1) ? 8 : 0);
+        const int col = kt * 8 + tq + ((q & 2) ? 4 : 0);
+        const double2 v = Y[((site * 9 + dir) * 48 + row % 48) * 48 + col];
+        Ym[t] = __double2half(row < 48 ? v.x : v.y);
+    }
+}
+
 __global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         b[t] = make_float2((float)a[t].x, (float)a[t].y);
@@ -550,6 +573,11 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
         k_blocks_to_f16<<<ew_grid(nblk * m.ncd * m.ncd), 256, 0, st>>>(h->Y64, (__half2*)h->Ytile, nblk, m.ncd);
         DWF_CHECK_LAUNCH();
         h->ytile_half = 1;
+        if (m.ncd == 48 && m.ndir == 9 && m.Ls_c <= 4) {
+            DWF_TRY(mg_alloc(h, &h->Ymma, nblk * m.ncd * m.ncd * sizeof(__half2)));
+            k_blocks_to_mma<<<ew_grid(nblk * m.ncd * m.ncd * 2), 256, 0, st>>>(h->Y64, (__half*)h->Ymma, m.Vc);
+            DWF_CHECK_LAUNCH();
+        }
     } else {
         h->Ytile = h->Y32;
         h->ytile_half = 0;
