@@ -359,7 +359,8 @@ DWF_API int mg_coarse_tc_form(const dwf_mg* h, int nrhs);
  * on the FP64 true residual <= tol); every launch covers all right-hand sides,
  * the coarse operator runs as the tensor-core contraction over the
  * nrhs * Ls_c columns, and converged systems drop out of the work.  stats:
- * NULL or an array of nrhs records.  2-d lattices with nvec = 8.  Returns
+ * NULL or an array of nrhs records.  nrhs > 1 takes 2-d lattices with
+ * nvec = 8; nrhs = 1 any hierarchy (mg_solve uses this path).  Returns
  * DWF_ERR_NOCONV if any right-hand side stopped above tol (x holds its last
  * iterate).  The handle keeps a workspace sized for the largest nrhs seen
  * (about (6 + 2 gcr_restart + 2 post_smooth) FP32 + 2 FP64 fine vectors per

@@ -146,7 +146,8 @@ template <class LT, class R, bool DAG, class LAY>
 __global__ void __launch_bounds__(256, 3) k_dwf4d(const typename LT::store* __restrict__ U,
                                                const typename cplx<R>::T* __restrict__ psi,
                                                typename cplx<R>::T* __restrict__ out, Fine4dParams p, LAY lay,
-                                               int ngroups) {
+                                               int ngroups, const int* skip) {
+    if (skip && *skip) return;
     using C = typename cplx<R>::T;
     const int site = (int)(blockIdx.x / ngroups) * 32 + threadIdx.x;
     const int s = (int)(blockIdx.x % ngroups) * 8 + threadIdx.y;
@@ -255,7 +256,7 @@ static dwf_status grid4d(const Fine4dParams& p, unsigned* blocks, int* ngroups) 
 
 template <class LT, class R, class LAY>
 static dwf_status launch4d(const void* U, const void* psi, void* out, const Fine4dParams& p, const LAY& lay,
-                           bool dagger, cudaStream_t st) {
+                           bool dagger, cudaStream_t st, const int* skip = nullptr) {
     unsigned blocks;
     int ng;
     DWF_TRY(grid4d(p, &blocks, &ng));
@@ -264,8 +265,8 @@ static dwf_status launch4d(const void* U, const void* psi, void* out, const Fine
     auto Ut = reinterpret_cast<const typename LT::store*>(U);
     auto pi = reinterpret_cast<const C*>(psi);
     auto po = reinterpret_cast<C*>(out);
-    if (dagger) k_dwf4d<LT, R, true, LAY><<<blocks, block, 0, st>>>(Ut, pi, po, p, lay, ng);
-    else        k_dwf4d<LT, R, false, LAY><<<blocks, block, 0, st>>>(Ut, pi, po, p, lay, ng);
+    if (dagger) k_dwf4d<LT, R, true, LAY><<<blocks, block, 0, st>>>(Ut, pi, po, p, lay, ng, skip);
+    else        k_dwf4d<LT, R, false, LAY><<<blocks, block, 0, st>>>(Ut, pi, po, p, lay, ng, skip);
     return DWF_OK;
 }
 
@@ -283,15 +284,15 @@ static Fine4dParams params4d(const Geom& g, double M5, double mf) {
 }
 
 dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
-                         bool dagger, int prec, int s_chunk, cudaStream_t st) {
+                         bool dagger, int prec, int s_chunk, cudaStream_t st, const int* skip) {
     (void)s_chunk;
     const Fine4dParams p = params4d(g, M5, mf);
     LayCanon lay{g.V};
     switch (prec) {
-        case DWF_F64:       DWF_TRY((launch4d<LinkF64, double>(U, psi, out, p, lay, dagger, st))); break;
-        case DWF_F32:       DWF_TRY((launch4d<LinkF32, float>(U, psi, out, p, lay, dagger, st))); break;
-        case DWF_F32_L16:   DWF_TRY((launch4d<LinkH16, float>(U, psi, out, p, lay, dagger, st))); break;
-        case DWF_F32_LBF16: DWF_TRY((launch4d<LinkBF16, float>(U, psi, out, p, lay, dagger, st))); break;
+        case DWF_F64:       DWF_TRY((launch4d<LinkF64, double>(U, psi, out, p, lay, dagger, st, skip))); break;
+        case DWF_F32:       DWF_TRY((launch4d<LinkF32, float>(U, psi, out, p, lay, dagger, st, skip))); break;
+        case DWF_F32_L16:   DWF_TRY((launch4d<LinkH16, float>(U, psi, out, p, lay, dagger, st, skip))); break;
+        case DWF_F32_LBF16: DWF_TRY((launch4d<LinkBF16, float>(U, psi, out, p, lay, dagger, st, skip))); break;
         default: set_error("bad precision %d", prec); return DWF_ERR_ARG;
     }
     DWF_CHECK_LAUNCH();

@@ -60,8 +60,18 @@ dwf_status fine_apply_2d_multi(const Geom& g, const void* U, const void* psi, vo
 // walls, 0 and Ls - 1); 2-d only
 dwf_status fine_apply_2d_range(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                                bool dagger, int prec, int s_lo, int s_hi, cudaStream_t st);
+// skip: optional device flag; nonzero leaves out untouched (one right-hand side)
 dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
-                         bool dagger, int prec, int s_chunk, cudaStream_t st);
+                         bool dagger, int prec, int s_chunk, cudaStream_t st, const int* skip = nullptr);
+
+// nrhs right-hand sides stored back to back with per-right-hand-side skip flags:
+// any nrhs on 2-d lattices, one right-hand side on 4-d lattices
+inline dwf_status fine_apply_rhs(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
+                                 bool dagger, int prec, int nrhs, const int* skip, cudaStream_t st) {
+    if (g.nd == 2) return fine_apply_2d_multi(g, U, psi, out, M5, mf, dagger, prec, nrhs, skip, st);
+    if (nrhs != 1) { set_error("4-d lattices take one right-hand side per call"); return DWF_ERR_UNSUPPORTED; }
+    return fine_apply_4d(g, U, psi, out, M5, mf, dagger, prec, 0, st, skip);
+}
 
 inline dwf_status fine_apply(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
                              bool dagger, int prec, cudaStream_t st, int s_chunk = 0) {

@@ -29,7 +29,7 @@ namespace dwf {
 namespace {
 
 constexpr int BK_MAX = 32;            // bound on the restart lengths
-constexpr int BMDOT_BLOCKS = 152;     // blocks per (right-hand side, basis vector) row of a Gram-Schmidt dot
+constexpr int BMDOT_BLOCKS = 608;     // blocks per right-hand side of a Gram-Schmidt multi-dot
 constexpr int CROW = (RED_GROUPS + 1) * RED_CSTRIDE;   // unsigneds of completion counters per row
 constexpr int PROW = RED_MAX * RED_BLOCKS;             // doubles of partial sums per row
 
@@ -167,51 +167,74 @@ __global__ void __launch_bounds__(RED_THREADS) k_bres_update(const float2* rin, 
     });
 }
 
-// Classical Gram-Schmidt dots: coef[j] = <W_j, w> / nrm[j] for j < k (k =
-// gridDim.y), per right-hand side, also summed into C[k][j] (set on the first
-// pass).  Grid (B, k, nrhs); W: device array of basis block pointers.
+// Classical Gram-Schmidt dots: coef[j] = <W_j, w> / nrm[j] for j < k, per
+// right-hand side, also summed into C[k][j] (set on the first pass).  Grid
+// (B, nrhs): each thread reads its elements of w once and of every W_j once
+// (k + 1 vectors per pass instead of 2 k), keeping the k partial dots in
+// registers (KM >= k, unrolled with guards).  The last block of a row sums the
+// per-block partials of every j in a fixed order.  W: device array of basis
+// block pointers.
+template <int KM>
 __global__ void __launch_bounds__(RED_THREADS) k_bmdot(float2* const* __restrict__ W, const float2* __restrict__ w,
-                                                       long long n, double* __restrict__ part, unsigned* counters,
-                                                       BGcr* g, int first, const int* skip) {
-    const int r = blockIdx.z, j = blockIdx.y;
+                                                       long long n, int k, double* __restrict__ part,
+                                                       unsigned* counters, BGcr* g, int first, const int* skip) {
+    const int r = blockIdx.y;
     if (skip && skip[r]) return;
-    const float4* Wj = reinterpret_cast<const float4*>(W[j] + r * n);
+    __shared__ const float4* Wp[KM];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) Wp[j] = reinterpret_cast<const float4*>(W[j] + r * n);
+    __syncthreads();
     const float4* w4 = reinterpret_cast<const float4*>(w + r * n);
-    const long long n2 = n >> 1;
-    float re = 0.f, im = 0.f;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + 3 * stride < n2; i += 4 * stride) {
-        const float4 a0 = Wj[i], a1 = Wj[i + stride], a2 = Wj[i + 2 * stride], a3 = Wj[i + 3 * stride];
-        const float4 b0 = w4[i], b1 = w4[i + stride], b2 = w4[i + 2 * stride], b3 = w4[i + 3 * stride];
-        cdot4(a0, b0, re, im); cdot4(a1, b1, re, im); cdot4(a2, b2, re, im); cdot4(a3, b3, re, im);
+    float re[KM], im[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) { re[j] = 0.f; im[j] = 0.f; }
+    ROW_LOOP(i, n >> 1) {
+        const float4 wi = w4[i];
+#pragma unroll
+        for (int j = 0; j < KM; ++j)
+            if (j < k) cdot4(Wp[j][i], wi, re[j], im[j]);
     }
-    for (; i < n2; i += stride) cdot4(Wj[i], w4[i], re, im);
-    double v[2] = {re, im};
-    block_sum<2>(v);
-    const size_t rowi = (size_t)r * BK_MAX + j;
-    double* pr = part + rowi * 2 * BMDOT_BLOCKS;
-    if (threadIdx.x == 0) {
-        pr[blockIdx.x] = v[0];
-        pr[BMDOT_BLOCKS + blockIdx.x] = v[1];
+    double* pr = part + (size_t)r * BK_MAX * 2 * BMDOT_BLOCKS;     // [j][re / im][block]
+#pragma unroll
+    for (int j0 = 0; j0 < KM; j0 += 4) {
+        if (j0 >= k) break;                                       // block-uniform
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { v[2 * q] = re[j0 + q]; v[2 * q + 1] = im[j0 + q]; }
+        block_sum<8>(v);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < k) {
+                    pr[(size_t)(j0 + q) * 2 * BMDOT_BLOCKS + blockIdx.x] = v[2 * q];
+                    pr[(size_t)(j0 + q) * 2 * BMDOT_BLOCKS + BMDOT_BLOCKS + blockIdx.x] = v[2 * q + 1];
+                }
     }
-    if (!grid_last_block(counters + rowi * CROW)) return;
+    if (!grid_last_block(counters + (size_t)r * BK_MAX * CROW)) return;
     __threadfence();
-    double w2[2] = {0.0, 0.0};
-    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
-        w2[0] += __ldcg(pr + bb);
-        w2[1] += __ldcg(pr + BMDOT_BLOCKS + bb);
+    for (int j = 0; j < k; ++j) {
+        double w2[2] = {0.0, 0.0};
+        for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
+            w2[0] += __ldcg(pr + (size_t)j * 2 * BMDOT_BLOCKS + bb);
+            w2[1] += __ldcg(pr + (size_t)j * 2 * BMDOT_BLOCKS + BMDOT_BLOCKS + bb);
+        }
+        block_sum<2>(w2);
+        if (threadIdx.x == 0) {
+            const double nn = g[r].nrm[j];
+            const double cr = nn > 0 ? w2[0] / nn : 0.0, ci = nn > 0 ? w2[1] / nn : 0.0;
+            g[r].coef[j][0] = cr;
+            g[r].coef[j][1] = ci;
+            g[r].C[k][j][0] = first ? cr : g[r].C[k][j][0] + cr;
+            g[r].C[k][j][1] = first ? ci : g[r].C[k][j][1] + ci;
+        }
     }
-    block_sum<2>(w2);
-    if (threadIdx.x == 0) {
-        const double nn = g[r].nrm[j];
-        const double cr = nn > 0 ? w2[0] / nn : 0.0, ci = nn > 0 ? w2[1] / nn : 0.0;
-        const int k = gridDim.y;
-        g[r].coef[j][0] = cr;
-        g[r].coef[j][1] = ci;
-        g[r].C[k][j][0] = first ? cr : g[r].C[k][j][0] + cr;
-        g[r].C[k][j][1] = first ? ci : g[r].C[k][j][1] + ci;
-    }
+}
+
+static void launch_bmdot(dim3 grid, float2* const* W, const float2* w, long long n, int k, double* part,
+                         unsigned* counters, BGcr* g, int first, const int* skip, cudaStream_t st) {
+    if (k <= 4)       k_bmdot<4><<<grid, RED_THREADS, 0, st>>>(W, w, n, k, part, counters, g, first, skip);
+    else if (k <= 8)  k_bmdot<8><<<grid, RED_THREADS, 0, st>>>(W, w, n, k, part, counters, g, first, skip);
+    else if (k <= 16) k_bmdot<16><<<grid, RED_THREADS, 0, st>>>(W, w, n, k, part, counters, g, first, skip);
+    else              k_bmdot<32><<<grid, RED_THREADS, 0, st>>>(W, w, n, k, part, counters, g, first, skip);
 }
 
 // w -= sum_{j<k} coef_j W_j per right-hand side.  FINAL: also nrm[k] = |w|^2,
@@ -498,8 +521,8 @@ static dim3 row_grid(long long n2, int nrhs, int cap = 1216) {
 
 static dwf_status bapply_A(BSolver& s, const float2* in, float2* out, const int* skip) {
     dwf_mg* h = s.h;
-    DWF_TRY(fine_apply_2d_multi(h->G, h->Ulo, in, s.v->tmp, h->M5, h->mf, false, h->prm.fine_prec, s.nrhs, skip, s.st));
-    DWF_TRY(fine_apply_2d_multi(h->G, h->Ulo, s.v->tmp, out, h->M5, 1.0, true, h->prm.fine_prec, s.nrhs, skip, s.st));
+    DWF_TRY(fine_apply_rhs(h->G, h->Ulo, in, s.v->tmp, h->M5, h->mf, false, h->prm.fine_prec, s.nrhs, skip, s.st));
+    DWF_TRY(fine_apply_rhs(h->G, h->Ulo, s.v->tmp, out, h->M5, 1.0, true, h->prm.fine_prec, s.nrhs, skip, s.st));
     return DWF_OK;
 }
 
@@ -511,11 +534,11 @@ static dwf_status borthogonalise(BSolver& s, BGcr* g, float2* const* Wb, int k, 
     const int rg = red_grid4(n);
     const dim3 rgrid((unsigned)rg, (unsigned)s.nrhs);
     if (k > 0) {
-        const dim3 mgrid((unsigned)(rg < BMDOT_BLOCKS ? rg : BMDOT_BLOCKS), (unsigned)k, (unsigned)s.nrhs);
+        const dim3 mgrid((unsigned)(rg < BMDOT_BLOCKS ? rg : BMDOT_BLOCKS), (unsigned)s.nrhs);
         const dim3 egrid = row_grid(n >> 1, s.nrhs, 152 * 16);
         const int passes = s.h->prm.cgs_passes;
         for (int pass = 0; pass < passes; ++pass) {
-            k_bmdot<<<mgrid, RED_THREADS, 0, s.st>>>(dW, Wb[k], n, v.mpart, v.mcount, g, pass == 0, skip);
+            launch_bmdot(mgrid, dW, Wb[k], n, k, v.mpart, v.mcount, g, pass == 0, skip, s.st);
             if (pass + 1 < passes)
                 k_bmaxpy<false><<<egrid, RED_THREADS, 0, s.st>>>(Wb[k], dW, g, k, res, n, v.red, steps, skip);
             else
@@ -689,8 +712,8 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
     if (!h || !B || !X) { set_error("NULL argument"); return DWF_ERR_ARG; }
     if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
     if (!(tol > 0.0)) { set_error("tol must be > 0"); return DWF_ERR_ARG; }
-    if (h->mg.nd != 2 || (nrhs > 1 && h->mg.ncd != 16)) {
-        set_error("the batched solver supports 2-d lattices, with nvec = 8 for more than one right-hand side");
+    if (nrhs > 1 && (h->mg.nd != 2 || h->mg.ncd != 16)) {
+        set_error("more than one right-hand side per hierarchy needs a 2-d lattice with nvec = 8");
         return DWF_ERR_UNSUPPORTED;
     }
     if (h->prm.gcr_restart < 1 || h->prm.gcr_restart > BK_MAX || h->prm.post_smooth > BK_MAX ||
@@ -746,7 +769,7 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
             first = false;
         } else {
             DWF_CHECK_CUDA(cudaMemcpyAsync(v.odone, hod, nrhs * sizeof(int), cudaMemcpyHostToDevice, s.st));
-            DWF_TRY(fine_apply_2d_multi(h->G, h->U64, X, v.t64, h->M5, h->mf, false, DWF_F64, nrhs, v.odone, s.st));
+            DWF_TRY(fine_apply_rhs(h->G, h->U64, X, v.t64, h->M5, h->mf, false, DWF_F64, nrhs, v.odone, s.st));
             k_bsub64<<<eg64, 256, 0, s.st>>>(v.r64, B, v.t64, n, v.odone);
             k_bnorm2_64<<<rg64, RED_THREADS, 0, s.st>>>(v.r64, n, v.red, v.rn2, v.odone);
             DWF_CHECK_LAUNCH();
@@ -776,7 +799,7 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
         // correction system in FP32: A e = D_PV^dag r / |r|
         k_bd2f_scale<<<eg64, 256, 0, s.st>>>(v.ps, v.r64, v.scale, n, v.idone);
         DWF_CHECK_LAUNCH();
-        DWF_TRY(fine_apply_2d_multi(h->G, h->Ulo, v.ps, v.rA, h->M5, 1.0, true, h->prm.fine_prec, nrhs, v.idone, s.st));
+        DWF_TRY(fine_apply_rhs(h->G, h->Ulo, v.ps, v.rA, h->M5, 1.0, true, h->prm.fine_prec, nrhs, v.idone, s.st));
         k_bcopy<<<eg32, 256, 0, s.st>>>(v.r, v.rA, n, v.idone);
         k_bnorm2_32<<<rg32, RED_THREADS, 0, s.st>>>(v.rA, n, v.red, v.rA2, v.idone);
         DWF_CHECK_LAUNCH();
