@@ -29,7 +29,9 @@ namespace dwf {
 namespace {
 
 constexpr int BK_MAX = 32;            // bound on the restart lengths
-constexpr int BMDOT_BLOCKS = 608;     // blocks per right-hand side of a Gram-Schmidt multi-dot
+constexpr int BMDOT_BLOCKS = 608;     // partial slots per (right-hand side, basis vector) of a Gram-Schmidt dot
+constexpr int BMDOT_ROW_BLOCKS = 152; // blocks per row of the per-row form
+constexpr long long BMDOT_FUSE_N = 8LL << 20;   // complex values from which the fused form is used
 constexpr int CROW = (RED_GROUPS + 1) * RED_CSTRIDE;   // unsigneds of completion counters per row
 constexpr int PROW = RED_MAX * RED_BLOCKS;             // doubles of partial sums per row
 
@@ -167,7 +169,54 @@ __global__ void __launch_bounds__(RED_THREADS) k_bres_update(const float2* rin, 
     });
 }
 
-// Classical Gram-Schmidt dots: coef[j] = <W_j, w> / nrm[j] for j < k, per
+// Classical Gram-Schmidt dots: coef[j] = <W_j, w> / nrm[j] for j < k (k =
+// gridDim.y), per right-hand side, also summed into C[k][j] (set on the first
+// pass).  Grid (B, k, nrhs); W: device array of basis block pointers.
+__global__ void __launch_bounds__(RED_THREADS) k_bmdot_rows(float2* const* __restrict__ W, const float2* __restrict__ w,
+                                                       long long n, double* __restrict__ part, unsigned* counters,
+                                                       BGcr* g, int first, const int* skip) {
+    const int r = blockIdx.z, j = blockIdx.y;
+    if (skip && skip[r]) return;
+    const float4* Wj = reinterpret_cast<const float4*>(W[j] + r * n);
+    const float4* w4 = reinterpret_cast<const float4*>(w + r * n);
+    const long long n2 = n >> 1;
+    float re = 0.f, im = 0.f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n2; i += 4 * stride) {
+        const float4 a0 = Wj[i], a1 = Wj[i + stride], a2 = Wj[i + 2 * stride], a3 = Wj[i + 3 * stride];
+        const float4 b0 = w4[i], b1 = w4[i + stride], b2 = w4[i + 2 * stride], b3 = w4[i + 3 * stride];
+        cdot4(a0, b0, re, im); cdot4(a1, b1, re, im); cdot4(a2, b2, re, im); cdot4(a3, b3, re, im);
+    }
+    for (; i < n2; i += stride) cdot4(Wj[i], w4[i], re, im);
+    double v[2] = {re, im};
+    block_sum<2>(v);
+    const size_t rowi = (size_t)r * BK_MAX + j;
+    double* pr = part + rowi * 2 * BMDOT_BLOCKS;
+    if (threadIdx.x == 0) {
+        pr[blockIdx.x] = v[0];
+        pr[BMDOT_BLOCKS + blockIdx.x] = v[1];
+    }
+    if (!grid_last_block(counters + rowi * CROW)) return;
+    __threadfence();
+    double w2[2] = {0.0, 0.0};
+    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
+        w2[0] += __ldcg(pr + bb);
+        w2[1] += __ldcg(pr + BMDOT_BLOCKS + bb);
+    }
+    block_sum<2>(w2);
+    if (threadIdx.x == 0) {
+        const double nn = g[r].nrm[j];
+        const double cr = nn > 0 ? w2[0] / nn : 0.0, ci = nn > 0 ? w2[1] / nn : 0.0;
+        const int k = gridDim.y;
+        g[r].coef[j][0] = cr;
+        g[r].coef[j][1] = ci;
+        g[r].C[k][j][0] = first ? cr : g[r].C[k][j][0] + cr;
+        g[r].C[k][j][1] = first ? ci : g[r].C[k][j][1] + ci;
+    }
+}
+
+// The same dots for vectors larger than L2: coef[j] = <W_j, w> / nrm[j] for j < k, per
 // right-hand side, also summed into C[k][j] (set on the first pass).  Grid
 // (B, nrhs): each thread reads its elements of w once and of every W_j once
 // (k + 1 vectors per pass instead of 2 k), keeping the k partial dots in
@@ -534,11 +583,15 @@ static dwf_status borthogonalise(BSolver& s, BGcr* g, float2* const* Wb, int k, 
     const int rg = red_grid4(n);
     const dim3 rgrid((unsigned)rg, (unsigned)s.nrhs);
     if (k > 0) {
-        const dim3 mgrid((unsigned)(rg < BMDOT_BLOCKS ? rg : BMDOT_BLOCKS), (unsigned)s.nrhs);
+        const bool fused = n >= BMDOT_FUSE_N;
+        const int nb = fused ? BMDOT_BLOCKS : BMDOT_ROW_BLOCKS;
+        const dim3 mgrid((unsigned)(rg < nb ? rg : nb), fused ? (unsigned)s.nrhs : (unsigned)k,
+                         fused ? 1u : (unsigned)s.nrhs);
         const dim3 egrid = row_grid(n >> 1, s.nrhs, 152 * 16);
         const int passes = s.h->prm.cgs_passes;
         for (int pass = 0; pass < passes; ++pass) {
-            launch_bmdot(mgrid, dW, Wb[k], n, k, v.mpart, v.mcount, g, pass == 0, skip, s.st);
+            if (fused) launch_bmdot(mgrid, dW, Wb[k], n, k, v.mpart, v.mcount, g, pass == 0, skip, s.st);
+            else k_bmdot_rows<<<mgrid, RED_THREADS, 0, s.st>>>(dW, Wb[k], n, v.mpart, v.mcount, g, pass == 0, skip);
             if (pass + 1 < passes)
                 k_bmaxpy<false><<<egrid, RED_THREADS, 0, s.st>>>(Wb[k], dW, g, k, res, n, v.red, steps, skip);
             else
