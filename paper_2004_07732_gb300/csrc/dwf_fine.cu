@@ -150,6 +150,10 @@ __device__ __forceinline__ void dwf2d_site(const typename LT::store* __restrict_
 #pragma unroll
         for (int k = 0; k < PF; ++k) win[k] = win[k + 1];
         if (s + PF + 1 <= slast) win[PF] = ld_sp(psi, (long long)(s + PF + 1) * V + site);
+        // L2 prefetch two planes beyond the window, one lane per 128-byte line:
+        // more bytes in flight without the registers of a deeper window
+        if (s + PF + 3 <= slast && (threadIdx.x & (128 / sizeof(Sp2<R>) - 1)) == 0)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + (long long)(s + PF + 3) * V + site));
         Sp2<R> o = hop2d<R, DAG>(nb_xf, nb_xb, nb_yf, nb_yb, u0f, u0b, u1f, u1b);
         o.c0 = o.c0 + scale(cur.c0, diag);
         o.c1 = o.c1 + scale(cur.c1, diag);
