@@ -495,6 +495,11 @@ __global__ void __launch_bounds__(CM_WARPS * 32, 3) k_coarse_mma(const uint4* __
     const uint4* A = Ym + (long long)xc * (9 * 3 * 6 * 32) + lane;
 #pragma unroll 1
     for (int dir = 0; dir < 9; ++dir) {
+        // L2 prefetch of the next direction's 18 fragment rows (one lane per 128-byte line)
+        if (dir + 1 < 9 && (lane & 7) == 0) {
+#pragma unroll
+            for (int q = 0; q < 18; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(A + ((dir + 1) * 18 + q) * 32));
+        }
         const int nb = coarse_nb32(p, xc, dir);
         const float* vin = reinterpret_cast<const float*>(in + (colv ? sB : 0) * slice + (long long)nb * 48) + part;
 #pragma unroll
