@@ -139,6 +139,26 @@ def test_mg_solve_4d_reaches_tolerance(dw, nvec):
     h.close()
 
 
+def test_mg_solve_batched_4d_one_rhs_and_rejects_more(dw):
+    """The batched entry point takes a 4-d hierarchy with one right-hand side (the K-cycle
+    mg_solve runs) and reaches the same x; more than one right-hand side per 4-d hierarchy
+    is refused before any work."""
+    dims, Ls, M5, mf, nvec = (6, 6, 6, 6), 4, 1.8, 0.05, 6
+    h, U, rng = _setup4(dw, dims, Ls, nvec, 91, M5=M5, mf=mf, extra={"setup_maxiter": 100})
+    b = synth.gaussian_spinor(rng, dims, Ls, "su3").reshape(-1)
+    x = torch.empty(len(b), dtype=torch.complex128, device="cuda")
+    stats, status = dw.mg_solve_batched(h, _dev(b), x, 1, tol=1e-10)
+    D = dirac.dwf_matrix(U, dims, Ls, M5, mf, group="su3")
+    res = np.linalg.norm(b - D @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert status == 0 and res <= 1e-10 and abs(res - stats[0]["true_residual"]) < 1e-12
+    b2 = torch.cat([_dev(b), _dev(b)])
+    x2 = torch.empty_like(b2)
+    with pytest.raises(dw.DwfError) as e:
+        dw.mg_solve_batched(h, b2, x2, 2, tol=1e-10)
+    assert e.value.status == 6
+    h.close()
+
+
 def test_mg_solve_4d_bench_size(dw):
     """The bench's 4-d workload (16^3 x 32 x Ls=16, eps 0.3, M5 1.8, m 0.01; Nvec 24 on 2^4 blocks,
     16 post-smoothing steps, coarse tolerance 0.4) reaches 1e-10.  The residual b - D x is
