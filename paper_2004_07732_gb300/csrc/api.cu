@@ -45,8 +45,6 @@ dwf_status check_geom(const dwf_geom* g, Geom* out) {
     return DWF_OK;
 }
 
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
 // ----------------------------------------------------------------------------
 // link conversion FP64 -> storage format
 // ----------------------------------------------------------------------------

@@ -62,6 +62,8 @@ dwf_status check_geom(const dwf_geom* g, Geom* out);
 bool valid_prec(int prec);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+// spinor buffers are read as float4 / double2: 16-byte alignment is part of the ABI
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // ---------------------------------------------------------------------------
 // complex arithmetic on float2 / double2

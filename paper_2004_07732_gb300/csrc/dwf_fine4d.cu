@@ -368,7 +368,6 @@ static dwf_status check_packed(const dwf_geom* g, Geom* G) {
     if (G->nd != 4) { set_error("the packed layout is defined for 4-d SU(3) lattices"); return DWF_ERR_UNSUPPORTED; }
     return DWF_OK;
 }
-static bool aligned16p(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
 
 }  // namespace dwf
@@ -415,7 +414,7 @@ dwf_status dwf_pack_spinor(const dwf_geom* g, const void* psi, void* packed, voi
     DWF_TRY(check_packed(g, &G));
     const long long NB = (G.V + 31) / 32, n = (long long)G.Ls * NB * 32;
     if (!psi || !packed) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
-    if (!aligned16p(psi) || !aligned16p(packed)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
+    if (!aligned16(psi) || !aligned16(packed)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
     if (psi == packed) { set_error("psi and packed must be distinct buffers"); return DWF_ERR_ARG; }
     cudaStream_t st = as_stream(stream);
     k_pack_spinor<<<grid_for(n), 256, 0, st>>>((const float4*)psi, (float4*)packed, G.V, NB, n);
@@ -429,7 +428,7 @@ dwf_status dwf_unpack_spinor(const dwf_geom* g, const void* packed, void* psi, v
     DWF_TRY(check_packed(g, &G));
     const long long NB = (G.V + 31) / 32, n = (long long)G.Ls * G.V;
     if (!psi || !packed) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
-    if (!aligned16p(psi) || !aligned16p(packed)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
+    if (!aligned16(psi) || !aligned16(packed)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
     if (psi == packed) { set_error("psi and packed must be distinct buffers"); return DWF_ERR_ARG; }
     cudaStream_t st = as_stream(stream);
     k_unpack_spinor<<<grid_for(n), 256, 0, st>>>((const float4*)packed, (float4*)psi, G.V, NB, n);
@@ -443,7 +442,7 @@ dwf_status dwf_apply_packed(const dwf_geom* g, const void* U_packed, const void*
     Geom G;
     DWF_TRY(check_packed(g, &G));
     if (!U_packed || !psi || !out) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
-    if (!aligned16p(psi) || !aligned16p(out)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
+    if (!aligned16(psi) || !aligned16(out)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
     if (psi == out) { set_error("psi and out must be distinct buffers"); return DWF_ERR_ARG; }
     return fine_apply_4d_packed(G, U_packed, psi, out, M5, mf, dagger != 0, prec, as_stream(stream));
 }

@@ -47,8 +47,6 @@ dwf_status host_pipe(HostPipe** out) {
     return DWF_OK;
 }
 
-bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
-
 size_t link_bytes(int prec) {
     return prec == DWF_F64 ? 16 : (prec == DWF_F32 ? 8 : 4);
 }
