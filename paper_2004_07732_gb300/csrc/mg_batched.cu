@@ -8,14 +8,18 @@
 // block of its row, so one fixed launch sequence serves any set of
 // still-active systems and the coarse cycle stays a single CUDA graph.  The
 // coarse operator on the nrhs * Ls_c columns is the tensor-core contraction
-// (mg_coarse_tc.cu).  Per right-hand side the iteration is exactly the
+// (mg_coarse_tc.cu).  With one right-hand side it is the one-vector stencil:
+// that is the path mg_solve takes with the GCR coarse solver on 2-d and 4-d
+// lattices (4-d hierarchies take one right-hand side per call).  Per
+// right-hand side the iteration is exactly the
 // one-vector solver's: FP64 reliable updates of the true residual around
 // FGCR(gcr_restart) in FP32, the wall restriction, coarse GCR to coarse_tol,
 // prolongation and post_smooth GCR steps.
 //
 // Reductions: one row of partial sums and completion counters per right-hand
-// side (and per basis vector for the Gram-Schmidt dots), so the rows finish
-// independently and each result is summed in a fixed order.
+// side (and per basis vector for the Gram-Schmidt dots of vectors that fit in
+// L2; larger vectors take all basis vectors in one pass over w), so the rows
+// finish independently and each result is summed in a fixed order.
 #include <chrono>
 #include <mutex>
 #include <string.h>

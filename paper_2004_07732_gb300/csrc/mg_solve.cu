@@ -1,5 +1,10 @@
 // The K-cycle solve of Sec. 2.3 ("Summary") with the Table kcycle parameters.
 //
+// mg_solve hands the default configuration (restarted GCR as the coarse
+// solver, coarse_persistent != 2) to the batched K-cycle of mg_batched.cu with
+// one right-hand side.  This file runs the same iteration for the CGNR coarse
+// solver and for the persistent coarse GCR:
+//
 // Outer loop, FP64 (reliable updates): r = b - D_DW x with the FP64 operator;
 // stop when ||r|| / ||b|| <= tol; otherwise solve the left-preconditioned
 // correction system  D_PV^dag D_DW e = D_PV^dag r  approximately in FP32
@@ -8,8 +13,9 @@
 // Inner solver: flexible GCR, restart gcr_restart, on A = D_PV^dag D_DW with
 // the preconditioner M(r):
 //   1. restrict the wall of r onto the coarse walls (Eq. TruncProjectInterpolate);
-//   2. solve Dhat_PV^dag Dhat_DW e_c = r_c with CGNR on the coarse normal
-//      operator to coarse_tol (at most coarse_maxiter iterations);
+//   2. solve Dhat_PV^dag Dhat_DW e_c = r_c to coarse_tol (at most
+//      coarse_maxiter iterations): CGNR on the coarse normal operator, or the
+//      persistent restarted GCR;
 //   3. prolong e_c onto the fine walls;
 //   4. post-smooth: post_smooth GCR iterations on A z = r starting from the
 //      prolonged correction (0 pre-smoothing).
