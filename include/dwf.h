@@ -108,8 +108,8 @@ DWF_API dwf_status dwf_apply_host(const dwf_geom* g, const void* U_host, const v
 
 /* Batched apply: out_r = D_DW(mf) psi_r (or the adjoint) for nrhs right-hand
  * sides, each on its own 2-d U(1) lattice geoms[r] with links U[r] (pointers may
- * repeat), all in ONE persistent kernel launch over the concatenated site
- * ranges.  geoms, U, psi, out are HOST arrays of nrhs entries (the latter three
+ * repeat), all in ONE kernel launch over the concatenated site ranges (one
+ * thread block per range of sites of one right-hand side).  geoms, U, psi, out are HOST arrays of nrhs entries (the latter three
  * holding device pointers).  Operator, layouts and precisions as dwf_apply.
  * nrhs <= 256.  (The paper treats one system at a time; this is the
  * many-right-hand-side form of the same operator.) */
@@ -139,7 +139,9 @@ DWF_API dwf_status dwf_pvdag_apply(const dwf_geom* g, const void* U, const void*
  * DWF_ERR_ARG.  All calls on a device share that array: calls that overlap on
  * the GPU race and must be ordered on one stream.  The first call on each device
  * looks up the array's address (cudaGetSymbolAddress); make it before any
- * stream capture.  Arguments as dwf_pvdag_apply without `tmp`. */
+ * stream capture.  The address is cached per device ordinal for the life of
+ * the process, so do not call this entry point on a device after
+ * cudaDeviceReset.  Arguments as dwf_pvdag_apply without `tmp`. */
 DWF_API dwf_status dwf_pvdag_apply_noalloc(const dwf_geom* g, const void* U, const void* psi, void* out,
                                    double M5, double mf, int prec, void* stream);
 
@@ -270,13 +272,17 @@ typedef struct {
                              autotuned -- the first use for a given nrhs times mma.sync with 1, 2
                              and 4 column tiles per warp and, with FP16 blocks and >= 128
                              columns, tcgen05 with the accumulator in tensor memory, and keeps
-                             the fastest; 1 = tcgen05 wherever eligible                        */
+                             the fastest; 1 = tcgen05 wherever eligible (mma.sync with 4
+                             tiles elsewhere); 2, 3, 4 = mma.sync with 1, 2, 4 column tiles
+                             per warp (fixed forms, for testing each one)                     */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;
 
-/* Fill p with the Table kcycle defaults (2-level: level-3 CGNR settings on the
- * coarse level). */
+/* Fill p with the Table kcycle defaults of the paper's level 2 on the coarse
+ * level: restarted GCR on Dhat_PV^dag Dhat_DW to a relative residual of 0.25
+ * (coarse_solver = 1, coarse_restart 8, coarse_maxiter 1024), FP16 coarse blocks,
+ * 8 post-smoothing steps, outer FGCR(16). */
 DWF_API void dwf_mg_default_params(dwf_mg_params* p);
 
 /* Set up the two-level hierarchy of Sec. 2.3 for D_DW(mf) with links U
@@ -294,15 +300,24 @@ DWF_API dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double 
 /* Solve D_DW(mf) x = b (complex128 b, x) with the K-cycle of Sec. 2.3:
  * FP64 reliable updates of the true residual around restarted flexible GCR on
  * D_PV^dag D_DW (FP32 spinors, fine_prec links), preconditioned by truncated
- * wall restriction (Eq. TruncProjectInterpolate), coarsest CGNR on
- * (Dhat_PV^dag Dhat_DW)^dag (Dhat_PV^dag Dhat_DW) to coarse_tol, prolongation and
- * post_smooth GCR iterations.  Stops when ||b - D_DW x|| / ||b|| <= tol
+ * wall restriction (Eq. TruncProjectInterpolate), a coarse solve to coarse_tol
+ * (coarse_solver = 1, the default: restarted GCR on Dhat_PV^dag Dhat_DW;
+ * coarse_solver = 0: CGNR on (Dhat_PV^dag Dhat_DW)^dag (Dhat_PV^dag Dhat_DW)),
+ * prolongation and post_smooth GCR iterations.  Stops when ||b - D_DW x|| / ||b|| <= tol
  * (recomputed in FP64); DWF_ERR_NOCONV after maxiter outer iterations. */
 DWF_API dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, int maxiter, dwf_solve_stats* stats,
                             void* stream);
 
 /* Free the handle and everything it owns. */
 DWF_API void mg_destroy(dwf_mg* h);
+
+/* DWF_OK if the hierarchy h was set up for exactly these links (complex128,
+ * canonical layout, compared bitwise on the GPU), M5 and mf; DWF_ERR_ARG with
+ * a message otherwise.  mg_solve always solves with the operator of mg_setup,
+ * so a caller whose links may have moved since (a training step, a
+ * finite-difference probe) checks here first.  The paper has no counterpart.
+ * Synchronises `stream`. */
+DWF_API dwf_status mg_check_operator(const dwf_mg* h, const void* U, double M5, double mf, void* stream);
 
 /* Coarse geometry (nd, coarse L, Ls = Ls_c) and coarse dof per site (2*nvec). */
 DWF_API dwf_status mg_coarse_geom(const dwf_mg* h, dwf_geom* coarse, int* ncdof);
@@ -329,8 +344,10 @@ DWF_API dwf_status mg_restrict(const dwf_mg* h, const void* r_fine, void* r_coar
 DWF_API dwf_status mg_prolong(const dwf_mg* h, const void* e_coarse, void* e_fine, void* stream);
 
 /* Coarse Dhat_DW(mf) (or its adjoint) of Eq. coarsenDW on complex64 coarse
- * vectors; mf = 1 gives Dhat_PV.  FP32 arithmetic on the FP32 copy of the
- * Galerkin blocks. */
+ * vectors; mf = 1 gives Dhat_PV.  FP32 arithmetic on the handle's coarse block
+ * storage (coarse_block_prec: FP16 blocks by default, or the FP32 copy); the
+ * adjoint reads the same blocks through Dhat_W^dag = sigma_3 Dhat_W sigma_3
+ * (the generic narrow-block stencil reads pre-transposed FP32 adjoint blocks). */
 DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, double mf, int dagger,
                                    void* stream);
 

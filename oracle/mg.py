@@ -127,6 +127,73 @@ def coarse_dwf(Dhat_w, Ls_c, mf, nvec):
     return dirac.dwf_from_kernel(Dhat_w, Ls_c, mf, Pp, Pm)
 
 
+def sigma3(Vc, nvec):
+    """sigma_3 = diag(+1 x nvec, -1 x nvec) on every coarse site (the coarse gamma_5)."""
+    return sp.kron(sp.identity(Vc), sp.diags(np.concatenate([np.ones(nvec), -np.ones(nvec)]))).tocsr()
+
+
+def coarse_dwf_dagger_g5(Dhat_w, Ls_c, mf, nvec):
+    """Dhat_DW(m)^dag of Eq. coarsenDW with the kernel's adjoint written as
+    sigma_3 Dhat_W sigma_3.
+
+    The chirality-preserving prolongator (gamma_5 P = P sigma_3) makes the
+    Galerkin kernel gamma_5-hermitian, Dhat_W^dag = sigma_3 Dhat_W sigma_3, so
+    for an exact kernel this is the plain adjoint.  For a kernel whose blocks
+    were rounded one by one (FP16 storage) the two differ by the rounding, and
+    this form is the adjoint that uses one stored copy of the blocks.
+    """
+    Vc = Dhat_w.shape[0] // (2 * nvec)
+    S3 = sigma3(Vc, nvec)
+    # a kernel K with K^dag = sigma_3 Dhat_W sigma_3
+    K = (S3 @ Dhat_w.conj().T @ S3).tocsr()
+    return dirac.dagger(coarse_dwf(K, Ls_c, mf, nvec))
+
+
+def kernel_blocks(Dhat_w, cdims, ncd):
+    """Per-site blocks of a nearest-neighbour coarse kernel: Y[xc][dir] = block
+    (xc, neighbour(xc, dir)), dir 0 = self, then +mu, -mu for mu = 0..d-1.
+    Every coarse extent must be >= 3 (with extent 2 the two hops land on one
+    neighbour and their blocks cannot be told apart)."""
+    if min(cdims) < 3:
+        raise ValueError("kernel_blocks needs coarse extents >= 3")
+    Vc = int(np.prod(cdims))
+    nd = len(cdims)
+    D = Dhat_w.tocsr()
+    Y = np.zeros((Vc, 2 * nd + 1, ncd, ncd), dtype=complex)
+    nbrs = [np.arange(Vc)]
+    for mu in range(nd):
+        nbrs.append(dirac.neighbour(cdims, mu, +1)[0])
+        nbrs.append(dirac.neighbour(cdims, mu, -1)[0])
+    for xc in range(Vc):
+        rows = D[xc * ncd:(xc + 1) * ncd]
+        for d, nb in enumerate(nbrs):
+            Y[xc, d] = rows[:, nb[xc] * ncd:(nb[xc] + 1) * ncd].toarray()
+    return Y
+
+
+def kernel_from_blocks(Y, cdims):
+    """Assemble the sparse coarse kernel from per-site blocks Y[xc][dir] (the
+    layout of kernel_blocks).  On lattices with extent 2 the +mu and -mu
+    neighbours coincide and their blocks add, as in the operator."""
+    Y = np.asarray(Y)
+    Vc, ndir, ncd, _ = Y.shape
+    nd = (ndir - 1) // 2
+    nbrs = [np.arange(Vc)]
+    for mu in range(nd):
+        nbrs.append(dirac.neighbour(cdims, mu, +1)[0])
+        nbrs.append(dirac.neighbour(cdims, mu, -1)[0])
+    a = np.arange(ncd)
+    rows, cols, vals = [], [], []
+    for d, nb in enumerate(nbrs):
+        r = (np.arange(Vc)[:, None, None] * ncd + a[None, :, None]) + 0 * a[None, None, :]
+        c = (nb[:, None, None] * ncd + a[None, None, :]) + 0 * a[None, :, None]
+        rows.append(r.ravel())
+        cols.append(c.ravel())
+        vals.append(Y[:, d].ravel())
+    n = Vc * ncd
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
 def restrict(r, P, Ls, Ls_c, nd, nc, nvec):
     """Truncated restriction onto the coarse walls (Eq. TruncProjectInterpolate)."""
     nf = P.shape[0]

@@ -117,3 +117,97 @@ def gcr(apply_A, b, x0=None, tol=0.0, maxiter=8, precond=None):
         AZ.append(w)
         k += 1
     return x, r, k
+
+
+def bicgstab_l(apply_A, f, ell=6, tol=1e-10, max_cycles=10000, x0=None, stop=None, callback=None):
+    """BiCGStab(l) of Sleijpen & Fokkema (1993) for A x = f, the solver the paper
+    compares against as "BiCGStab-6 on D_PV^dag D_DW" (Sec. 2.3, Sec. 3).
+
+    One cycle makes l BiCG steps (each extends the residuals r_0..r_j and the
+    search directions u_0..u_j by one power of A, with the shadow residual
+    rt = the initial residual) followed by a minimal-residual step: the
+    residual r_0 - sum_j g_j r_j over r_1..r_l is minimised (modified
+    Gram-Schmidt of r_1..r_l, then back substitution for g).  Inner products
+    are <a, b> = a^dag b.  The cycle ends when stop(x) is true (default:
+    ||f - A x|| <= tol ||f||, on the recursive residual).  callback(x, r, R)
+    sees the iterate, the residual and the Gram-Schmidt-orthogonalised
+    r_1..r_l of every cycle.  Returns (x, applications of A).
+    """
+    f = np.asarray(f, dtype=complex).ravel()
+    x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=complex).ravel()
+    r = f - apply_A(x) if x0 is not None else f.copy()
+    nA = 1 if x0 is not None else 0
+    fn = norm(f)
+    if fn == 0.0:
+        return np.zeros_like(f), nA
+    if stop is None:
+        def stop(_x):
+            return False
+    rt = r.copy()
+    u = np.zeros_like(f)
+    rho0, alpha, omega = 1.0 + 0j, 0.0 + 0j, 1.0 + 0j
+    for _ in range(max_cycles):
+        if norm(r) <= tol * fn or stop(x):
+            break
+        R = [r] + [None] * ell
+        U = [u] + [None] * ell
+        rho0 = -omega * rho0
+        for j in range(ell):                      # BiCG part
+            rho1 = vdot(rt, R[j])
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                U[i] = R[i] - beta * U[i]
+            U[j + 1] = apply_A(U[j])
+            nA += 1
+            alpha = rho0 / vdot(rt, U[j + 1])
+            for i in range(j + 1):
+                R[i] = R[i] - alpha * U[i + 1]
+            R[j + 1] = apply_A(R[j])
+            nA += 1
+            x = x + alpha * U[0]
+        # MR part: modified Gram-Schmidt of R[1..l]
+        tau = np.zeros((ell + 1, ell + 1), dtype=complex)
+        sigma = np.zeros(ell + 1)
+        gp = np.zeros(ell + 1, dtype=complex)
+        for j in range(1, ell + 1):
+            for i in range(1, j):
+                tau[i, j] = vdot(R[i], R[j]) / sigma[i]
+                R[j] = R[j] - tau[i, j] * R[i]
+            sigma[j] = vdot(R[j], R[j]).real
+            gp[j] = vdot(R[j], R[0]) / sigma[j]
+        g = np.zeros(ell + 1, dtype=complex)
+        g[ell] = gp[ell]
+        omega = g[ell]
+        for j in range(ell - 1, 0, -1):
+            g[j] = gp[j] - sum(tau[j, i] * g[i] for i in range(j + 1, ell + 1))
+        g2 = np.zeros(ell + 1, dtype=complex)
+        for j in range(1, ell):
+            g2[j] = g[j + 1] + sum(tau[j, i] * g[i + 1] for i in range(j + 1, ell))
+        x = x + g[1] * R[0]
+        R[0] = R[0] - gp[ell] * R[ell]
+        U[0] = U[0] - g[ell] * U[ell]
+        for j in range(1, ell):
+            U[0] = U[0] - g[j] * U[j]
+            x = x + g2[j] * R[j]
+            R[0] = R[0] - gp[j] * R[j]
+        r, u = R[0], U[0]
+        if callback is not None:
+            callback(x, r, R[1:])
+    return x, nA
+
+
+def bicgstab_dw(Ddw, Dpv_dag, b, ell=6, tol=1e-10, max_cycles=10000):
+    """BiCGStab(l) on D_PV^dag D_DW x = D_PV^dag b, stopped when the true residual
+    of the original system ||b - D_DW x|| / ||b|| <= tol (checked after every cycle).
+    Returns (x, fine applications, true relative residual); one application of the
+    preconditioned operator counts as two fine applications (D_DW, D_PV^dag)."""
+    b = np.asarray(b, dtype=complex).ravel()
+    bn = norm(b)
+    A = (Dpv_dag @ Ddw).tocsr()
+
+    def stop(x):
+        return norm(b - Ddw @ x) <= tol * bn
+
+    x, nA = bicgstab_l(lambda v: A @ v, Dpv_dag @ b, ell=ell, tol=0.0, max_cycles=max_cycles, stop=stop)
+    return x, 2 * nA + 1, norm(b - Ddw @ x) / bn

@@ -12,6 +12,6 @@ from ._lib import (  # noqa: F401
 from ._lib import (  # noqa: F401
     MgParams, Multigrid, mg_default_params, mg_setup, mg_solve, mg_destroy, mg_get_prolongator,
     mg_get_null_vectors, mg_get_coarse_links, mg_restrict, mg_prolong, mg_coarse_apply, mg_coarse_apply_multi,
-    mg_solve_batched, mg_solve_groups, mg_coarse_tc_form,
+    mg_solve_batched, mg_solve_groups, mg_coarse_tc_form, mg_check_operator,
 )
 from .autograd import DwfSolve, solve  # noqa: F401,E402

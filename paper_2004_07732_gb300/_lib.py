@@ -110,6 +110,7 @@ def _setup_signatures(L):
         "mg_solve_batched": [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
         "mg_solve_groups": [_I, ctypes.POINTER(_VP), ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                             _D, _I, ctypes.POINTER(ctypes.POINTER(SolveStats))],
+        "mg_check_operator": [_VP, _VP, _D, _D, _VP],
         "mg_coarse_geom": [_VP, G, ctypes.POINTER(ctypes.c_int)],
         "mg_get_prolongator": [_VP, _VP, _VP],
         "mg_get_null_vectors": [_VP, _VP, _VP],
@@ -497,6 +498,13 @@ def mg_solve_groups(mgs, bs, xs, nrhs, tol=1e-10, maxiter=100000, raise_noconv=T
     if status != OK and (raise_noconv or status != ERR_NOCONV):
         check(status)
     return [[s.as_dict() for s in st] for st in stats], status
+
+
+def mg_check_operator(mg: Multigrid, U64, M5, mf, stream=None):
+    """Raise DwfError unless mg was set up for exactly the links U64 (complex128), M5 and mf."""
+    if U64.dtype != torch.complex128 or U64.numel() != link_size(mg.geom) or not U64.is_cuda:
+        raise ValueError("U64 must be a CUDA complex128 tensor of the link size")
+    check(lib().mg_check_operator(mg.ptr, _ptr(U64.contiguous()), float(M5), float(mf), _stream(stream)))
 
 
 def mg_destroy(mg: Multigrid):

@@ -1,7 +1,10 @@
 """torch.autograd.Function for x = D_DW(theta)^-1 b on U(1) link angles theta.
 
 Forward: links U = exp(i theta) and the solve run in libdwfmg (FP64 CGNR, or
-the multigrid K-cycle when a handle is given).  Backward: one adjoint solve
+the multigrid K-cycle when a handle is given).  A multigrid handle solves with
+the operator it was set up for, so it must come from mg_setup on exactly
+exp(i theta), M5 and mf: the forward pass checks that (mg_check_operator) and
+raises DwfError otherwise, e.g. once theta has moved in a training step.  Backward: one adjoint solve
 lambda = D_DW^-dag g, done as Gamma_5 D_DW^-1 Gamma_5 g (Gamma_5 = gamma_5 R,
 Sec. 2.1), then dL/db = lambda and dL/dtheta = -Re(lambda^dag dD_DW/dtheta x)
 from the link-force kernel.  Only x is kept between forward and backward (the
@@ -29,6 +32,8 @@ class DwfSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, b, geom, M5, mf, tol=1e-12, maxiter=200000, mg=None):
         U = _lib.links_from_angles(geom, theta.detach())
+        if mg is not None:
+            _lib.mg_check_operator(mg, U, M5, mf)
         x, st = _solve(geom, U, b.detach(), M5, mf, tol, maxiter, mg)
         ctx.save_for_backward(x)
         ctx.geom, ctx.M5, ctx.mf, ctx.tol, ctx.maxiter, ctx.mg = geom, M5, mf, tol, maxiter, mg

@@ -472,6 +472,7 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
     const TcParams p = tc_params(h, nrhs, mf, dagger);
     int form = 4;
     if (h->prm.coarse_tc == 1 && umma_eligible(h, p.ncols)) form = TC_UMMA;
+    else if (h->prm.coarse_tc >= 2) form = h->prm.coarse_tc == 2 ? 1 : h->prm.coarse_tc == 3 ? 2 : 4;
     else if (h->prm.coarse_tc == 0) {
         auto it = h->tc_choice.find(nrhs);
         if (it != h->tc_choice.end()) form = it->second;

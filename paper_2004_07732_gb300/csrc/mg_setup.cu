@@ -471,6 +471,17 @@ __global__ void k_blocks_to_mma(const double2* __restrict__ Y, __half* __restric
     }
 }
 
+// *differ = 1 if any complex value of a and b differs bitwise
+__global__ void k_links_differ(const double2* __restrict__ a, const double2* __restrict__ b, long long n, int* differ) {
+    bool d = false;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const double2 u = a[t], v = b[t];
+        d = d || __double_as_longlong(u.x) != __double_as_longlong(v.x) ||
+            __double_as_longlong(u.y) != __double_as_longlong(v.y);
+    }
+    if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicExch(differ, 1);
+}
+
 __global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         b[t] = make_float2((float)a[t].x, (float)a[t].y);
@@ -639,7 +650,7 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
         set_error("fine_prec must be one of the FP32 precisions"); return DWF_ERR_ARG;
     }
     if (prm.cgs_passes != 1 && prm.cgs_passes != 2) { set_error("cgs_passes must be 1 or 2"); return DWF_ERR_ARG; }
-    if (prm.coarse_tc != 0 && prm.coarse_tc != 1) { set_error("coarse_tc must be 0 or 1"); return DWF_ERR_ARG; }
+    if (prm.coarse_tc < 0 || prm.coarse_tc > 4) { set_error("coarse_tc must be in [0, 4]"); return DWF_ERR_ARG; }
     if (prm.coarse_block_prec != DWF_F32 && prm.coarse_block_prec != DWF_F32_L16) {
         set_error("coarse_block_prec must be DWF_F32 or DWF_F32_L16"); return DWF_ERR_ARG;
     }
@@ -715,6 +726,30 @@ void mg_destroy(dwf_mg* h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->hsc) cudaFreeHost(h->hsc);
     delete h;
+}
+
+dwf_status mg_check_operator(const dwf_mg* h, const void* U, double M5, double mf, void* stream) {
+    clear_error();
+    if (!h || !U) { set_error("NULL argument"); return DWF_ERR_ARG; }
+    if (M5 != h->M5 || mf != h->mf) {
+        set_error("the hierarchy was set up for M5 = %.17g, mf = %.17g, not M5 = %.17g, mf = %.17g", h->M5, h->mf,
+                  M5, mf);
+        return DWF_ERR_ARG;
+    }
+    cudaStream_t st = as_stream(stream);
+    const long long n = link_len(h->G);
+    int* flag = h->status + 8;                 // spare word of the setup status block
+    DWF_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    k_links_differ<<<ew_grid(n), 256, 0, st>>>((const double2*)h->U64, (const double2*)U, n, flag);
+    DWF_CHECK_LAUNCH();
+    int differ = 0;
+    DWF_CHECK_CUDA(cudaMemcpyAsync(&differ, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DWF_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (differ) {
+        set_error("the links differ from those the hierarchy was set up with: run mg_setup on the new links");
+        return DWF_ERR_ARG;
+    }
+    return DWF_OK;
 }
 
 dwf_status mg_coarse_geom(const dwf_mg* h, dwf_geom* c, int* ncdof) {

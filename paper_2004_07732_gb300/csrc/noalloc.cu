@@ -23,7 +23,9 @@
 //     on the array and give wrong results: order them on one stream.
 //   * the first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress (that device current) and caches it; make that first
-//     call before any stream capture.
+//     call before any stream capture.  The cache is per device ordinal for the
+//     life of the process: after cudaDeviceReset the cached address is stale, so
+//     a process that resets a device must not call this entry point again.
 #include <mutex>
 
 #include "common.cuh"
@@ -78,7 +80,7 @@ extern "C" dwf_status dwf_pvdag_apply_noalloc(const dwf_geom* g, const void* U, 
         return DWF_ERR_ARG;
     }
     if (!U || !psi || !out) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
-    if ((reinterpret_cast<uintptr_t>(psi) & 15u) || (reinterpret_cast<uintptr_t>(out) & 15u)) {
+    if (!aligned16(psi) || !aligned16(out)) {
         set_error("spinor buffers must be 16-byte aligned");
         return DWF_ERR_ARG;
     }

@@ -122,3 +122,25 @@ def test_autograd_gradient_vs_central_differences_128(dw):
         tm = flat.copy(); tm[idx] -= h
         fd = (L_fixed(tp) - L_fixed(tm)) / (2 * h)
         assert abs(fd - grad[idx]) < 2e-4 * max(abs(fd), 1e-3 * np.abs(grad).max()), (idx, fd, grad[idx])
+
+
+def test_autograd_rejects_a_hierarchy_of_other_links(dw):
+    """A multigrid handle solves with the operator of its setup: once theta moves (or M5 / m_f
+    differ) the differentiable solve must refuse it instead of returning a wrong x and gradient."""
+    dims, Ls, M5, mf = (8, 8), 4, 1.0, 0.05
+    rng = synth.rng_for(40)
+    theta = synth.u1_angles(rng, dims, 0.5)
+    b = _dev(synth.gaussian_spinor(rng, dims, Ls).reshape(-1))
+    g = dw.make_geom(dims, Ls)
+    starts = np.stack([synth.gaussian_complex(rng, (128,)) for _ in range(4)])
+    th = _dev(theta, torch.float64)
+    mg = dw.mg_setup(g, dw.links_from_angles(g, th), M5, mf, {"nvec": 4, "block": [4, 4, 1, 1],
+                                                               "setup_mass": -0.19}, _dev(starts))
+    dw.solve(th, b, g, M5, mf, tol=1e-10, mg=mg)          # the setup links: accepted
+    moved = th.clone()
+    moved[5] += 1e-6
+    with pytest.raises(dw.DwfError, match="links differ"):
+        dw.solve(moved, b, g, M5, mf, tol=1e-10, mg=mg)
+    with pytest.raises(dw.DwfError, match="set up for"):
+        dw.solve(th, b, g, M5, 2 * mf, tol=1e-10, mg=mg)
+    mg.close()
