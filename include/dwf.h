@@ -206,6 +206,28 @@ DWF_API dwf_status cgne_solve(const dwf_geom* g, const void* U, const void* b, v
                       double M5, double mf, double tol, int maxiter,
                       dwf_solve_stats* stats, void* stream);
 
+/* BiCGStab(l) (Sleijpen & Fokkema) on the Pauli-Villars preconditioned system
+ * D_PV^dag D_DW(mf) x = D_PV^dag b: the solver the paper compares with CGNR and
+ * multigrid as "BiCGStab-6 on D_PV^dag D_DW" (Sec. 2.3, Sec. 3, Fig.
+ * iterationscompare; convergent because spec(D_PV^dag D_DW) lies in the right
+ * half plane, App. B).  U, b, x: complex128 (canonical layouts), x = 0 on
+ * entry is not required (it is overwritten).  ell in [1, 8] (the paper's 6).
+ * FP64 reliable updates of the true residual r = b - D_DW x surround inner
+ * BiCGStab(ell) solves of D_PV^dag D_DW e = D_PV^dag r / |r| in inner_prec:
+ * DWF_F64 (complex128 vectors and links), or DWF_F32 / DWF_F32_L16 /
+ * DWF_F32_LBF16 (complex64 vectors, links converted to that storage by the
+ * library); each inner solve reduces its residual by 1e-4 (FP32) or 1e-12
+ * (FP64), or to what tol still needs.  Stops when ||b - D_DW x|| / ||b|| <= tol
+ * (recomputed in FP64).  maxiter caps the BiCG steps (ell per cycle; each step
+ * applies D_PV^dag D_DW twice).  Returns DWF_ERR_NOCONV (x = last iterate) at
+ * the cap or when two reliable updates in a row fail to lower the residual.
+ * stats (may be NULL): iterations = BiCG steps, restarts = reliable updates,
+ * fine_applies = D_DW, D_PV^dag applications (Sec. 3 counting).  The work
+ * vectors (2 ell + 5) are allocated stream-ordered for the call. */
+DWF_API dwf_status bicgstab_solve(const dwf_geom* g, const void* U, const void* b, void* x, double M5, double mf,
+                                  int ell, double tol, int maxiter, int inner_prec, dwf_solve_stats* stats,
+                                  void* stream);
+
 /* Diagnostic for failure detection (no paper counterpart): runs a kernel
  * whose bounded device wait cannot complete -- which = 0: an mbarrier that
  * expects one arrival more than it gets; which = 1: a cooperative software grid
@@ -216,7 +238,8 @@ DWF_API dwf_status cgne_solve(const dwf_geom* g, const void* U, const void* b, v
 DWF_API dwf_status dwf_check_wait_timeout(int which, double seconds, void* stream);
 
 /* ------------------------------------------------------------------------
- * Differentiation of x = D_DW^-1 b (U(1) links U = exp(i theta))
+ * Differentiation of x = D_DW^-1 b with respect to the links (derived from
+ * the Wilson hops of Sec. 2: only they depend on U, on every s slice)
  * ------------------------------------------------------------------------ */
 
 /* U_mu(x) = exp(i theta_mu(x)) on the GPU; theta is FP64 [mu][site], U_out
@@ -228,12 +251,30 @@ DWF_API dwf_status dwf_links_from_angles(const dwf_geom* g, const double* theta,
  * Gamma_5, so an adjoint solve is Gamma_5 D_DW^-1 Gamma_5.  in != out. */
 DWF_API dwf_status dwf_gamma5_reflect(const dwf_geom* g, const void* in, void* out, int prec, void* stream);
 
-/* force[mu][site] = Re( lam^dag (dD_DW / dtheta_mu(site)) x ) summed over all
- * s slices (2-d U(1), FP64; U, lam, x complex128).  With lam = D_DW^-dag g for
- * the upstream gradient g of a real loss, dL/dtheta = -force.  force is a
- * device array of nd * V doubles. */
+/* The link force of lam^dag D_DW x, FP64 (U, lam, x complex128), summed over
+ * all s slices.
+ * 2-d U(1), U = exp(i theta): force[mu][site] = Re( lam^dag (dD_DW /
+ *   dtheta_mu(site)) x ), nd * V doubles.
+ * 4-d SU(3): force[mu][site] is the traceless Hermitian 3 x 3 matrix F (complex128
+ *   row-major, the link layout: 18 doubles per link) with
+ *   Re( lam^dag (dD_DW / d eps) x ) = tr(H F) for the variation
+ *   U_mu(site) -> exp(i eps H) U_mu(site), H traceless Hermitian: the
+ *   derivative projected onto su(3).
+ * With lam = D_DW^-dag g for the upstream gradient g of a real loss L,
+ * dL/dtheta = -force (U(1)) and dL/d eps = -tr(H F) (SU(3)). */
 DWF_API dwf_status dwf_link_force(const dwf_geom* g, const void* U, const void* lam, const void* x, double* force,
                                   void* stream);
+
+/* The complex link gradient G of Re(lam^dag D_DW x), for 2-d U(1) and 4-d
+ * SU(3): Re( lam^dag dD_DW x ) = Re sum conj(G_ij) dU_ij for any change dU of
+ * the links (the backward hops read U^dag).  Per link G is the colour outer
+ * product of lam and the spin-projected x along the link, summed over s:
+ * G_mu(y) = -1/2 ph sum_s [ lam(y) ((1 - gamma_mu) x(y + mu))^dag
+ *                         + ((1 + gamma_mu) x(y)) lam(y + mu)^dag ]
+ * (ph = -1 on antiperiodic boundary-crossing links).  grad: complex128 in the
+ * link layout.  With lam = D_DW^-dag g, PyTorch's gradient of L with respect
+ * to U (dL/dRe U + i dL/dIm U) is -G. */
+DWF_API dwf_status dwf_link_grad(const dwf_geom* g, const void* lam, const void* x, void* grad, void* stream);
 
 /* ------------------------------------------------------------------------
  * Multigrid (Sec. 2.3, Sec. 3, Table kcycle)

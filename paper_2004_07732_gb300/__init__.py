@@ -5,8 +5,8 @@ include/dwf.h; this package only marshals torch tensors to device pointers.
 """
 from ._lib import (  # noqa: F401
     DwfError, Geom, SolveStats, PREC, lib, make_geom, spinor_size, link_size, spinor_dtype,
-    links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_pvdag_apply_noalloc, dwf_dot, cgne_solve,
-    links_from_angles, gamma5_reflect, link_force, dwf_apply_batched, check_wait_timeout, dwf_apply_host,
+    links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_pvdag_apply_noalloc, dwf_dot, cgne_solve, bicgstab_solve,
+    links_from_angles, gamma5_reflect, link_force, link_grad, dwf_apply_batched, check_wait_timeout, dwf_apply_host,
     packed_spinor_size, packed_link_size, pack_links, pack_spinor, unpack_spinor, dwf_apply_packed,
 )
 from ._lib import (  # noqa: F401
@@ -14,4 +14,4 @@ from ._lib import (  # noqa: F401
     mg_get_null_vectors, mg_get_coarse_links, mg_restrict, mg_prolong, mg_coarse_apply, mg_coarse_apply_multi,
     mg_solve_batched, mg_solve_groups, mg_coarse_tc_form, mg_check_operator,
 )
-from .autograd import DwfSolve, solve  # noqa: F401,E402
+from .autograd import DwfSolve, DwfSolveLinks, solve, solve_links  # noqa: F401,E402

@@ -98,6 +98,7 @@ def _setup_signatures(L):
         "dwf_pvdag_apply_noalloc": [G, _VP, _VP, _VP, _D, _D, _I, _VP],
         "dwf_dot": [_VP, _VP, ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _VP],
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
+        "bicgstab_solve": [G, _VP, _VP, _VP, _D, _D, _I, _D, _I, _I, ctypes.POINTER(SolveStats), _VP],
         "dwf_apply_batched": [_I, ctypes.POINTER(Geom), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                               ctypes.POINTER(_VP), _D, _D, _I, _I, _VP],
         "dwf_check_wait_timeout": [_I, _D, _VP],
@@ -105,6 +106,7 @@ def _setup_signatures(L):
         "dwf_links_from_angles": [G, _VP, _VP, _VP],
         "dwf_gamma5_reflect": [G, _VP, _VP, _I, _VP],
         "dwf_link_force": [G, _VP, _VP, _VP, _VP, _VP],
+        "dwf_link_grad": [G, _VP, _VP, _VP, _VP],
         "mg_setup": [G, _VP, _D, _D, ctypes.POINTER(MgParams), _VP, ctypes.POINTER(_VP), _VP],
         "mg_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
         "mg_solve_batched": [_VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(SolveStats), _VP],
@@ -320,6 +322,21 @@ def cgne_solve(geom, U, b, x, M5, mf, tol=1e-10, maxiter=100000, stream=None, ra
     return st.as_dict(), status
 
 
+def bicgstab_solve(geom, U, b, x, M5, mf, ell=6, tol=1e-10, maxiter=100000, inner_prec="f32_l16", stream=None,
+                   raise_noconv=True):
+    """BiCGStab(ell) on D_PV^dag D_DW x = D_PV^dag b with FP64 reliable updates (complex128 U, b, x)."""
+    _check_spinor(b, geom, "f64", "b")
+    _check_spinor(x, geom, "f64", "x")
+    if U.dtype != torch.complex128 or U.numel() != link_size(geom) or not U.is_cuda:
+        raise ValueError("U must be a CUDA complex128 tensor of the link size")
+    st = SolveStats()
+    status = lib().bicgstab_solve(ctypes.byref(geom), _ptr(U), _ptr(b), _ptr(x), float(M5), float(mf), int(ell),
+                                  float(tol), int(maxiter), PREC[inner_prec], ctypes.byref(st), _stream(stream))
+    if status != OK and (raise_noconv or status != ERR_NOCONV):
+        check(status)
+    return st.as_dict(), status
+
+
 def dwf_apply_batched(geoms, Us, psis, outs, M5, mf, dagger=False, prec="f32_l16", stream=None):
     """One launch applying D_DW to every (geometry, links, psi) triple of the lists."""
     n = len(psis)
@@ -378,11 +395,26 @@ def gamma5_reflect(geom, vin, vout=None, stream=None):
 
 
 def link_force(geom, U, lam, x, stream=None):
+    """Re(lam^dag dD_DW x) per link: float64 per angle (2-d U(1)); for 4-d SU(3) the traceless
+    Hermitian force F (complex128, the link layout) with Re(lam^dag dD x) = tr(H F) under
+    U -> exp(i eps H) U."""
     _check_spinor(lam, geom, "f64", "lam")
     _check_spinor(x, geom, "f64", "x")
-    F = torch.empty(link_size(geom), dtype=torch.float64, device=lam.device)
+    if geom.group == GROUP["su3"]:
+        F = torch.empty(link_size(geom), dtype=torch.complex128, device=lam.device)
+    else:
+        F = torch.empty(link_size(geom), dtype=torch.float64, device=lam.device)
     check(lib().dwf_link_force(ctypes.byref(geom), _ptr(U), _ptr(lam), _ptr(x), _ptr(F), _stream(stream)))
     return F
+
+
+def link_grad(geom, lam, x, stream=None):
+    """Complex link gradient G (complex128, link layout): Re(lam^dag dD_DW x) = Re sum conj(G) dU."""
+    _check_spinor(lam, geom, "f64", "lam")
+    _check_spinor(x, geom, "f64", "x")
+    G = torch.empty(link_size(geom), dtype=torch.complex128, device=lam.device)
+    check(lib().dwf_link_grad(ctypes.byref(geom), _ptr(lam), _ptr(x), _ptr(G), _stream(stream)))
+    return G
 
 
 # ---------------------------------------------------------------------------

@@ -1,4 +1,8 @@
-"""torch.autograd.Function for x = D_DW(theta)^-1 b on U(1) link angles theta.
+"""torch.autograd.Functions for x = D_DW^-1 b: on U(1) link angles theta
+(DwfSolve), and on the links themselves for any group (DwfSolveLinks: 2-d
+U(1) or 4-d SU(3); the gradient with respect to U follows PyTorch's complex
+convention dL/dRe U + i dL/dIm U, so a parametrisation such as
+U = exp(i omega) U_0 written in torch chains through it).
 
 Forward: links U = exp(i theta) and the solve run in libdwfmg (FP64 CGNR, or
 the multigrid K-cycle when a handle is given).  A multigrid handle solves with
@@ -56,3 +60,40 @@ class DwfSolve(torch.autograd.Function):
 def solve(theta, b, geom, M5, mf, tol=1e-12, maxiter=200000, mg=None):
     """Differentiable x = D_DW^-1 b (see DwfSolve)."""
     return DwfSolve.apply(theta, b, geom, M5, mf, tol, maxiter, mg)
+
+
+class DwfSolveLinks(torch.autograd.Function):
+    """x = D_DW(U)^-1 b with U (complex128, canonical link layout) differentiable.
+
+    Backward: lambda = D^-dag g by one adjoint solve (Gamma_5 D^-1 Gamma_5), then
+    dL/db = lambda and dL/dU = -G with G the complex link gradient of
+    Re(lambda^dag dD x) (dwf_link_grad: colour outer products of lambda and the
+    spin-projected x along every link, summed over s).  With a multigrid handle
+    the links must be those of its setup (checked)."""
+
+    @staticmethod
+    def forward(ctx, U, b, geom, M5, mf, tol=1e-12, maxiter=200000, mg=None):
+        Ud = U.detach().contiguous()
+        if mg is not None:
+            _lib.mg_check_operator(mg, Ud, M5, mf)
+        x, st = _solve(geom, Ud, b.detach(), M5, mf, tol, maxiter, mg)
+        ctx.save_for_backward(x)
+        ctx.geom, ctx.M5, ctx.mf, ctx.tol, ctx.maxiter, ctx.mg = geom, M5, mf, tol, maxiter, mg
+        ctx.U = Ud
+        ctx.stats = st
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        geom = ctx.geom
+        g = gx.contiguous().to(torch.complex128)
+        y, _ = _solve(geom, ctx.U, _lib.gamma5_reflect(geom, g), ctx.M5, ctx.mf, ctx.tol, ctx.maxiter, ctx.mg)
+        lam = _lib.gamma5_reflect(geom, y)
+        G = _lib.link_grad(geom, lam, x)
+        return -G, lam, None, None, None, None, None, None
+
+
+def solve_links(U, b, geom, M5, mf, tol=1e-12, maxiter=200000, mg=None):
+    """Differentiable x = D_DW(U)^-1 b with respect to the links U and b (see DwfSolveLinks)."""
+    return DwfSolveLinks.apply(U, b, geom, M5, mf, tol, maxiter, mg)

@@ -235,3 +235,36 @@ def test_kernel_blocks_round_trip_and_sigma3_adjoint():
     bad = bad.tocsr()
     assert np.abs(mg.coarse_dwf_dagger_g5(bad, Ls_c, 0.02, nvec).toarray()
                   - dirac.dagger(mg.coarse_dwf(bad, Ls_c, 0.02, nvec)).toarray()).max() > 0.1
+
+
+def _expm_herm(H, eps):
+    w, Q = np.linalg.eigh(H)
+    return (Q * np.exp(1j * eps * w)[None, :]) @ Q.conj().T
+
+
+@pytest.mark.parametrize("anti", [None, [0, 0, 0, 1]])
+def test_su3_force_matches_central_differences(anti):
+    """4-d SU(3), 2^4 x Ls 4: dl/d eps along random algebra directions H on random links
+    (U -> exp(i eps H) U) by central differences equals -2 tr(H F) of the adjoint force."""
+    dims, Ls, M5, mf = (2, 2, 2, 2), 4, 1.8, 0.05
+    rng = np.random.default_rng(50)
+    U = synth.su3_links(rng, dims, 0.4)
+    b = synth.gaussian_spinor(rng, dims, Ls, "su3").reshape(-1)
+    links = [(0, 3), (1, 0), (2, 9), (3, 15)]
+    l0, F = force.loss_and_force_su3(U, b, dims, Ls, M5, mf, links, anti)
+    for (mu, site), Fl in zip(links, F):
+        assert np.abs(Fl - Fl.conj().T).max() < 1e-12 and abs(np.trace(Fl)) < 1e-12
+        G = synth.gaussian_complex(rng, (3, 3))
+        H = 0.5 * (G + G.conj().T)
+        H -= np.trace(H).real / 3 * np.eye(3)
+        h = 1e-5
+        Lpm = []
+        for e in (h, -h):
+            Up = U.copy()
+            Up[mu, site] = _expm_herm(H, e) @ U[mu, site]
+            D = dirac.dwf_matrix(Up, dims, Ls, M5, mf, "su3", anti).toarray()
+            xs = np.linalg.solve(D, b)
+            Lpm.append(np.vdot(xs, xs).real)
+        fd = (Lpm[0] - Lpm[1]) / (2 * h)
+        want = -2 * np.trace(H @ Fl).real
+        assert abs(fd - want) < 1e-6 * max(1.0, abs(fd)), (mu, site, fd, want)
