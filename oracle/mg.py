@@ -79,14 +79,22 @@ def build_prolongator(vecs, dims, block, nd, nc):
     (P sparse of shape (V*ns*nc, Vc*2*Nvec), coarse dims).  Columns are
     ordered [coarse site][chirality +,-][vector].
     """
-    ns = dirac.n_spin(nd)
-    dof = ns * nc
+    _, g5 = dirac.gammas(nd)
+    chir = np.kron(np.diag(g5).real, np.ones(nc))          # +1 / -1 per site dof
+    return build_prolongator_chiral(vecs, dims, block, chir)
+
+
+def build_prolongator_chiral(vecs, dims, block, chir):
+    """The prolongator of build_prolongator for vectors with any per-site dof
+    layout: chir[d] = +1 / -1 is the chirality (the gamma_5, or on a coarse
+    level the sigma_3, eigenvalue) of site dof d.  Each vector's chiral halves
+    are orthonormalised per aggregate, in vector order."""
+    chir = np.asarray(chir, dtype=float)
+    dof = len(chir)
     V = int(np.prod(dims))
     nvec = len(vecs)
     agg, cdims = aggregate_map(dims, block)
     Vc = int(np.prod(cdims))
-    _, g5 = dirac.gammas(nd)
-    chir = np.kron(np.diag(g5).real, np.ones(nc))          # +1 / -1 per site dof
     Vm = np.stack([np.asarray(v).reshape(V, dof) for v in vecs], axis=-1)   # (V, dof, nvec)
     rows, cols, vals = [], [], []
     for a in range(Vc):
@@ -196,12 +204,26 @@ def kernel_from_blocks(Y, cdims):
 
 def restrict(r, P, Ls, Ls_c, nd, nc, nvec):
     """Truncated restriction onto the coarse walls (Eq. TruncProjectInterpolate)."""
-    nf = P.shape[0]
-    V = nf // (dirac.n_spin(nd) * nc)
+    V = P.shape[0] // (dirac.n_spin(nd) * nc)
     Pp, Pm = dirac.site_projectors(V, nd, nc)
+    Cp, Cm = coarse_projectors(P.shape[1] // (2 * nvec), nvec)
+    return restrict_walls(r, P, Ls, Ls_c, Pp, Pm, Cp, Cm)
+
+
+def prolong(e_c, P, Ls, Ls_c, nd, nc, nvec):
+    """Truncated prolongation from the coarse walls (Eq. TruncProjectInterpolate)."""
+    V = P.shape[0] // (dirac.n_spin(nd) * nc)
+    Pp, Pm = dirac.site_projectors(V, nd, nc)
+    Cp, Cm = coarse_projectors(P.shape[1] // (2 * nvec), nvec)
+    return prolong_walls(e_c, P, Ls, Ls_c, Pp, Pm, Cp, Cm)
+
+
+def restrict_walls(r, P, Ls, Ls_c, Pp, Pm, Cp, Cm):
+    """Eq. TruncProjectInterpolate between any two levels: Cm P^dag Pm r_1 on coarse
+    slice 1 and Cp P^dag Pp r_Ls on coarse slice Ls_c (zero elsewhere); (Pp, Pm) and
+    (Cp, Cm) are the chirality projectors of the finer and the coarser level."""
+    nf = P.shape[0]
     r = np.asarray(r).reshape(Ls, nf)
-    Vc = P.shape[1] // (2 * nvec)
-    Cp, Cm = coarse_projectors(Vc, nvec)
     rho = P.conj().T @ (Pm @ r[0] + Pp @ r[Ls - 1])
     out = np.zeros((Ls_c, P.shape[1]), dtype=complex)
     out[0] = Cm @ rho
@@ -209,13 +231,9 @@ def restrict(r, P, Ls, Ls_c, nd, nc, nvec):
     return out.reshape(-1)
 
 
-def prolong(e_c, P, Ls, Ls_c, nd, nc, nvec):
-    """Truncated prolongation from the coarse walls (Eq. TruncProjectInterpolate)."""
+def prolong_walls(e_c, P, Ls, Ls_c, Pp, Pm, Cp, Cm):
+    """The mirror of restrict_walls: Pm P e_1 on slice 1 and Pp P e_{Ls_c} on slice Ls."""
     nf = P.shape[0]
-    V = nf // (dirac.n_spin(nd) * nc)
-    Pp, Pm = dirac.site_projectors(V, nd, nc)
-    Vc = P.shape[1] // (2 * nvec)
-    Cp, Cm = coarse_projectors(Vc, nvec)
     e_c = np.asarray(e_c).reshape(Ls_c, P.shape[1])
     eta = P @ (Cm @ e_c[0] + Cp @ e_c[Ls_c - 1])
     out = np.zeros((Ls, nf), dtype=complex)
@@ -289,4 +307,116 @@ class TwoLevel:
                 outer += 1
                 if norm(b - self.Ddw @ x) <= tol * bn:
                     break
+        return x, outer, norm(b - self.Ddw @ x) / bn
+
+
+# ----------------------------------------------------------------------------
+# Third level (Table kcycle: level l > 1 has 12 null vectors, 2^2 aggregates)
+# ----------------------------------------------------------------------------
+
+def coarse_setup_operator(Dhat_w, M5, m_setup):
+    """Dhat_W(m_setup) = P^dag D_W(m_setup) P = Dhat_W + (m_setup + M5) 1: with
+    P^dag P = 1 the Wilson mass shift passes through the Galerkin product, so the
+    level-2 setup relaxes on the coarse kernel shifted to the setup mass."""
+    return (Dhat_w + (m_setup + M5) * sp.identity(Dhat_w.shape[0], format="csr")).tocsr()
+
+
+def coarse_chirality(nvec):
+    """sigma_3 eigenvalue of each coarse site dof [chirality +, -][vector]."""
+    return np.concatenate([np.ones(nvec), -np.ones(nvec)])
+
+
+class ThreeLevel:
+    """Three-level PV-preconditioned K-cycle (Sec. 2.3 Summary, Table kcycle), with
+    optional deflation of the coarsest level (Table zerospacing).
+
+    Level 1: outer FGCR(restart) on A = D_PV^dag D_DW, post_smooth GCR steps.
+    Level 2: Dhat_W = P^dag D_W P on Ls_c slices; the coarse system
+      Ahat = Dhat_PV^dag Dhat_DW is solved by flexible GCR to l2_tol (at most
+      l2_maxiter steps), preconditioned by the wall restriction to level 3, the
+      level-3 solve, the prolongation and l2_post_smooth GCR steps on Ahat.
+    Level 3: Dhat2_W = P2^dag Dhat_W P2 on Ls_cc slices; CGNR on
+      (Ahat2)^dag Ahat2, Ahat2 = Dhat2_PV^dag Dhat2_DW, to coarsest_tol; with
+      n_deflate > 0 it starts from the exact solution of the normal equations on
+      the span of the n_deflate lowest eigenvectors of (Ahat2)^dag Ahat2.
+    """
+
+    def __init__(self, U, dims, Ls, M5, mf, P, nvec, P2, nvec2, Ls_c=4, Ls_cc=4, group="u1", antiperiodic=None,
+                 l2_tol=0.25, l2_maxiter=16, l2_post_smooth=8, coarsest_tol=0.05, coarsest_maxiter=1024,
+                 post_smooth=8, restart=16, n_deflate=0):
+        nd = len(dims)
+        self.nd, self.nc = nd, (1 if group == "u1" else 3)
+        self.Ls, self.Ls_c, self.Ls_cc = Ls, Ls_c, Ls_cc
+        self.nvec, self.nvec2, self.P, self.P2 = nvec, nvec2, P, P2
+        self.Ddw = dirac.dwf_matrix(U, dims, Ls, M5, mf, group, antiperiodic)
+        self.Dpv_dag = dirac.dagger(dirac.pv_matrix(U, dims, Ls, M5, group, antiperiodic))
+        self.A = (self.Dpv_dag @ self.Ddw).tocsr()
+        Dw = dirac.wilson_matrix(U, dims, -M5, group, antiperiodic)
+        self.Dhat_w = galerkin_kernel(P, Dw)
+        self.A2 = (dirac.dagger(coarse_dwf(self.Dhat_w, Ls_c, 1.0, nvec)) @ coarse_dwf(self.Dhat_w, Ls_c, mf, nvec)).tocsr()
+        self.Dhat2_w = galerkin_kernel(P2, self.Dhat_w)
+        self.A3 = (dirac.dagger(coarse_dwf(self.Dhat2_w, Ls_cc, 1.0, nvec2))
+                   @ coarse_dwf(self.Dhat2_w, Ls_cc, mf, nvec2)).tocsr()
+        self.A3dag = dirac.dagger(self.A3)
+        Vc = P.shape[1] // (2 * nvec)
+        Vc2 = P2.shape[1] // (2 * nvec2)
+        self.proj1 = dirac.site_projectors(P.shape[0] // (dirac.n_spin(nd) * self.nc), nd, self.nc)
+        self.proj2 = coarse_projectors(Vc, nvec)
+        self.proj3 = coarse_projectors(Vc2, nvec2)
+        self.l2_tol, self.l2_maxiter, self.l2_post_smooth = l2_tol, l2_maxiter, l2_post_smooth
+        self.coarsest_tol, self.coarsest_maxiter = coarsest_tol, coarsest_maxiter
+        self.post_smooth, self.restart = post_smooth, restart
+        self.defl = None
+        if n_deflate > 0:
+            from .solvers import low_modes
+            self.defl = low_modes((self.A3dag @ self.A3).tocsr(), n_deflate)
+        self.l2_iters, self.l3_iters = [], []
+
+    def solve3(self, r3):
+        from .solvers import cgnr_deflated
+        if self.defl is None:
+            e3, it = cgnr_fixed(self.A3, r3, self.coarsest_tol, self.coarsest_maxiter, Ddag=self.A3dag)
+        else:
+            lam, V = self.defl
+            e3, it = cgnr_deflated(self.A3, r3, self.coarsest_tol, self.coarsest_maxiter, V, lam, Adag=self.A3dag)
+        self.l3_iters.append(it)
+        return e3
+
+    def precondition2(self, r2):
+        """Level-2 preconditioner: restrict to level 3, solve, prolong, post-smooth on Ahat."""
+        r3 = restrict_walls(r2, self.P2, self.Ls_c, self.Ls_cc, self.proj2[0], self.proj2[1], *self.proj3)
+        e3 = self.solve3(r3)
+        e0 = prolong_walls(e3, self.P2, self.Ls_c, self.Ls_cc, self.proj2[0], self.proj2[1], *self.proj3)
+        z, _, _ = gcr(lambda v: self.A2 @ v, r2, x0=e0, maxiter=self.l2_post_smooth)
+        return z
+
+    def solve2(self, r2):
+        e2, _, k = gcr(lambda v: self.A2 @ v, r2, tol=self.l2_tol, maxiter=self.l2_maxiter,
+                       precond=self.precondition2)
+        self.l2_iters.append(k)
+        return e2
+
+    def precondition(self, r):
+        """Level-1 preconditioner z = M(r): restrict, level-2 solve, prolong, post-smooth on A."""
+        r2 = restrict_walls(r, self.P, self.Ls, self.Ls_c, self.proj1[0], self.proj1[1], *self.proj2)
+        e2 = self.solve2(r2)
+        e0 = prolong_walls(e2, self.P, self.Ls, self.Ls_c, self.proj1[0], self.proj1[1], *self.proj2)
+        z, _, _ = gcr(lambda v: self.A @ v, r, x0=e0, maxiter=self.post_smooth)
+        return z
+
+    def solve(self, b, tol=1e-10, max_restarts=200):
+        """Outer flexible GCR(restart) on D_PV^dag D_DW x = D_PV^dag b, stopped on
+        ||b - D_DW x|| / ||b|| <= tol.  Returns (x, outer iterations, true residual)."""
+        b = np.asarray(b, dtype=complex).ravel()
+        bn = norm(b)
+        x = np.zeros_like(b)
+        outer = 0
+        for _ in range(max_restarts):
+            rt = b - self.Ddw @ x
+            if norm(rt) <= tol * bn:
+                break
+            xc, _, k = gcr(lambda v: self.A @ v, self.Dpv_dag @ rt, maxiter=self.restart, precond=self.precondition,
+                           tol=tol * bn / max(norm(self.Dpv_dag @ rt), 1e-300) * 0.5)
+            x = x + xc
+            outer += k
         return x, outer, norm(b - self.Ddw @ x) / bn

@@ -56,19 +56,20 @@ def cgnr(D, b, tol=1e-10, maxiter=100000, x0=None, Ddag=None):
     return x, it, norm(b - D @ x) / bn
 
 
-def cgnr_fixed(D, b, tol, maxiter, Ddag=None):
-    """CGNR stopped on the recursive residual ||b - D x|| <= tol ||b|| or maxiter.
+def cgnr_fixed(D, b, tol, maxiter, Ddag=None, x0=None):
+    """CGNR stopped on the recursive residual ||b - D x|| <= tol ||b|| or maxiter,
+    from x0 (default 0).
 
     Used for inexact inner solves; returns (x, iterations).
     """
     if Ddag is None:
         Ddag = D.conj().T.tocsr()
     b = np.asarray(b, dtype=complex).ravel()
-    x = np.zeros_like(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=complex).ravel()
     bn = norm(b)
     if bn == 0.0:
-        return x, 0
-    rr = b.copy()
+        return np.zeros_like(b), 0
+    rr = b - D @ x if x0 is not None else b.copy()
     r = Ddag @ rr
     p = r.copy()
     rn2 = vdot(r, r).real
@@ -211,3 +212,24 @@ def bicgstab_dw(Ddw, Dpv_dag, b, ell=6, tol=1e-10, max_cycles=10000):
 
     x, nA = bicgstab_l(lambda v: A @ v, Dpv_dag @ b, ell=ell, tol=0.0, max_cycles=max_cycles, stop=stop)
     return x, 2 * nA + 1, norm(b - Ddw @ x) / bn
+
+
+def low_modes(N, k):
+    """The k smallest eigenpairs (lam ascending, V columns orthonormal) of a
+    Hermitian matrix N, by dense diagonalisation (small problems only)."""
+    Nd = N.toarray() if hasattr(N, "toarray") else np.asarray(N)
+    w, Q = np.linalg.eigh(Nd)
+    return w[:k], Q[:, :k]
+
+
+def cgnr_deflated(A, b, tol, maxiter, V, lam, Adag=None):
+    """Deflated CGNR on A x = b: the start x0 = V diag(1 / lam) V^dag A^dag b
+    solves the normal equations A^dag A x = A^dag b exactly on the span of the
+    low eigenvectors V of A^dag A (eigenvalues lam), then CGNR continues from
+    x0 to ||b - A x|| <= tol ||b||.  Returns (x, iterations)."""
+    if Adag is None:
+        Adag = A.conj().T.tocsr()
+    b = np.asarray(b, dtype=complex).ravel()
+    f = Adag @ b
+    x0 = V @ ((V.conj().T @ f) / lam)
+    return cgnr_fixed(A, b, tol, maxiter, Ddag=Adag, x0=x0)

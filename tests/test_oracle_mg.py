@@ -268,3 +268,95 @@ def test_su3_force_matches_central_differences(anti):
         fd = (Lpm[0] - Lpm[1]) / (2 * h)
         want = -2 * np.trace(H @ Fl).real
         assert abs(fd - want) < 1e-6 * max(1.0, abs(fd)), (mu, site, fd, want)
+
+
+def _three_level(dims=(16, 16), Ls=6, nvec=4, nvec2=6, Ls_c=4, Ls_cc=4, sigma=0.3, seed=70, n_deflate=0):
+    M5, mf, m_setup = 1.0, 0.02, -0.3
+    U = _u1(dims, sigma, seed)
+    P, cdims = mg.build_prolongator(_null_vectors(U, dims, nvec, seed + 1, m_setup=m_setup, iters=60), dims,
+                                    (4, 4), 2, 1)
+    Dhat = mg.galerkin_kernel(P, dirac.wilson_matrix(U, dims, -M5))
+    S = mg.coarse_setup_operator(Dhat, M5, m_setup)
+    rng = np.random.default_rng(seed + 2)
+    v2 = [mg.relax_null_vector(S, synth.gaussian_complex(rng, (Dhat.shape[0],)), maxiter=60)[0] for _ in range(nvec2)]
+    P2, cdims2 = mg.build_prolongator_chiral(v2, cdims, (2, 2), mg.coarse_chirality(nvec))
+    ml = mg.ThreeLevel(U, dims, Ls, M5, mf, P, nvec, P2, nvec2, Ls_c=Ls_c, Ls_cc=Ls_cc, n_deflate=n_deflate)
+    return ml, U, Dhat, P2, cdims, cdims2, v2
+
+
+def test_level2_setup_operator_is_the_galerkin_of_the_shifted_kernel():
+    """P^dag D_W(m) P = Dhat_W(-M5) + (m + M5) 1 because P^dag P = 1."""
+    dims, block, nvec, M5, m = (8, 8), (4, 4), 3, 1.0, -0.27
+    U = _u1(dims, 0.5, 71)
+    P, _ = mg.build_prolongator(_null_vectors(U, dims, nvec, 72), dims, block, 2, 1)
+    want = mg.galerkin_kernel(P, dirac.wilson_matrix(U, dims, m)).toarray()
+    got = mg.coarse_setup_operator(mg.galerkin_kernel(P, dirac.wilson_matrix(U, dims, -M5)), M5, m).toarray()
+    assert np.abs(got - want).max() < 1e-13
+
+
+def test_level2_prolongator_galerkin_identities():
+    """Level 2 -> 3: P2^dag P2 = 1, sigma_3 P2 = P2 sigma_3 (chirality kept), the level-2 near-null
+    halves lie in the span, and P2^dag Dhat_DW P2 (P2 diagonal in s) is Eq. coarsenDW around
+    P2^dag Dhat_W P2 (Sec. 2.3 applied to the coarse kernel)."""
+    ml, U, Dhat, P2, cdims, cdims2, v2 = _three_level(Ls_c=4, Ls_cc=4)
+    nvec, nvec2 = 4, 6
+    P2d = P2.toarray()
+    assert cdims2 == (2, 2)
+    assert np.abs(P2d.conj().T @ P2d - np.eye(P2d.shape[1])).max() < 1e-13
+    S2 = mg.sigma3(16, nvec).toarray()
+    S3 = mg.sigma3(4, nvec2).toarray()
+    assert np.abs(S2 @ P2d - P2d @ S3).max() < 1e-14
+    Cp, Cm = mg.coarse_projectors(16, nvec)
+    for v in v2:
+        for proj in (Cp, Cm):
+            w = proj @ v
+            assert np.linalg.norm(P2 @ (P2.conj().T @ w) - w) < 1e-12 * np.linalg.norm(w)
+    Dhat2 = mg.galerkin_kernel(P2, Dhat)
+    Ps = np.kron(np.eye(4), P2d)
+    for m in (0.02, 1.0):
+        lhs = Ps.conj().T @ mg.coarse_dwf(Dhat, 4, m, nvec).toarray() @ Ps
+        rhs = mg.coarse_dwf(Dhat2, 4, m, nvec2).toarray()
+        assert np.abs(lhs - rhs).max() < 1e-12
+    # the coarser kernel keeps sigma_3-hermiticity: its sigma_3 adjoint is its adjoint
+    assert np.abs(mg.coarse_dwf_dagger_g5(Dhat2, 4, 0.02, nvec2).toarray()
+                  - dirac.dagger(mg.coarse_dwf(Dhat2, 4, 0.02, nvec2)).toarray()).max() < 1e-13
+
+
+def test_deflated_cgnr_start_and_dense_solution():
+    """Deflated CGNR: the start is the projection of the exact solution onto the deflation space
+    (V V^dag x*, V = low eigenvectors of A^dag A), the iteration reaches the dense solution, and
+    deflation cuts the iterations to a loose tolerance."""
+    ml, *_ = _three_level()
+    A = ml.A3
+    rng = np.random.default_rng(73)
+    b = synth.gaussian_complex(rng, (A.shape[0],))
+    Ad = A.toarray()
+    xd = np.linalg.solve(Ad, b)
+    from oracle import solvers as sv
+    lam, V = sv.low_modes((ml.A3dag @ A).tocsr(), 24)
+    x0 = V @ ((V.conj().T @ (ml.A3dag @ b)) / lam)
+    assert np.linalg.norm(x0 - V @ (V.conj().T @ xd)) < 1e-10 * np.linalg.norm(xd)
+    x, it = sv.cgnr_deflated(A, b, 1e-12, 5000, V, lam, Adag=ml.A3dag)
+    assert np.linalg.norm(x - xd) < 1e-9 * np.linalg.norm(xd)
+    _, it_plain = sv.cgnr_fixed(A, b, 0.05, 5000, Ddag=ml.A3dag)
+    _, it_defl = sv.cgnr_deflated(A, b, 0.05, 5000, V, lam, Adag=ml.A3dag)
+    assert it_defl < it_plain
+    # a right-hand side inside the deflation space needs no iteration
+    bb = Ad @ V[:, :5].sum(axis=1)
+    _, it0 = sv.cgnr_deflated(A, bb, 1e-10, 5000, V, lam, Adag=ml.A3dag)
+    assert it0 == 0
+
+
+@pytest.mark.parametrize("n_deflate", [0, 32])
+def test_three_level_kcycle_solves_to_tolerance(n_deflate):
+    """The three-level K-cycle (with and without coarsest deflation) reaches 1e-10 and the dense solution."""
+    ml, *_ = _three_level(n_deflate=n_deflate)
+    b = synth.gaussian_complex(np.random.default_rng(74), (ml.A.shape[0],))
+    x, outer, res = ml.solve(b, tol=1e-10)
+    assert res <= 1e-10
+    D = ml.Ddw.toarray()
+    xd = np.linalg.solve(D, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10 * np.linalg.cond(D)
+    assert max(ml.l2_iters) <= 16 and len(ml.l3_iters) >= len(ml.l2_iters)
+    _, it_cg, _ = solvers.cgnr(ml.Ddw, b, tol=1e-10)
+    assert outer < it_cg / 4
