@@ -12,8 +12,9 @@ reported alongside.
                psi and links, apply, D2H of the result, all inside the timed region
   roofline     the apply kernel: algorithmic bytes / CUDA-event duration vs the
                measured HBM copy bandwidth
-  solve        256x256 x Ls=16 (sigma 0.7, M5 1, m 0.005): FP64 CGNE and MG, each
-               to ||b - D x|| / ||b|| <= 1e-10, wall time on the same GPU
+  solve        256x256 x Ls=16 (sigma 0.7, M5 1, m 0.005; and the paper-like sigma 0.214):
+               FP64 CGNE, BiCGStab-6, the two-level and the deflated three-level
+               K-cycle, each to ||b - D x|| / ||b|| <= 1e-10, wall time on the same GPU
   cpu_baseline the FP64 oracle's CSR apply on the host cores, bounded sample
 
 --impl reference times the FP64 CPU oracle (the only reference this method
@@ -202,11 +203,12 @@ def cpu_oracle_apply(budget_s=12.0):
         D @ b
         reps += 1
     t = (time.perf_counter() - t0) / reps
-    gbs = apply_bytes(wl.V, wl.Ls) / t / 1e9
-    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"scipy CSR matvec of D_DW on {wl.dims[0]}x{wl.dims[1]}xLs{wl.Ls} (1/16 of the "
-                      f"bench lattice), {reps} reps in {budget_s:.0f} s, same algorithmic bytes per site",
-            "seconds_per_apply": t, "host_cpus": os.cpu_count()}
+    gbs = apply_bytes(wl.V, wl.Ls, 32, 16) / t / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "precision": "f64",
+            "sample": f"scipy CSR matvec (single-threaded) of the FP64 D_DW on {wl.dims[0]}x{wl.dims[1]}xLs{wl.Ls} "
+                      f"(1/16 of the bench lattice), {reps} reps in {budget_s:.0f} s, charged the FP64 algorithmic "
+                      f"bytes per 5-d site (32 B in, 32 B out, 2 x 16 B links / Ls)",
+            "seconds_per_apply": t, "seconds_per_site_apply": t / (wl.V * wl.Ls), "host_cpus": os.cpu_count()}
 
 
 def run_reference(args):
@@ -221,7 +223,7 @@ def run_reference(args):
             per.append(r["seconds_per_apply"])
             base = r
     t = float(np.mean(per))
-    v = apply_bytes(SOLVE_WL.V, SOLVE_WL.Ls) / t / 1e9
+    v = apply_bytes(SOLVE_WL.V, SOLVE_WL.Ls, 32, 16) / t / 1e9
     base["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -332,10 +334,21 @@ def run_ours(args):
     if not args.skip_coarse:
         coarse_multi = time_coarse_multi(dw, dev)
 
-    # ---------------- time to solution on the 256^2 workload ----------------
-    solve = None
+    # ---------------- time to solution on the 256^2 workloads ----------------
+    solve = smooth = None
     if not args.skip_solve:
         solve = time_solves(dw, dev, args)
+        smooth = time_solves(dw, dev, args, synth.SCHWINGER_256_SMOOTH)
+
+    # ---------------- small FP64 workload, FP64 apply, differentiation ----------------
+    cfg1 = fp64_apply = grad = ls_sweep = None
+    if not args.skip_solve:
+        cfg1 = time_config1(dw, dev, stream)
+        grad = time_gradient(dw, dev)
+        if not args.skip_mg:
+            ls_sweep = time_ls_sweep(dw, dev)
+    if not args.skip_fp64:
+        fp64_apply = time_fp64_apply(dw, dev, stream, args)
 
     clk.__exit__(None, None, None)
     peaks, peak_kind = measured_peaks()
@@ -362,7 +375,8 @@ def run_ours(args):
                         "serial_copies_ms_per_step": t_e2e_by["serial"] * 1e3},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": launches, "su3_apply": su3, "su3_solve": su3_solve, "batched_apply": batched,
-                "solve": solve,
+                "solve": solve, "solve_smooth_sigma0214": smooth, "config1_fp64": cfg1, "fp64_apply": fp64_apply,
+                "gradient": grad, "coarse_Ls_sweep": ls_sweep,
                 "batched_solve": batched_solve, "coarse_multi_rhs": coarse_multi}
         print(json.dumps(line), flush=True)
     ranks.close()
@@ -554,9 +568,12 @@ def time_batched_solve(dw, dev, args, cgne_per_class=2):
             "cgne_iterations_sampled": cg_it, "speedup_vs_cgne": cg_s / t_mg if t_mg > 0 else None}
 
 
-def time_solves(dw, dev, args):
+def time_solves(dw, dev, args, wl=SOLVE_WL):
+    """One workload to a true residual of 1e-10 on the same GPU: FP64 CGNE, BiCGStab-6 on
+    D_PV^dag D_DW (FP32 / FP16-link inner solves, FP64 reliable updates), the two-level K-cycle and
+    the paper's three-level K-cycle with 128 deflated coarsest modes (Table kcycle, Table
+    zerospacing).  MG times are given without and with the setup."""
     import torch
-    wl = SOLVE_WL
     U, srcs = wl.draw(1)
     g = dw.make_geom(wl.dims, wl.Ls)
     U64 = torch.from_numpy(U.reshape(-1)).to(dev)
@@ -567,15 +584,26 @@ def time_solves(dw, dev, args):
     st, status = dw.cgne_solve(g, U64, b, x, wl.M5, wl.mf, tol=1e-10, maxiter=200000, raise_noconv=False)
     torch.cuda.synchronize(dev)
     t_cg = time.perf_counter() - t0
-    res = {"workload": wl.name, "tol": 1e-10,
+    res = {"workload": f"{wl.name} (sigma {wl.sigma}, M5 {wl.M5}, m {wl.mf})", "tol": 1e-10,
            "cgne_fp64": {"seconds": t_cg, "iterations": st["iterations"], "fine_applies": st["fine_applies"],
                          "true_residual": st["true_residual"], "status": status}}
+    dw.bicgstab_solve(g, U64, b, x, wl.M5, wl.mf, ell=6, tol=1e-10, maxiter=12, raise_noconv=False)   # warm
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sb, bstatus = dw.bicgstab_solve(g, U64, b, x, wl.M5, wl.mf, ell=6, tol=1e-10, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    t_bs = time.perf_counter() - t0
+    res["bicgstab6"] = {"seconds": t_bs, "bicg_steps": sb["iterations"], "fine_applies": sb["fine_applies"],
+                        "reliable_updates": sb["restarts"], "true_residual": sb["true_residual"], "status": bstatus,
+                        "speedup_vs_cgne": t_cg / t_bs if t_bs > 0 else None}
     if hasattr(dw, "mg_setup") and not args.skip_mg:
-        res.update(time_mg(dw, dev, wl, U, U64, b, g, t_cg))
+        res["mg"] = time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2)
+        res["mg3_deflated"] = time_mg(dw, dev, wl, U64, b, g, t_cg, levels=3)
+        res["mg_speedup_vs_cgne"] = res["mg"]["speedup_vs_cgne"]
     return res
 
 
-def time_mg(dw, dev, wl, U, U64, b, g, t_cg):
+def time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2):
     import torch
     params = dw.mg_default_params()
     params["setup_mass"] = SETUP_MASS[wl.sigma]
@@ -585,20 +613,162 @@ def time_mg(dw, dev, wl, U, U64, b, g, t_cg):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     mg = dw.mg_setup(g, U64, wl.M5, wl.mf, params, torch.from_numpy(starts.reshape(-1)).to(dev))
+    if levels == 3:
+        Vc = wl.V // 16
+        lp = dw.mg_default_level_params()
+        s2 = np.stack([synth.gaussian_complex(rng, (Vc * 16,)) for _ in range(lp["nvec"])])
+        ls = synth.gaussian_complex(rng, ((Vc // 4) * lp["Ls_c"] * 2 * lp["nvec"],))
+        dw.mg_add_level(mg, {"setup_mass": SETUP_MASS[wl.sigma]}, torch.from_numpy(s2.reshape(-1)).to(dev),
+                        torch.from_numpy(ls).to(dev))
     torch.cuda.synchronize(dev)
     t_setup = time.perf_counter() - t0
     x = torch.empty_like(b)
-    dw.mg_solve(mg, b, x, tol=1e-10)          # warm run (allocations, graphs)
+    dw.mg_solve(mg, b, x, tol=1e-10, maxiter=2, raise_noconv=False)     # warm run (allocations, graphs)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     st, status = dw.mg_solve(mg, b, x, tol=1e-10, raise_noconv=False)
     torch.cuda.synchronize(dev)
     t_mg = time.perf_counter() - t0
     dw.mg_destroy(mg)
-    return {"mg": {"seconds": t_mg, "setup_seconds": t_setup, "outer_iterations": st["iterations"],
-                   "fine_applies": st["fine_applies"], "coarse_avg_iters": st["coarse_avg_iters"],
-                   "true_residual": st["true_residual"], "status": status},
-            "mg_speedup_vs_cgne": t_cg / t_mg if t_mg > 0 else None}
+    out = {"levels": levels, "seconds": t_mg, "setup_seconds": t_setup, "seconds_with_setup": t_mg + t_setup,
+           "outer_iterations": st["iterations"], "fine_applies": st["fine_applies"],
+           "coarse_avg_iters": st["coarse_avg_iters"], "true_residual": st["true_residual"], "status": status,
+           "speedup_vs_cgne": t_cg / t_mg if t_mg > 0 else None,
+           "speedup_vs_cgne_with_setup": t_cg / (t_mg + t_setup) if t_mg > 0 else None}
+    if levels == 3:
+        out["coarsest_avg_iters"] = st["coarsest_avg_iters"]
+        out["deflated_modes"] = 128
+    return out
+
+
+def time_ls_sweep(dw, dev):
+    """The coarse-Ls study of the paper's discussion: 128^2 x Ls 32 (sigma 0.214, m 0.01), two-level
+    K-cycle with the coarse Lhat_s reduced to 4, 8, 16 and kept at 32 (wall transfer), and the bulk
+    transfer at Lhat_s = 32; fine applications and wall time to 1e-10 for each."""
+    import torch
+    wl = synth.SCHWINGER_128_LS32
+    U, srcs = wl.draw(1)
+    g = dw.make_geom(wl.dims, wl.Ls)
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    b = torch.from_numpy(srcs[0].reshape(-1)).to(dev)
+    x = torch.empty_like(b)
+    rng = synth.rng_for(wl.seed + 7000)
+    starts = torch.from_numpy(np.stack([synth.gaussian_complex(rng, (wl.V * 2,)) for _ in range(8)]).reshape(-1)).to(dev)
+    out = {"workload": f"{wl.name}: Ls {wl.Ls}, sigma {wl.sigma}, M5 {wl.M5}, m {wl.mf}, to 1e-10", "runs": []}
+    for Ls_c, transfer in ((4, 0), (8, 0), (16, 0), (32, 0), (32, 1)):
+        mg = dw.mg_setup(g, U64, wl.M5, wl.mf, {"setup_mass": SETUP_MASS[wl.sigma], "Ls_c": Ls_c,
+                                                "transfer": transfer}, starts)
+        dw.mg_solve(mg, b, x, tol=1e-10, maxiter=2, raise_noconv=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st, status = dw.mg_solve(mg, b, x, tol=1e-10, raise_noconv=False)
+        torch.cuda.synchronize(dev)
+        out["runs"].append({"Ls_c": Ls_c, "transfer": "bulk" if transfer else "walls",
+                            "seconds": time.perf_counter() - t0, "fine_applies": st["fine_applies"],
+                            "outer_iterations": st["iterations"], "coarse_avg_iters": st["coarse_avg_iters"],
+                            "true_residual": st["true_residual"], "status": status})
+        dw.mg_destroy(mg)
+    return out
+
+
+def time_config1(dw, dev, stream, reps=200):
+    """The 32^2 x Ls 8 FP64 workload (sigma 0.5, m 0.01): one D_DW apply (latency; it is far too small
+    to reach HBM bandwidth) and FP64 CGNE to 1e-10."""
+    import torch
+    wl = synth.SCHWINGER_32
+    U, srcs = wl.draw(1)
+    g = dw.make_geom(wl.dims, wl.Ls)
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    b = torch.from_numpy(srcs[0].reshape(-1)).to(dev)
+    out = torch.empty_like(b)
+    for _ in range(10):
+        dw.dwf_apply(g, U64, b, out, wl.M5, wl.mf)
+    torch.cuda.synchronize(dev)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        dw.dwf_apply(g, U64, b, out, wl.M5, wl.mf)
+    e.record(stream)
+    e.synchronize()
+    t_apply = a.elapsed_time(e) * 1e-3 / reps
+    x = torch.empty_like(b)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st, status = dw.cgne_solve(g, U64, b, x, wl.M5, wl.mf, tol=1e-10, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    return {"workload": f"{wl.name}: FP64, sigma {wl.sigma}, M5 {wl.M5}, m {wl.mf}",
+            "apply_us": t_apply * 1e6, "apply_GBps": apply_bytes(wl.V, wl.Ls, 32, 16) / t_apply / 1e9,
+            "cgne_fp64": {"seconds": time.perf_counter() - t0, "iterations": st["iterations"],
+                          "true_residual": st["true_residual"], "status": status}}
+
+
+def time_fp64_apply(dw, dev, stream, args):
+    """FP64 D_DW on the 1024^2 x Ls 16 lattice against the FP64 rate cuBLAS DGEMM reaches on the same
+    GPU (the FP64 apply is bound by the FP64 units, not HBM)."""
+    import torch
+    wl = APPLY_WL
+    U, srcs = wl.draw(1)
+    g = dw.make_geom(wl.dims, wl.Ls)
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    psi = torch.from_numpy(srcs[0].reshape(-1)).to(dev)
+    out = torch.empty_like(psi)
+    for _ in range(3):
+        dw.dwf_apply(g, U64, psi, out, wl.M5, wl.mf)
+    torch.cuda.synchronize(dev)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(5, args.steps // 5)
+    a.record(stream)
+    for _ in range(n):
+        dw.dwf_apply(g, U64, psi, out, wl.M5, wl.mf)
+    e.record(stream)
+    e.synchronize()
+    t = a.elapsed_time(e) * 1e-3 / n
+    del psi, out, U64
+    # measured FP64 rate: cuBLAS DGEMM 8192^3 (2 N^3 flops), best of 5
+    N = 8192
+    A = torch.randn(N, N, dtype=torch.float64, device=dev)
+    B = torch.randn(N, N, dtype=torch.float64, device=dev)
+    torch.matmul(A, B)
+    best = 1e30
+    for _ in range(5):
+        a.record(stream)
+        torch.matmul(A, B)
+        e.record(stream)
+        e.synchronize()
+        best = min(best, a.elapsed_time(e) * 1e-3)
+    dgemm = 2.0 * N ** 3 / best / 1e12
+    del A, B
+    sites = wl.V * wl.Ls
+    # per 5-d site: 2 directions x (project 2 + complex multiply 6 + reconstruct 4) x 2 hops, diagonal
+    # and s-hops: 60 real flops (the counting convention of the 2-d kernel)
+    flops = 60.0 * sites
+    return {"workload": f"{wl.name}: FP64 spinors and links", "ms": t * 1e3,
+            "GBps": apply_bytes(wl.V, wl.Ls, 32, 16) / t / 1e9, "TFLOPs": flops / t / 1e12,
+            "dgemm_TFLOPs_measured": dgemm, "frac_of_dgemm": flops / t / 1e12 / dgemm,
+            "flops_per_site": 60}
+
+
+def time_gradient(dw, dev):
+    """The 128^2 x Ls 12 workload (sigma 0.7, m 0.005): x = D^-1 b with FP64 CGNE (tol 1e-12), loss |x|^2,
+    backward = one adjoint solve and the link force; forward and backward wall times."""
+    import torch
+    wl = synth.SCHWINGER_128_GRAD
+    theta, rng = wl.angles()
+    b = torch.from_numpy(synth.gaussian_spinor(rng, wl.dims, wl.Ls).reshape(-1)).to(dev)
+    g = dw.make_geom(wl.dims, wl.Ls)
+    th = torch.from_numpy(theta.reshape(-1)).to(dev).requires_grad_(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    x = dw.solve(th, b, g, wl.M5, wl.mf, tol=1e-12)
+    loss = (x.abs() ** 2).sum()
+    torch.cuda.synchronize(dev)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize(dev)
+    t_bwd = time.perf_counter() - t0
+    return {"workload": f"{wl.name}: d|x|^2/dtheta, FP64 CGNE solves to 1e-12", "forward_seconds": t_fwd,
+            "backward_seconds": t_bwd, "angles": int(th.numel())}
 
 
 def time_coarse_multi(dw, dev, nrhs=64, reps=20):
@@ -664,6 +834,7 @@ def main():
     ap.add_argument("--skip-su3", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-coarse", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

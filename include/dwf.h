@@ -145,19 +145,46 @@ DWF_API dwf_status dwf_pvdag_apply(const dwf_geom* g, const void* U, const void*
 DWF_API dwf_status dwf_pvdag_apply_noalloc(const dwf_geom* g, const void* U, const void* psi, void* out,
                                    double M5, double mf, int prec, void* stream);
 
-/* Packed layout of 4-d SU(3) fields (FP32 spinors), a private alternative to
- * the canonical layout with the same operator (Eq. DWoperator, Sec. 2).  The
- * sites of a slice are taken in blocks of 32 consecutive canonical site
- * indices (NB = ceil(V / 32) blocks; sites past V pad the last block).  A
- * spinor block holds six planes of 32 float4: plane k, slot i is complex
- * values 2k, 2k+1 (spin-major, colour fastest) of site 32 b + i, so the
- * float4 of (s, site, k) sits at ((s NB + site / 32) 6 + k) 32 + site % 32.  A
- * link block holds nine planes of 32 entries: entry j = 3 row + column of
- * U_mu(site) at ((mu NB + site / 32) 9 + j) 32 + site % 32, in the storage of
- * `prec` (complex64, half pairs or bfloat16 pairs).  A warp then reads each
- * piece of 32 neighbour spinors as one contiguous run.  4-d lattices only
- * (DWF_ERR_UNSUPPORTED otherwise).  Sizes are in complex values (0 for a bad
- * or 2-d geometry). */
+/* out = D_M(mf) psi (dagger != 0: D_M(mf)^dag psi), the Mobius domain wall
+ * operator, the generalisation of the Shamir form the paper's method carries
+ * over to (its conclusions: each factor of the DW / PV factorisation is linear
+ * in the Wilson kernel).  In the sign convention of Eq. DWoperator:
+ *   D_M = (1_s x D_W(-M5)) (b5 - c5 H_s) + 1 + H_s,
+ * H_s = the fifth-dimension hops of Eq. DWoperator (P_- on (s, s+1), P_+ on
+ * (s+1, s), -mf P_+ on (1, Ls), -mf P_- on (Ls, 1)); b5 = 1, c5 = 0 is dwf_apply
+ * exactly.  Its effective operator is the overlap operator of the Mobius kernel
+ * gamma_5 (b5 + c5) D_W (2 + (b5 - c5) D_W)^-1.  tmp: caller-owned scratch of one
+ * spinor (unused when b5 = 1, c5 = 0); psi, out, tmp distinct.  Layouts,
+ * precisions and errors as dwf_apply; 2-d and 4-d. */
+DWF_API dwf_status dwf_mobius_apply(const dwf_geom* g, const void* U, const void* psi, void* out, void* tmp,
+                                    double M5, double mf, double b5, double c5, int dagger, int prec, void* stream);
+
+/* out = D_PV^dag p(D_PV D_PV^dag) D(mf) psi with p(y) = sum_k coeffs[k] y^k
+ * (ncoef in [1, 64], host array): the Pauli-Villars preconditioned operator
+ * with [D_PV D_PV^dag]^-1 approximated by a polynomial (Sec. 2.3 and App. A);
+ * coeffs = {1} is dwf_pvdag_apply's D_PV^dag D_DW, {2, -1} the next order.  D is
+ * the Mobius operator of (b5, c5) (Shamir for 1, 0) and D_PV = D(1).  tmp:
+ * caller-owned scratch of four spinors, not overlapping psi or out.  Horner's
+ * scheme: 2 (ncoef - 1) + 2 operator applications. */
+DWF_API dwf_status dwf_pv_poly_apply(const dwf_geom* g, const void* U, const void* psi, void* out, void* tmp,
+                                     double M5, double mf, double b5, double c5, const double* coeffs, int ncoef,
+                                     int prec, void* stream);
+
+/* Packed (slice-paired) layout of 4-d SU(3) fields (FP32 spinors, even Ls), a
+ * private alternative to the canonical layout with the same operator (Eq.
+ * DWoperator, Sec. 2).  Sites are taken in blocks of 32 consecutive canonical
+ * site indices (NB = ceil(V / 32) blocks; sites past V pad the last block) and
+ * slices in pairs (2j, 2j+1).  For pair j, block b and complex element k of a
+ * site (spin-major, colour fastest, k < 12) a plane of 32 float4 holds, for
+ * site 32 b + i, (Re psi_2j[k], Re psi_2j+1[k], Im psi_2j[k], Im psi_2j+1[k]) at
+ * float4 index ((j NB + b) 12 + k) 32 + i: every real operation of the hop
+ * then runs as one packed FP32 instruction over the two slices, and a warp
+ * reads each element of 32 neighbour spinors as one contiguous run.  A link
+ * block holds nine planes of 32 entries: entry e = 3 row + column of
+ * U_mu(site) at ((mu NB + site / 32) 9 + e) 32 + site % 32, in the storage of
+ * `prec` (complex64, half pairs or bfloat16 pairs).  4-d lattices with even Ls
+ * only (DWF_ERR_UNSUPPORTED otherwise).  Sizes are in complex values (0 for a
+ * bad, 2-d or odd-Ls geometry). */
 DWF_API size_t dwf_packed_spinor_size(const dwf_geom* g);
 DWF_API size_t dwf_packed_link_size(const dwf_geom* g);
 
@@ -195,6 +222,9 @@ typedef struct {
     double coarse_avg_iters;   /* average coarsest-solver iterations per cycle          */
     double true_residual;      /* final ||b - D_DW x|| / ||b||, recomputed in FP64     */
     double seconds;            /* wall time of the call                                 */
+    double coarsest_avg_iters; /* three-level hierarchies: average coarsest-level CGNR
+                                  iterations per coarsest solve (coarse_avg_iters is then
+                                  the intermediate GCR steps per intermediate solve)   */
 } dwf_solve_stats;
 
 /* Conjugate gradient on the normal equations D_DW^dag D_DW x = D_DW^dag b
@@ -316,6 +346,9 @@ typedef struct {
                              the fastest; 1 = tcgen05 wherever eligible (mma.sync with 4
                              tiles elsewhere); 2, 3, 4 = mma.sync with 1, 2, 4 column tiles
                              per warp (fixed forms, for testing each one)                     */
+    int transfer;         /* 0 (default): the truncated wall transfer of Eq. TruncProjectInterpolate;
+                             1: the bulk transfer the paper compares it with (Sec. 4.1), P^dag /
+                             P on every slice, which needs Ls_c = Ls                           */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;
@@ -383,6 +416,22 @@ DWF_API dwf_status mg_get_coarse_links(const dwf_mg* h, void* Y_out, void* strea
  * P_- P e_1 on fine slice 1 and P_+ P e_{Ls_c} on slice Ls (zero elsewhere). */
 DWF_API dwf_status mg_restrict(const dwf_mg* h, const void* r_fine, void* r_coarse, void* stream);
 DWF_API dwf_status mg_prolong(const dwf_mg* h, const void* e_coarse, void* e_fine, void* stream);
+/* (With transfer = 1 both act on every slice instead: P^dag r_s and P e_s.) */
+
+/* Transfer-operator diagnostics of the paper's discussion (Sec. 4.1), for a
+ * complex64 fine vector v (typically a low eigenvector of D_PV^dag D_DW) and the
+ * handle's transfer (walls, or every slice with transfer = 1):
+ *   mg_transfer_colinearity: out = (1 - P R) v, the local colinearity;
+ *   mg_transfer_oblique:     out = (1 - P Ahat^-1 R A) v, the oblique projector,
+ *     A = D_PV^dag D_DW (FP32, fine_prec links), Ahat = Dhat_PV^dag Dhat_DW, with
+ *     Ahat^-1 a coarse GCR solve to relative residual tol (*iters: its steps).
+ * mg_coarse_solve: that coarse solve on its own (restarted GCR(16) on Ahat e = r
+ * from e = 0, complex64 coarse vectors).  All three allocate their work vectors
+ * stream-ordered and synchronise; they are diagnostics, not the solver's path. */
+DWF_API dwf_status mg_transfer_colinearity(dwf_mg* h, const void* v, void* out, void* stream);
+DWF_API dwf_status mg_transfer_oblique(dwf_mg* h, const void* v, void* out, double tol, int* iters, void* stream);
+DWF_API dwf_status mg_coarse_solve(dwf_mg* h, const void* rc, void* ec, double tol, int maxiter, int* iters,
+                                   void* stream);
 
 /* Coarse Dhat_DW(mf) (or its adjoint) of Eq. coarsenDW on complex64 coarse
  * vectors; mf = 1 gives Dhat_PV.  FP32 arithmetic on the handle's coarse block
@@ -434,6 +483,108 @@ DWF_API dwf_status mg_solve_batched(dwf_mg* h, int nrhs, const void* b, void* x,
  * status, with its index in the message. */
 DWF_API dwf_status mg_solve_groups(int ngroups, dwf_mg* const* handles, const int* nrhs, const void* const* b,
                                    void* const* x, double tol, int maxiter, dwf_solve_stats* const* stats);
+
+/* ------------------------------------------------------------------------
+ * Third level and coarsest-level deflation (Sec. 3: Table kcycle, levels
+ * l > 1; Table zerospacing, deflation of the coarsest level)
+ * ------------------------------------------------------------------------ */
+
+/* Parameters of the level built on the handle's coarse Wilson kernel.  The
+ * defaults (dwf_mg_default_level_params) are Table kcycle's: */
+typedef struct {
+    int nvec;             /* near-null vectors of the coarse kernel before chiral doubling (12) */
+    int block[4];         /* aggregate of coarse sites per direction (2, 2)                      */
+    int Ls_c;             /* fifth-dimension extent of the new (coarsest) level (4)              */
+    int setup_maxiter;    /* CG iterations per near-null vector (250)                            */
+    double setup_tol;     /* CG residual reduction per near-null vector (1e-4)                   */
+    double setup_mass;    /* Wilson mass m of the setup operator (0: set it to the level-1 value) */
+    int gcr_maxiter;      /* flexible GCR steps of the intermediate solve (16, no restart)       */
+    double tol;           /* intermediate relative residual tolerance (0.25)                     */
+    int post_smooth;      /* GCR post-smoothing steps on the intermediate level (8)              */
+    double coarsest_tol;  /* CGNR tolerance of the coarsest solve (0.05)                         */
+    int coarsest_maxiter; /* and its iteration cap (1024)                                        */
+    int n_deflate;        /* low modes of the coarsest normal operator deflated (128; 0 = none)  */
+    int lanczos_steps;    /* Lanczos steps that build the deflation space (256; at least
+                             2 n_deflate are taken)                                           */
+    int filter_degree;    /* degree of the Chebyshev filter the Lanczos runs on (64; 0: none) */
+    int coarsest_solver;  /* 0: CGNR on the normal operator (Table kcycle, default); 1: restarted
+                             GCR on Dhat2_PV^dag Dhat2_DW itself (valid by the right-half-plane
+                             property, App. B), same tolerance and start                      */
+    int coarsest_restart; /* restart length of that GCR (8)                                    */
+} dwf_mg_level_params;
+
+DWF_API void dwf_mg_default_level_params(dwf_mg_level_params* p);
+
+/* Add a third level to a 2-d two-level hierarchy (mg_setup), making it the
+ * paper's three-level K-cycle: mg_solve then solves the intermediate system
+ * Dhat_PV^dag Dhat_DW e = r by flexible GCR (tol, gcr_maxiter), preconditioned
+ * by the truncated wall restriction to the new level (Eq.
+ * TruncProjectInterpolate), the coarsest solve, the prolongation and
+ * post_smooth GCR steps; the coarsest solve is CGNR on the normal operator of
+ * Dhat2_PV^dag Dhat2_DW to coarsest_tol, started from the deflated guess.
+ * Setup, on the GPU: CG on S S^dag v = 0 with S = Dhat_W(setup_mass) =
+ * Dhat_W(-M5) + (setup_mass + M5) 1 (the Galerkin image of the shifted Wilson
+ * kernel) from null_starts (nvec complex128 coarse vectors [vec][site][dof], FP64);
+ * chiral doubling by sigma_3 and Gram-Schmidt per aggregate (the prolongator
+ * P2); Dhat2_W = P2^dag Dhat_W P2 (FP64, FP32 copy for the stencil).  Deflation
+ * (n_deflate > 0): Lanczos with full reorthogonalisation from lanczos_start
+ * (one complex128 coarsest vector, [s][site][dof]) on p(N), the Chebyshev
+ * polynomial of degree filter_degree of the coarsest normal operator N that is
+ * bounded by 1 on [a, b] and grows below a (b: an upper bound of spec N from 40
+ * plain Lanczos steps; a: raised until the wanted modes lie below it, at most
+ * three runs), so that the lowest modes of N are the top of spec p(N); the
+ * largest n_deflate eigenvalues of the Lanczos matrix (bisection) and their
+ * vectors (inverse iteration), orthonormalised, give the basis V = Q S, and the
+ * Rayleigh-Ritz matrix H = V^dag N V is factorised (Cholesky): every coarsest
+ * solve starts from x0 = V H^-1 V^dag A^dag r, the exact solution of the normal
+ * equations on span V.  2-d, one right-hand side per solve
+ * (mg_solve; mg_solve_batched with nrhs = 1).  The handle owns the level until
+ * mg_destroy; DWF_ERR_ARG if it already has one. */
+DWF_API dwf_status mg_add_level(dwf_mg* h, const dwf_mg_level_params* p, const void* null_starts,
+                                const void* lanczos_start, void* stream);
+
+/* The new level's lattice (nd, L, Ls = its Ls_c) and dof per site (2 nvec). */
+DWF_API dwf_status mg_level_geom(const dwf_mg* h, dwf_geom* coarse, int* ncdof);
+
+/* Copy one of the new level's FP64 setup outputs (device pointer out, async):
+ * what = 0: the relaxed near-null vectors, complex128 [vec][coarse site][dof];
+ * 1: the prolongator P2, complex128 [coarse site][chirality +,-][coarse dof of
+ *    that chirality][vec];
+ * 2: the Galerkin blocks of Dhat2_W, complex128 [site][dir][row][col] (dir as
+ *    for mg_get_coarse_links). */
+DWF_API dwf_status mg_level_get(const dwf_mg* h, int what, void* out, void* stream);
+
+/* Dhat2_DW(mf) (dagger != 0: its adjoint) of Eq. coarsenDW on the new level,
+ * complex64 [s][site][dof] vectors, FP32 blocks and arithmetic. */
+DWF_API dwf_status mg_level_apply(const dwf_mg* h, const void* in, void* out, double mf, int dagger, void* stream);
+
+/* Truncated restriction (coarse -> new level) and prolongation (new level ->
+ * coarse) of Eq. TruncProjectInterpolate with P2 and the sigma_3 projectors,
+ * complex64 vectors. */
+DWF_API dwf_status mg_level_restrict(const dwf_mg* h, const void* r2, void* r3, void* stream);
+DWF_API dwf_status mg_level_prolong(const dwf_mg* h, const void* e3, void* e2, void* stream);
+
+/* The coarsest solve on its own: CGNR on A^dag A x = A^dag b, A = Dhat2_PV^dag
+ * Dhat2_DW (complex64 b, x), to ||b - A x|| <= tol ||b|| or maxiter
+ * iterations, from the deflated guess (deflate != 0) or from 0.  maxiter = 0
+ * returns the starting guess.  *iters (may be NULL) = iterations.  Synchronises. */
+DWF_API dwf_status mg_level_coarsest_solve(dwf_mg* h, const void* b, void* x, double tol, int maxiter, int deflate,
+                                           int* iters, void* stream);
+
+/* The Lanczos estimates of the lowest eigenvalues of the coarsest normal
+ * operator (ascending) that set up the deflation: copies up to cap of them to
+ * the host array out and returns how many there are (0 without deflation). */
+DWF_API int mg_level_ritz_values(const dwf_mg* h, double* out, int cap);
+
+/* How the deflation space was built: info[0] = vectors kept, info[1] = the
+ * filter's final cut a, info[2] = its top b (the bound of spec N), info[3] =
+ * filtered Lanczos runs made (the cut starts at 2e-3 b and grows fourfold, at
+ * most to b / 4, until every kept mode's Rayleigh quotient lies below it). */
+DWF_API dwf_status mg_level_deflation_info(const dwf_mg* h, double* info);
+
+/* Intermediate (GCR) and coarsest (CGNR) iterations of the last intermediate
+ * solve. */
+DWF_API dwf_status mg_level_last_iterations(const dwf_mg* h, int* l2_iters, int* l3_iters);
 
 #ifdef __cplusplus
 }

@@ -365,3 +365,65 @@ def dwf_apply_points(U, psi, dims, Ls, M5, mf, points, group="u1", dagger_=False
         acc = acc + (B @ psi[s - 1, site] if s > 0 else -mf * B @ psi[Ls - 1, site])
         out.append(acc)
     return np.array(out)
+
+
+# ----------------------------------------------------------------------------
+# Mobius domain wall operator and the polynomial Pauli-Villars correction
+# (the generalisations the paper names in its conclusions and Sec. 2.3)
+# ----------------------------------------------------------------------------
+
+def s_hops(V, Ls, mf, nd, nc):
+    """H_s: the fifth-dimension hops of Eq. DWoperator without the diagonal:
+    P_- on block (s, s+1), P_+ on (s+1, s), -m P_+ on (1, Ls), -m P_- on (Ls, 1)."""
+    Pp, Pm = site_projectors(V, nd, nc)
+    up = sp.diags([np.ones(Ls - 1)], [1], shape=(Ls, Ls))
+    dn = sp.diags([np.ones(Ls - 1)], [-1], shape=(Ls, Ls))
+    c_1L = sp.csr_matrix(([1.0], ([0], [Ls - 1])), shape=(Ls, Ls))
+    c_L1 = sp.csr_matrix(([1.0], ([Ls - 1], [0])), shape=(Ls, Ls))
+    return (sp.kron(up, Pm) + sp.kron(dn, Pp) + sp.kron(c_1L, -mf * Pp) + sp.kron(c_L1, -mf * Pm)).tocsr()
+
+
+def mobius_matrix(U, dims, Ls, M5, mf, b5, c5, group="u1", antiperiodic=None):
+    """Mobius domain wall operator in the sign convention of Eq. DWoperator:
+    D_M = (b5 D_W + 1) on the diagonal blocks and (1 - c5 D_W) times each fifth-
+    dimension hop of H_s (P_-, P_+ and the -m walls), i.e.
+    D_M = (1_s x D_W) (b5 - c5 H_s) + 1 + H_s.
+    b5 = 1, c5 = 0 is the Shamir operator; the kernel is D_W(U, -M5)."""
+    nd = len(dims)
+    V = int(np.prod(dims))
+    nc = 1 if group == "u1" else 3
+    Dw = wilson_matrix(U, dims, -M5, group, antiperiodic)
+    Hs = s_hops(V, Ls, mf, nd, nc)
+    n = Hs.shape[0]
+    I = sp.identity(n, dtype=complex, format="csr")
+    DW5 = sp.kron(sp.identity(Ls, format="csr"), Dw)
+    return (DW5 @ (b5 * I - c5 * Hs) + I + Hs).tocsr()
+
+
+def mobius_from_kernel(Dk, Ls, mf, b5, c5, Pp, Pm):
+    """The Mobius form around any d-dim kernel Dk (a coarse kernel, e.g.):
+    (1_s x Dk)(b5 - c5 H_s) + 1 + H_s, H_s built from the chirality projectors Pp / Pm."""
+    n = Dk.shape[0]
+    up = sp.diags([np.ones(Ls - 1)], [1], shape=(Ls, Ls))
+    dn = sp.diags([np.ones(Ls - 1)], [-1], shape=(Ls, Ls))
+    c_1L = sp.csr_matrix(([1.0], ([0], [Ls - 1])), shape=(Ls, Ls))
+    c_L1 = sp.csr_matrix(([1.0], ([Ls - 1], [0])), shape=(Ls, Ls))
+    Hs = (sp.kron(up, Pm) + sp.kron(dn, Pp) + sp.kron(c_1L, -mf * Pp) + sp.kron(c_L1, -mf * Pm)).tocsr()
+    I = sp.identity(Ls * n, dtype=complex, format="csr")
+    return (sp.kron(sp.identity(Ls, format="csr"), Dk) @ (b5 * I - c5 * Hs) + I + Hs).tocsr()
+
+
+def pv_poly_operator(Ddw, Dpv, coeffs):
+    """D_PV^dag p(D_PV D_PV^dag) D_DW with p(y) = sum_k c_k y^k: the approximation
+    D_PV^-1 = D_PV^dag [D_PV D_PV^dag]^-1 ~ D_PV^dag p(D_PV D_PV^dag) of the
+    Pauli-Villars preconditioner; c = (1) is the truncation D_PV^dag D_DW of
+    Eq. NormalExp, c = (2, -1) the next order (App. A)."""
+    Dpvd = dagger(Dpv)
+    N = (Dpv @ Dpvd).tocsr()
+    n = N.shape[0]
+    P = sp.csr_matrix((n, n), dtype=complex)
+    Nk = sp.identity(n, dtype=complex, format="csr")
+    for c in coeffs:
+        P = P + c * Nk
+        Nk = (Nk @ N).tocsr()
+    return (Dpvd @ P @ Ddw).tocsr()

@@ -420,3 +420,33 @@ class ThreeLevel:
             x = x + xc
             outer += k
         return x, outer, norm(b - self.Ddw @ x) / bn
+
+
+# ----------------------------------------------------------------------------
+# Transfer-operator study (the paper's discussion section: boundary-only versus
+# bulk transfers, local colinearity and the oblique projector)
+# ----------------------------------------------------------------------------
+
+def restrict_bulk(r, P, Ls):
+    """The bulk alternative to Eq. TruncProjectInterpolate: P^dag on every slice (Lhat_s = Ls)."""
+    return (sp.kron(sp.identity(Ls), P.conj().T) @ np.asarray(r).reshape(-1))
+
+
+def prolong_bulk(e_c, P, Ls):
+    """P on every slice (the adjoint of restrict_bulk)."""
+    return (sp.kron(sp.identity(Ls), P) @ np.asarray(e_c).reshape(-1))
+
+
+def colinearity(v, restrict_fn, prolong_fn):
+    """||(1 - P R) v|| for a normalised vector v: how well the transfer keeps v."""
+    v = np.asarray(v).reshape(-1)
+    return norm(v - prolong_fn(restrict_fn(v))) / norm(v)
+
+
+def oblique(v, A, Ac, restrict_fn, prolong_fn):
+    """||(1 - P Ac^-1 R A) v|| / ||v||: the error left in the direction v by one exact coarse-grid
+    correction with the coarse operator Ac (dense solve)."""
+    v = np.asarray(v).reshape(-1)
+    rc = restrict_fn(A @ v)
+    ec = np.linalg.solve(Ac.toarray() if hasattr(Ac, "toarray") else Ac, rc)
+    return norm(v - prolong_fn(ec)) / norm(v)

@@ -38,7 +38,7 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("fine_applies", ctypes.c_longlong), ("coarse_applies", ctypes.c_longlong),
                 ("coarse_avg_iters", ctypes.c_double), ("true_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("coarsest_avg_iters", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -52,7 +52,16 @@ class MgParams(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("coarse_persistent", ctypes.c_int), ("coarse_solver", ctypes.c_int),
                 ("coarse_restart", ctypes.c_int), ("coarse_block_prec", ctypes.c_int), ("cgs_passes", ctypes.c_int),
-                ("coarse_tc", ctypes.c_int)]
+                ("coarse_tc", ctypes.c_int), ("transfer", ctypes.c_int)]
+
+
+class LevelParams(ctypes.Structure):
+    _fields_ = [("nvec", ctypes.c_int), ("block", ctypes.c_int * 4), ("Ls_c", ctypes.c_int),
+                ("setup_maxiter", ctypes.c_int), ("setup_tol", ctypes.c_double), ("setup_mass", ctypes.c_double),
+                ("gcr_maxiter", ctypes.c_int), ("tol", ctypes.c_double), ("post_smooth", ctypes.c_int),
+                ("coarsest_tol", ctypes.c_double), ("coarsest_maxiter", ctypes.c_int), ("n_deflate", ctypes.c_int),
+                ("lanczos_steps", ctypes.c_int), ("filter_degree", ctypes.c_int), ("coarsest_solver", ctypes.c_int),
+                ("coarsest_restart", ctypes.c_int)]
 
 
 _lib = None
@@ -96,6 +105,8 @@ def _setup_signatures(L):
         "pv_apply": [G, _VP, _VP, _VP, _D, _I, _I, _VP],
         "dwf_pvdag_apply": [G, _VP, _VP, _VP, _VP, _D, _D, _I, _VP],
         "dwf_pvdag_apply_noalloc": [G, _VP, _VP, _VP, _D, _D, _I, _VP],
+        "dwf_mobius_apply": [G, _VP, _VP, _VP, _VP, _D, _D, _D, _D, _I, _I, _VP],
+        "dwf_pv_poly_apply": [G, _VP, _VP, _VP, _VP, _D, _D, _D, _D, ctypes.POINTER(ctypes.c_double), _I, _I, _VP],
         "dwf_dot": [_VP, _VP, ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _VP],
         "cgne_solve": [G, _VP, _VP, _VP, _D, _D, _D, _I, ctypes.POINTER(SolveStats), _VP],
         "bicgstab_solve": [G, _VP, _VP, _VP, _D, _D, _I, _D, _I, _I, ctypes.POINTER(SolveStats), _VP],
@@ -120,8 +131,21 @@ def _setup_signatures(L):
         "mg_restrict": [_VP, _VP, _VP, _VP],
         "mg_prolong": [_VP, _VP, _VP, _VP],
         "mg_coarse_apply": [_VP, _VP, _VP, _D, _I, _VP],
+        "mg_transfer_colinearity": [_VP, _VP, _VP, _VP],
+        "mg_transfer_oblique": [_VP, _VP, _VP, _D, ctypes.POINTER(ctypes.c_int), _VP],
+        "mg_coarse_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP],
         "mg_coarse_apply_multi": [_VP, _I, _VP, _VP, _D, _I, _VP],
         "mg_coarse_tc_form": [_VP, _I],
+        "mg_add_level": [_VP, ctypes.POINTER(LevelParams), _VP, _VP, _VP],
+        "mg_level_geom": [_VP, G, ctypes.POINTER(ctypes.c_int)],
+        "mg_level_get": [_VP, _I, _VP, _VP],
+        "mg_level_apply": [_VP, _VP, _VP, _D, _I, _VP],
+        "mg_level_restrict": [_VP, _VP, _VP, _VP],
+        "mg_level_prolong": [_VP, _VP, _VP, _VP],
+        "mg_level_coarsest_solve": [_VP, _VP, _VP, _D, _I, _I, ctypes.POINTER(ctypes.c_int), _VP],
+        "mg_level_ritz_values": [_VP, ctypes.POINTER(ctypes.c_double), _I],
+        "mg_level_last_iterations": [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "mg_level_deflation_info": [_VP, ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -130,6 +154,8 @@ def _setup_signatures(L):
             fn.restype = ctypes.c_int
     L.dwf_mg_default_params.argtypes = [ctypes.POINTER(MgParams)]
     L.dwf_mg_default_params.restype = None
+    L.dwf_mg_default_level_params.argtypes = [ctypes.POINTER(LevelParams)]
+    L.dwf_mg_default_level_params.restype = None
     L.mg_destroy.argtypes = [_VP]
     L.mg_destroy.restype = None
 
@@ -299,6 +325,33 @@ def dwf_pvdag_apply_noalloc(geom, U, psi, out, M5, mf, prec="f64", stream=None):
         _check_spinor(t, geom, prec, nm)
     check(lib().dwf_pvdag_apply_noalloc(ctypes.byref(geom), _ptr(U), _ptr(psi), _ptr(out), float(M5),
                                         float(mf), PREC[prec], _stream(stream)))
+    return out
+
+
+def dwf_mobius_apply(geom, U, psi, out, M5, mf, b5, c5, dagger=False, prec="f64", tmp=None, stream=None):
+    """Mobius D_M(mf) psi (or its adjoint); tmp: one spinor of scratch (allocated here if None)."""
+    _check_spinor(psi, geom, prec, "psi")
+    _check_spinor(out, geom, prec, "out")
+    if tmp is None:
+        tmp = torch.empty_like(psi)
+    _check_spinor(tmp, geom, prec, "tmp")
+    check(lib().dwf_mobius_apply(ctypes.byref(geom), _ptr(U), _ptr(psi), _ptr(out), _ptr(tmp), float(M5), float(mf),
+                                 float(b5), float(c5), int(bool(dagger)), PREC[prec], _stream(stream)))
+    return out
+
+
+def dwf_pv_poly_apply(geom, U, psi, out, M5, mf, coeffs, b5=1.0, c5=0.0, prec="f64", tmp=None, stream=None):
+    """D_PV^dag p(D_PV D_PV^dag) D psi with p(y) = sum_k coeffs[k] y^k; tmp: four spinors of scratch."""
+    _check_spinor(psi, geom, prec, "psi")
+    _check_spinor(out, geom, prec, "out")
+    n = spinor_size(geom)
+    if tmp is None:
+        tmp = torch.empty(4 * n, dtype=spinor_dtype(prec), device=psi.device)
+    if tmp.numel() < 4 * n or tmp.dtype != spinor_dtype(prec) or not tmp.is_cuda:
+        raise ValueError("tmp must hold four spinors of the precision")
+    c = (ctypes.c_double * len(coeffs))(*[float(v) for v in coeffs])
+    check(lib().dwf_pv_poly_apply(ctypes.byref(geom), _ptr(U), _ptr(psi), _ptr(out), _ptr(tmp), float(M5), float(mf),
+                                  float(b5), float(c5), c, len(coeffs), PREC[prec], _stream(stream)))
     return out
 
 
@@ -609,3 +662,138 @@ def mg_coarse_apply_multi(mg: Multigrid, vin, vout, nrhs, mf, dagger=False, stre
 def mg_coarse_tc_form(mg: Multigrid, nrhs) -> int:
     """Form of the coarse contraction the autotuner chose for nrhs (0: not tuned yet)."""
     return int(lib().mg_coarse_tc_form(mg.ptr, int(nrhs)))
+
+
+# ---------------------------------------------------------------------------
+# third level and coarsest deflation
+# ---------------------------------------------------------------------------
+def mg_default_level_params() -> dict:
+    p = LevelParams()
+    lib().dwf_mg_default_level_params(ctypes.byref(p))
+    d = {k: getattr(p, k) for k, _ in LevelParams._fields_}
+    d["block"] = list(p.block)
+    return d
+
+
+def mg_add_level(mg: Multigrid, params=None, null_starts=None, lanczos_start=None, stream=None):
+    """Add the third level (and its deflation) to a two-level hierarchy.
+
+    null_starts: nvec complex128 coarse vectors ([vec][coarse site][dof]); lanczos_start: one
+    complex128 vector of the new level's size (needed when n_deflate > 0)."""
+    p = LevelParams()
+    lib().dwf_mg_default_level_params(ctypes.byref(p))
+    for k, v in (params or {}).items():
+        if k == "block":
+            for i, b in enumerate(v):
+                p.block[i] = int(b)
+        else:
+            setattr(p, k, v)
+    if null_starts is None:
+        raise ValueError("null_starts are required")
+    check(lib().mg_add_level(mg.ptr, ctypes.byref(p), _ptr(null_starts.contiguous()),
+                             _ptr(lanczos_start.contiguous()) if lanczos_start is not None else None,
+                             _stream(stream)))
+    cg = Geom()
+    ncd = ctypes.c_int()
+    check(lib().mg_level_geom(mg.ptr, ctypes.byref(cg), ctypes.byref(ncd)))
+    mg.level_geom, mg.level_ncdof, mg.level_params = cg, ncd.value, p
+    mg.level_V = cg.L[0] * cg.L[1]
+    mg.level_size = mg.level_V * cg.Ls * ncd.value
+    return mg
+
+
+def mg_level_get(mg: Multigrid, what: int):
+    """The new level's null vectors (0), prolongator (1) or Galerkin blocks (2), complex128."""
+    p = mg.level_params
+    n = {0: p.nvec * mg.Vc * mg.ncdof, 1: mg.Vc * mg.ncdof * p.nvec,
+         2: mg.level_V * 5 * mg.level_ncdof * mg.level_ncdof}[what]
+    out = torch.empty(n, dtype=torch.complex128, device="cuda")
+    check(lib().mg_level_get(mg.ptr, int(what), _ptr(out), _stream(None)))
+    return out
+
+
+def _check_level_vec(mg, t, name):
+    if t.dtype != torch.complex64 or t.numel() != mg.level_size or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor of the new level's size")
+
+
+def _check_coarse_vec(mg, t, name):
+    if t.dtype != torch.complex64 or t.numel() != mg.coarse_size or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor of the coarse size")
+
+
+def mg_level_apply(mg: Multigrid, vin, vout, mf, dagger=False, stream=None):
+    _check_level_vec(mg, vin, "in")
+    _check_level_vec(mg, vout, "out")
+    check(lib().mg_level_apply(mg.ptr, _ptr(vin), _ptr(vout), float(mf), int(bool(dagger)), _stream(stream)))
+    return vout
+
+
+def mg_level_restrict(mg: Multigrid, r2, r3, stream=None):
+    _check_coarse_vec(mg, r2, "r2")
+    _check_level_vec(mg, r3, "r3")
+    check(lib().mg_level_restrict(mg.ptr, _ptr(r2), _ptr(r3), _stream(stream)))
+    return r3
+
+
+def mg_level_prolong(mg: Multigrid, e3, e2, stream=None):
+    _check_level_vec(mg, e3, "e3")
+    _check_coarse_vec(mg, e2, "e2")
+    check(lib().mg_level_prolong(mg.ptr, _ptr(e3), _ptr(e2), _stream(stream)))
+    return e2
+
+
+def mg_level_coarsest_solve(mg: Multigrid, b, x, tol=0.05, maxiter=1024, deflate=True, stream=None) -> int:
+    _check_level_vec(mg, b, "b")
+    _check_level_vec(mg, x, "x")
+    it = ctypes.c_int()
+    check(lib().mg_level_coarsest_solve(mg.ptr, _ptr(b), _ptr(x), float(tol), int(maxiter), int(bool(deflate)),
+                                        ctypes.byref(it), _stream(stream)))
+    return it.value
+
+
+def mg_level_ritz_values(mg: Multigrid):
+    n = lib().mg_level_ritz_values(mg.ptr, None, 0)
+    buf = (ctypes.c_double * max(n, 1))()
+    lib().mg_level_ritz_values(mg.ptr, buf, n)
+    return [buf[i] for i in range(n)]
+
+
+def mg_level_last_iterations(mg: Multigrid):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(lib().mg_level_last_iterations(mg.ptr, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mg_level_deflation_info(mg: Multigrid) -> dict:
+    info = (ctypes.c_double * 4)()
+    check(lib().mg_level_deflation_info(mg.ptr, info))
+    return {"vectors": int(info[0]), "filter_cut": info[1], "filter_top": info[2], "filter_runs": int(info[3])}
+
+
+def mg_transfer_colinearity(mg: Multigrid, v, out=None, stream=None):
+    """(1 - P R) v for a complex64 fine vector v (the handle's transfer)."""
+    _check_spinor(v, mg.geom, "f32", "v")
+    out = torch.empty_like(v) if out is None else out
+    check(lib().mg_transfer_colinearity(mg.ptr, _ptr(v), _ptr(out), _stream(stream)))
+    return out
+
+
+def mg_transfer_oblique(mg: Multigrid, v, out=None, tol=1e-6, stream=None):
+    """(1 - P Ahat^-1 R A) v for a complex64 fine vector v; returns (out, coarse GCR steps)."""
+    _check_spinor(v, mg.geom, "f32", "v")
+    out = torch.empty_like(v) if out is None else out
+    it = ctypes.c_int()
+    check(lib().mg_transfer_oblique(mg.ptr, _ptr(v), _ptr(out), float(tol), ctypes.byref(it), _stream(stream)))
+    return out, it.value
+
+
+def mg_coarse_solve(mg: Multigrid, rc, ec, tol=1e-6, maxiter=10000, stream=None) -> int:
+    """Restarted GCR on Dhat_PV^dag Dhat_DW ec = rc (complex64 coarse vectors); returns the steps."""
+    for t, nm in ((rc, "rc"), (ec, "ec")):
+        if t.dtype != torch.complex64 or t.numel() != mg.coarse_size or not t.is_cuda:
+            raise ValueError(f"{nm} must be a complex64 CUDA tensor of the coarse size")
+    it = ctypes.c_int()
+    check(lib().mg_coarse_solve(mg.ptr, _ptr(rc), _ptr(ec), float(tol), int(maxiter), ctypes.byref(it),
+                                _stream(stream)))
+    return it.value

@@ -9,13 +9,10 @@
 // link (the spin projection of the Wilson operator).  P_+ / P_- are the upper /
 // lower spin pairs, so the s-hops add half spinors of psi_{s-1} and psi_{s+1}.
 //
-// Two memory layouts share the kernel body.  Canonical: psi[s][site][spin][colour]
-// and U[mu][site][3][3], as the C ABI defines them.  Packed (FP32 spinors
-// only): the sites of a slice are grouped in blocks of 32, and a block stores
-// the six 16-byte pieces of its 32 spinors as six planes of 32 (piece k of site
-// i at plane k, slot i), the links likewise as nine planes of 32 entries.  A
-// warp then reads each piece of 32 neighbour spinors as one contiguous 512-byte
-// run instead of 32 pieces at a 96-byte stride.
+// Layout: canonical, psi[s][site][spin][colour] and U[mu][site][3][3], as the
+// C ABI defines them.  The packed layout (dwf_pack_spinor / dwf_apply_packed) has
+// its own kernel in dwf_fine4d_pair.cu; this file keeps the packed links'
+// conversion and the packed entry points.
 #include "common.cuh"
 #include "fine_kernels.cuh"
 
@@ -37,18 +34,6 @@ struct LayCanon {
     __device__ __forceinline__ long long rec(int s, int site) const { return (long long)s * V + site; }
     __device__ __forceinline__ long long lk(int mu, int site) const { return (long long)mu * (V * 9) + (long long)site * 9; }
 };
-// Packed layout: NB = ceil(V / 32) blocks of 32 sites per slice.
-struct LayPacked {
-    static constexpr int KS = 32, JS = 32;
-    long long V, NB;
-    __device__ __forceinline__ long long f4(int s, int site) const {
-        return (long long)s * (NB * 192) + ((site >> 5) * 192 + (site & 31));
-    }
-    __device__ __forceinline__ long long lk(int mu, int site) const {
-        return (long long)mu * (NB * 288) + (long long)(site >> 5) * 288 + (site & 31);
-    }
-};
-
 template <class LAY>
 __device__ __forceinline__ void ld_spin4(const float2* p, const LAY& L, int s, int site, Spin4<float>& v) {
     const float4* q = reinterpret_cast<const float4*>(p) + L.f4(s, site);
@@ -299,50 +284,6 @@ dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* ou
     return DWF_OK;
 }
 
-dwf_status fine_apply_4d_packed(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
-                                bool dagger, int prec, cudaStream_t st) {
-    const Fine4dParams p = params4d(g, M5, mf);
-    LayPacked lay{g.V, (g.V + 31) / 32};
-    switch (prec) {
-        case DWF_F32:       DWF_TRY((launch4d<LinkF32, float>(U, psi, out, p, lay, dagger, st))); break;
-        case DWF_F32_L16:   DWF_TRY((launch4d<LinkH16, float>(U, psi, out, p, lay, dagger, st))); break;
-        case DWF_F32_LBF16: DWF_TRY((launch4d<LinkBF16, float>(U, psi, out, p, lay, dagger, st))); break;
-        default: set_error("the packed layout takes FP32 spinors (precision %d)", prec); return DWF_ERR_ARG;
-    }
-    DWF_CHECK_LAUNCH();
-    return DWF_OK;
-}
-
-// ---------------------------------------------------------------------------
-// conversions between the canonical and the packed layout
-// ---------------------------------------------------------------------------
-// one thread per (slice, site): the six pieces of a spinor; sites past V in
-// the last block are written as zero by the packing
-__global__ void k_pack_spinor(const float4* __restrict__ in, float4* __restrict__ out, long long V, long long NB,
-                              long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / (NB * 32), site = i % (NB * 32);
-        float4* q = out + ((s * NB + (site >> 5)) * 6) * 32 + (site & 31);
-        if (site < V) {
-            const float4* r = in + (s * V + site) * 6;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) q[k * 32] = __ldg(r + k);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) q[k * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-}
-__global__ void k_unpack_spinor(const float4* __restrict__ in, float4* __restrict__ out, long long V, long long NB,
-                                long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / V, site = i % V;
-        const float4* q = in + ((s * NB + (site >> 5)) * 6) * 32 + (site & 31);
-        float4* r = out + (s * V + site) * 6;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) r[k] = __ldg(q + k * 32);
-    }
-}
 template <class T> __device__ __forceinline__ T cvt_link_p(double2 v);
 template <> __device__ __forceinline__ float2 cvt_link_p<float2>(double2 v) {
     return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
@@ -378,7 +319,7 @@ extern "C" {
 
 size_t dwf_packed_spinor_size(const dwf_geom* g) {
     Geom G;
-    if (check_geom(g, &G) != DWF_OK || G.nd != 4) return 0;
+    if (check_geom(g, &G) != DWF_OK || G.nd != 4 || G.Ls % 2) return 0;
     return (size_t)(G.Ls * ((G.V + 31) / 32) * 32 * 12);
 }
 
@@ -412,28 +353,20 @@ dwf_status dwf_pack_spinor(const dwf_geom* g, const void* psi, void* packed, voi
     clear_error();
     Geom G;
     DWF_TRY(check_packed(g, &G));
-    const long long NB = (G.V + 31) / 32, n = (long long)G.Ls * NB * 32;
     if (!psi || !packed) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
     if (!aligned16(psi) || !aligned16(packed)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
     if (psi == packed) { set_error("psi and packed must be distinct buffers"); return DWF_ERR_ARG; }
-    cudaStream_t st = as_stream(stream);
-    k_pack_spinor<<<grid_for(n), 256, 0, st>>>((const float4*)psi, (float4*)packed, G.V, NB, n);
-    DWF_CHECK_LAUNCH();
-    return DWF_OK;
+    return pack_spinor_paired(G, psi, packed, as_stream(stream));
 }
 
 dwf_status dwf_unpack_spinor(const dwf_geom* g, const void* packed, void* psi, void* stream) {
     clear_error();
     Geom G;
     DWF_TRY(check_packed(g, &G));
-    const long long NB = (G.V + 31) / 32, n = (long long)G.Ls * G.V;
     if (!psi || !packed) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
     if (!aligned16(psi) || !aligned16(packed)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
     if (psi == packed) { set_error("psi and packed must be distinct buffers"); return DWF_ERR_ARG; }
-    cudaStream_t st = as_stream(stream);
-    k_unpack_spinor<<<grid_for(n), 256, 0, st>>>((const float4*)packed, (float4*)psi, G.V, NB, n);
-    DWF_CHECK_LAUNCH();
-    return DWF_OK;
+    return unpack_spinor_paired(G, packed, psi, as_stream(stream));
 }
 
 dwf_status dwf_apply_packed(const dwf_geom* g, const void* U_packed, const void* psi, void* out, double M5,
@@ -444,7 +377,7 @@ dwf_status dwf_apply_packed(const dwf_geom* g, const void* U_packed, const void*
     if (!U_packed || !psi || !out) { set_error("NULL device pointer"); return DWF_ERR_ARG; }
     if (!aligned16(psi) || !aligned16(out)) { set_error("spinor buffers must be 16-byte aligned"); return DWF_ERR_ARG; }
     if (psi == out) { set_error("psi and out must be distinct buffers"); return DWF_ERR_ARG; }
-    return fine_apply_4d_packed(G, U_packed, psi, out, M5, mf, dagger != 0, prec, as_stream(stream));
+    return fine_apply_4d_paired(G, U_packed, psi, out, M5, mf, dagger != 0, prec, as_stream(stream));
 }
 
 }  // extern "C"

@@ -31,6 +31,42 @@ struct MgGeom {
 // Device-owned buffers are released by a single cudaFree of `arena`.
 struct dwf_mg_impl;
 
+// Parameters of one coarse stencil launch (Eq. coarsenDW on a coarse lattice).
+struct CoarseParams {
+    long long Vc;
+    int nd;
+    int Lc[4];
+    int Ls_c;
+    int ncd, nvec, ndir;
+    float mf;
+};
+
+// Aggregation of a lattice L into blocks b (coarse lattice Lc).
+struct AggIndex {
+    int nd, L[4], b[4], Lc[4];
+    // fine site of local index l in aggregate xc
+    __host__ __device__ long long fine_site(long long xc, int l) const {
+        long long site = 0, stride = 1;
+        long long rem = xc;
+        int lr = l;
+        for (int mu = 0; mu < nd; ++mu) {
+            int c = (int)(rem % Lc[mu]);
+            rem /= Lc[mu];
+            int lc = lr % b[mu];
+            lr /= b[mu];
+            site += (long long)(c * b[mu] + lc) * stride;
+            stride *= L[mu];
+        }
+        return site;
+    }
+};
+
+// State of one near-null relaxation (CG on the homogeneous normal system).
+struct NvState {
+    double rr, rr0, alpha, beta;
+    int done, iters;
+};
+
 }  // namespace dwf
 
 struct dwf_mg {
@@ -67,6 +103,7 @@ struct dwf_mg {
     cudaGraphExec_t coarse_graph_cycle;   // captured coarse GCR: one restart cycle
     cudaStream_t cap_stream;              // private stream used only to record graphs
     void* batched;                        // workspace and graphs of the batched solver (mg_batched.cu)
+    void* lvl3;                           // third level and coarsest deflation (mg_level3.cu), or nullptr
     mutable std::map<int, int> tc_choice; // autotuned form of the many-right-hand-side coarse contraction, by nrhs
 };
 
@@ -117,6 +154,35 @@ bool coarse_gcr_persistent_ok(const dwf_mg* h);
 dwf_status coarse_gcr_persistent(const dwf_mg* h, const float2* rc, float2* ec, float2* const* S, float2* const* W,
                                  float2* t, double* partials, void* bar, int* out_iters, double* out_rr2,
                                  cudaStream_t st);
+
+// per-site kernel of the coarse stencil on FP32 column-major blocks (any
+// coarse lattice with 24 <= ncd, ncd * Ls_c <= 512); the adjoint uses sigma_3
+dwf_status coarse_site_apply(const CoarseParams& p, const float2* B, const float2* in, float2* out, bool dagger,
+                             const int* skip, int* status, cudaStream_t st);
+
+// grid of an element-wise kernel over n values (at most 8 blocks of 256 per SM)
+inline int level_ew_grid(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 152LL * 8 ? b : 152LL * 8);
+}
+
+// setup kernels shared with the third level (mg_setup.cu)
+__global__ void __launch_bounds__(RED_THREADS) k_nv_init(double2* __restrict__ r, const double2* __restrict__ Av, long long n, RedScratch rs,
+                          NvState* S, int maxiter);
+__global__ void __launch_bounds__(RED_THREADS) k_nv_alpha(const double2* __restrict__ t, long long n, RedScratch rs, NvState* S);
+__global__ void __launch_bounds__(RED_THREADS) k_nv_update(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
+                            const double2* __restrict__ Ap, long long n, RedScratch rs, NvState* S, double tol2,
+                            int maxiter);
+__global__ void k_nv_p(double2* __restrict__ p, const double2* __restrict__ r, long long n, const NvState* S);
+__global__ void k_block_ortho(const double2* __restrict__ vecs, double2* __restrict__ P, AggIndex ai, int nchd,
+                              int ncol, int dof, int nvec, long long V, int nb, int* status, int cblock);
+__global__ void k_blocks_to_f32(const double2* __restrict__ Y, float2* __restrict__ Y32, long long nblocks, int ncd);
+__global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n);
+
+// the third level: the level-2 solve of the K-cycle (FGCR preconditioned by the
+// level-3 solve) from r_c to e_c on one right-hand side; iteration counts out
+dwf_status level2_solve(dwf_mg* h, const float2* rc, float2* ec, int* l2_iters, int* l3_iters, cudaStream_t st);
+void level3_free(dwf_mg* h);
 
 inline long long fine_len(const dwf_mg* h) { return h->G.V * h->G.Ls * site_dof(h->G); }
 inline long long coarse_len(const dwf_mg* h) { return h->mg.Vc * h->mg.Ls_c * h->mg.ncd; }

@@ -563,6 +563,8 @@ struct BSolver {
     BView* v;
     cudaStream_t st;
     int nrhs;
+    long long l3_iters = 0;      // coarsest iterations of a three-level hierarchy
+    long long l3_solves = 0;     // and coarsest solves
 };
 
 static dim3 row_grid(long long n2, int nrhs, int cap = 1216) {
@@ -732,7 +734,16 @@ static dwf_status bprecondition(BSolver& s, const float2* res, float2* zout, flo
     const long long n = v.nf;
     const dim3 eg = row_grid(n >> 1, s.nrhs);
     DWF_TRY(restrict_wall(h, res, v.rc, v.idone, s.st, s.nrhs));
-    DWF_TRY(bcoarse_solve(s, citers_out));
+    if (h->lvl3) {
+        // three levels: flexible GCR on the intermediate level, preconditioned by the coarsest solve
+        int l2 = 0, l3 = 0;
+        DWF_TRY(level2_solve(h, v.rc, v.ec, &l2, &l3, s.st));
+        citers_out[0] = l2;
+        s.l3_iters += l3;
+        s.l3_solves += l2;
+    } else {
+        DWF_TRY(bcoarse_solve(s, citers_out));
+    }
     DWF_TRY(prolong_wall(h, v.ec, zout, v.idone, s.st, s.nrhs));
     const int S = h->prm.post_smooth;
     if (S == 0) return bapply_A(s, zout, wout, v.idone);
@@ -769,6 +780,10 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
     if (!h || !B || !X) { set_error("NULL argument"); return DWF_ERR_ARG; }
     if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
     if (!(tol > 0.0)) { set_error("tol must be > 0"); return DWF_ERR_ARG; }
+    if (nrhs > 1 && h->lvl3) {
+        set_error("a three-level hierarchy solves one right-hand side per call");
+        return DWF_ERR_UNSUPPORTED;
+    }
     if (nrhs > 1 && (h->mg.nd != 2 || h->mg.ncd != 16)) {
         set_error("more than one right-hand side per hierarchy needs a 2-d lattice with nvec = 8");
         return DWF_ERR_UNSUPPORTED;
@@ -914,6 +929,7 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
             stats[r].fine_applies = fine[r];
             stats[r].coarse_applies = 2 * coarse_it[r];
             stats[r].coarse_avg_iters = coarse_solves[r] ? (double)coarse_it[r] / coarse_solves[r] : 0.0;
+            stats[r].coarsest_avg_iters = s.l3_solves ? (double)s.l3_iters / s.l3_solves : 0.0;
             stats[r].true_residual = res[r];
             stats[r].seconds = secs;
         }

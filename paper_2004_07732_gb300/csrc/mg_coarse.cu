@@ -12,15 +12,6 @@
 
 namespace dwf {
 
-struct CoarseParams {
-    long long Vc;
-    int nd;
-    int Lc[4];
-    int Ls_c;
-    int ncd, nvec, ndir;
-    float mf;
-};
-
 __device__ __forceinline__ long long coarse_neighbour(const CoarseParams& p, long long xc, int dir) {
     if (dir == 0) return xc;
     const int mu = (dir - 1) >> 1;
@@ -613,6 +604,16 @@ dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, doub
     return DWF_OK;
 }
 
+dwf_status coarse_site_apply(const CoarseParams& p, const float2* B, const float2* in, float2* out, bool dagger,
+                             const int* skip, int* status, cudaStream_t st) {
+    if (!site_ok(p, 0)) { set_error("the per-site coarse stencil does not take %d dof on %d slices", p.ncd, p.Ls_c);
+                          return DWF_ERR_UNSUPPORTED; }
+    k_coarse_site<float2><<<(unsigned)p.Vc, p.ncd * p.Ls_c, site_smem_bytes<float2>(p.ndir, p.ncd, p.Ls_c), st>>>(
+        B, in, out, p, dagger, skip, status);
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
 // Yd[x][dir] (column-major) = Y[x + dir][-dir]^dag from the row-major FP64 blocks.
 __global__ void k_adjoint_blocks(const double2* __restrict__ Y, float2* __restrict__ Yd, CoarseParams p) {
     const int ncd = p.ncd;
@@ -647,6 +648,7 @@ struct TransferParams {
     int nd, L[4], b[4], Lc[4];
     long long V, Vc;
     int Ls, Ls_c, nvec, ncd, nchd, dof, ncol, nb;
+    int bulk;            // 1: P^dag / P on every slice (Lhat_s = Ls) instead of the walls
 };
 
 __device__ __forceinline__ long long agg_of(const TransferParams& p, long long site) {
@@ -699,6 +701,7 @@ __global__ void k_restrict(const float2* __restrict__ P, const float2* __restric
     int sf = -1;
     if (c == 1 && s == 0) sf = 0;                 // Phat_- P^dag P_- r_1 on coarse slice 1
     if (c == 0 && s == p.Ls_c - 1) sf = p.Ls - 1; // Phat_+ P^dag P_+ r_Ls on coarse slice Lhat_s
+    if (p.bulk) sf = s;                           // bulk: every slice
     if (sf >= 0) {
         const float2* rs = r + (long long)sf * p.V * p.dof;
         for (int l = 0; l < p.nb; ++l) {
@@ -729,6 +732,7 @@ __global__ void k_prolong(const float2* __restrict__ P, const float2* __restrict
     int sc = -1;
     if (c == 1 && s == 0) sc = 0;                 // P_- P e_1 on fine slice 1
     if (c == 0 && s == p.Ls - 1) sc = p.Ls_c - 1; // P_+ P e_{Lhat_s} on fine slice Ls
+    if (p.bulk) sc = s;                           // bulk: every slice
     if (sc >= 0) {
         const long long xc = agg_of(p, x);
         const float2* ev = e + ((long long)sc * p.Vc + xc) * p.ncd + c * p.nvec;
@@ -752,6 +756,7 @@ static TransferParams transfer_params(const dwf_mg* h) {
     p.dof = (int)site_dof(h->G);
     p.ncol = h->G.ncol;
     p.nb = h->mg.nb;
+    p.bulk = h->prm.transfer == 1 ? 1 : 0;
     return p;
 }
 

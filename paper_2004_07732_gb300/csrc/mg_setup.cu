@@ -20,11 +20,6 @@ namespace dwf {
 // ---------------------------------------------------------------------------
 // 1. near-null relaxation: FP64 CG kernels with a device-side stop flag
 // ---------------------------------------------------------------------------
-struct NvState {
-    double rr, rr0, alpha, beta;
-    int done, iters;
-};
-
 __global__ void __launch_bounds__(RED_THREADS) k_nv_init(double2* __restrict__ r, const double2* __restrict__ Av, long long n,
                                                          RedScratch rs, NvState* S, int maxiter) {
     double v[1] = {0.0};
@@ -126,25 +121,6 @@ static dwf_status relax_null(dwf_mg* h, double2* v, double2* r, double2* p, doub
 // ---------------------------------------------------------------------------
 // 2. chiral doubling + block Gram-Schmidt
 // ---------------------------------------------------------------------------
-struct AggIndex {
-    int nd, L[4], b[4], Lc[4];
-    // fine site of local index l in aggregate xc
-    __host__ __device__ long long fine_site(long long xc, int l) const {
-        long long site = 0, stride = 1;
-        long long rem = xc;
-        int lr = l;
-        for (int mu = 0; mu < nd; ++mu) {
-            int c = (int)(rem % Lc[mu]);
-            rem /= Lc[mu];
-            int lc = lr % b[mu];
-            lr /= b[mu];
-            site += (long long)(c * b[mu] + lc) * stride;
-            stride *= L[mu];
-        }
-        return site;
-    }
-};
-
 // fine dof index within a site of chirality c, chirality-local index l
 __host__ __device__ __forceinline__ int chiral_dof(int nd, int ncol, int c, int l) {
     if (nd == 2) return c;                        // spin c, one colour
@@ -152,9 +128,11 @@ __host__ __device__ __forceinline__ int chiral_dof(int nd, int ncol, int c, int 
 }
 
 // One warp per (aggregate, chirality): Gram-Schmidt (twice) of the nvec
-// vectors' chirality-c halves restricted to the aggregate.
+// vectors' chirality-c halves restricted to the aggregate.  cblock = 0: fine
+// sites (spin / colour dof, chirality from gamma_5); cblock > 0: coarse sites
+// whose dof are [chirality][cblock] (chirality from sigma_3).
 __global__ void k_block_ortho(const double2* __restrict__ vecs, double2* __restrict__ P, AggIndex ai, int nchd,
-                              int ncol, int dof, int nvec, long long V, int nb, int* status) {
+                              int ncol, int dof, int nvec, long long V, int nb, int* status, int cblock) {
     extern __shared__ double2 smem[];   // [nvec][nb*nchd]
     const long long xc = blockIdx.x;
     const int c = blockIdx.y;
@@ -164,7 +142,8 @@ __global__ void k_block_ortho(const double2* __restrict__ vecs, double2* __restr
         for (int e = lane; e < na; e += 32) {
             int l = e / nchd, cd = e % nchd;
             long long site = ai.fine_site(xc, l);
-            smem[k * na + e] = vecs[(long long)k * V * dof + site * dof + chiral_dof(ai.nd, ncol, c, cd)];
+            smem[k * na + e] = vecs[(long long)k * V * dof + site * dof +
+                                    (cblock ? c * cblock + cd : chiral_dof(ai.nd, ncol, c, cd))];
         }
     __syncwarp();
     for (int k = 0; k < nvec; ++k) {
@@ -548,7 +527,8 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
         dim3 grid((unsigned)m.Vc, 2);
         size_t sh = (size_t)m.nvec * m.nb * m.nchd * sizeof(double2);
         if (sh > 48 * 1024) DWF_CHECK_CUDA(cudaFuncSetAttribute(k_block_ortho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        k_block_ortho<<<grid, 32, sh, st>>>(h->nullv, h->P64, ai, m.nchd, G.ncol, (int)dof, m.nvec, G.V, m.nb, h->status);
+        k_block_ortho<<<grid, 32, sh, st>>>(h->nullv, h->P64, ai, m.nchd, G.ncol, (int)dof, m.nvec, G.V, m.nb, h->status,
+                                            0);
         DWF_CHECK_LAUNCH();
     }
     k_d2f<<<ew_grid(Psz), 256, 0, st>>>(h->P64, h->P32, Psz);
@@ -632,6 +612,7 @@ void dwf_mg_default_params(dwf_mg_params* p) {
     p->coarse_block_prec = DWF_F32_L16;
     p->cgs_passes = 1;
     p->coarse_tc = 0;
+    p->transfer = 0;
 }
 
 dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,
@@ -653,6 +634,10 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
     if (prm.coarse_tc < 0 || prm.coarse_tc > 4) { set_error("coarse_tc must be in [0, 4]"); return DWF_ERR_ARG; }
     if (prm.coarse_block_prec != DWF_F32 && prm.coarse_block_prec != DWF_F32_L16) {
         set_error("coarse_block_prec must be DWF_F32 or DWF_F32_L16"); return DWF_ERR_ARG;
+    }
+    if (prm.transfer != 0 && prm.transfer != 1) { set_error("transfer must be 0 (walls) or 1 (bulk)"); return DWF_ERR_ARG; }
+    if (prm.transfer == 1 && prm.Ls_c != G.Ls) {
+        set_error("the bulk transfer keeps every slice: Ls_c must equal Ls (%d)", G.Ls); return DWF_ERR_ARG;
     }
     if (prm.gcr_restart < 1 || prm.post_smooth < 0 || prm.coarse_maxiter < 1 || prm.setup_maxiter < 0) {
         set_error("bad solver parameters"); return DWF_ERR_ARG;
@@ -701,6 +686,7 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
     h->coarse_graph_cycle = nullptr;
     h->cap_stream = nullptr;
     h->batched = nullptr;
+    h->lvl3 = nullptr;
     dwf_status s = coarse_init_attributes();
     if (s == DWF_OK) s = setup_impl(h, U, null_starts);
     if (s != DWF_OK) {
@@ -717,6 +703,7 @@ void mg_destroy(dwf_mg* h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
     batched_state_free(h);
+    level3_free(h);
     for (void* p : h->allocs) cudaFree(p);
     for (void* p : h->fine_vecs) cudaFree(p);
     for (void* p : h->coarse_vecs) cudaFree(p);

@@ -685,7 +685,7 @@ extern "C" dwf_status mg_solve(dwf_mg* h, const void* b, void* x, double tol, in
         set_error("gcr_restart, post_smooth and coarse_restart must be in [1, %d]", GCR_MAXK); return DWF_ERR_ARG;
     }
     if (stream) h->st = as_stream(stream);
-    if (h->prm.coarse_solver == 1 && h->prm.coarse_persistent != 2) {
+    if ((h->prm.coarse_solver == 1 && h->prm.coarse_persistent != 2) || h->lvl3) {
         // the same K-cycle through the right-hand-side-batched implementation with one
         // column: its GCR updates only w and r per step and assembles the solution
         // once per cycle (fewer passes over the fine vectors)

@@ -131,6 +131,8 @@ SCHWINGER_256_SMOOTH = Workload("u1_2d_256x256_Ls16_smooth", (256, 256), 16, "u1
 SCHWINGER_128_GRAD = Workload("u1_2d_128x128_Ls12", (128, 128), 12, "u1", 0.7, 1.0, 0.005, 1004)
 SCHWINGER_1024 = Workload("u1_2d_1024x1024_Ls16", (1024, 1024), 16, "u1", 0.7, 1.0, 0.005, 1006)
 SU3_16x32 = Workload("su3_4d_16x16x16x32_Ls16", (16, 16, 16, 32), 16, "su3", 0.3, 1.8, 0.01, 1005)
+# the coarse-Ls study of the paper's discussion (a 128^2 field near beta 6, outer Ls = 32)
+SCHWINGER_128_LS32 = Workload("u1_2d_128x128_Ls32_smooth", (128, 128), 32, "u1", 0.214, 1.0, 0.01, 1007)
 
 
 def batched_classes():

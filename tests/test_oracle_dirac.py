@@ -273,3 +273,71 @@ def test_generic_point_evaluator_matches_assembled_operator(group, dims, dag):
     pts = [(s, x) for s in range(Ls) for x in range(V)]
     pv = dirac.dwf_apply_points(U, psi, dims, Ls, 1.3, 0.05, pts, group=group, dagger_=dag, antiperiodic=anti)
     assert np.abs(pv.reshape(len(pts), -1) - np.array([full[s, x] for s, x in pts])).max() < 1e-13
+
+
+@pytest.mark.parametrize("b5,c5", [(1.5, 0.5), (2.0, 1.0), (1.3, 0.1)])
+def test_mobius_overlap_identity_and_shamir_limit(b5, c5):
+    """The Mobius form reduces to Shamir at b5 = 1, c5 = 0, and its K_DW = (D_PV P)^-1 D_M P has identity
+    columns s > 1 and K_11 = (1+m)/2 - (1-m)/2 eps_Ls[X] gamma_5 with the Mobius kernel
+    X = gamma_5 (b5 + c5) D_W (2 + (b5 - c5) D_W)^-1 (the Shamir identity of Eq. DWFmatrix, R6,
+    with the kernel scaled as the Mobius family prescribes)."""
+    dims, Ls, m = (4, 4), 4, 0.05
+    V, n = 16, 32
+    U = _rand_u1(dims, 0.5, 4)
+    assert abs(dirac.mobius_matrix(U, dims, Ls, 1.0, m, 1.0, 0.0) - dirac.dwf_matrix(U, dims, Ls, 1.0, m)).max() == 0
+    Dd = dirac.mobius_matrix(U, dims, Ls, 1.0, m, b5, c5).toarray()
+    Dp = dirac.mobius_matrix(U, dims, Ls, 1.0, 1.0, b5, c5).toarray()
+    P = dirac.chiral_permutation(V, Ls, 2, 1).toarray()
+    K = np.linalg.solve(Dp @ P, Dd @ P)
+    for s in range(1, Ls):
+        want = np.zeros((Ls * n, n)); want[s * n:(s + 1) * n] = np.eye(n)
+        assert np.abs(K[:, s * n:(s + 1) * n] - want).max() < 1e-10
+    Dw = dirac.wilson_matrix(U, dims, -1.0).toarray()
+    G5 = np.kron(np.eye(V), np.diag([1.0, -1.0]))
+    I = np.eye(n)
+    X = G5 @ ((b5 + c5) * Dw) @ np.linalg.inv(2 * I + (b5 - c5) * Dw)
+    A = np.linalg.matrix_power(I - X, Ls)
+    B = np.linalg.matrix_power(I + X, Ls)
+    Dov = 0.5 * (1 + m) * I - 0.5 * (1 - m) * ((A - B) @ np.linalg.inv(A + B)) @ G5
+    assert np.abs(K[:n, :n] - Dov).max() < 1e-10
+    # a wrong sign of c5 breaks the identity
+    Dd2 = dirac.mobius_matrix(U, dims, Ls, 1.0, m, b5, -c5).toarray()
+    Dp2 = dirac.mobius_matrix(U, dims, Ls, 1.0, 1.0, b5, -c5).toarray()
+    K2 = np.linalg.solve(Dp2 @ P, Dd2 @ P)
+    assert np.abs(K2[:n, :n] - Dov).max() > 1e-3
+
+
+def test_pv_polynomial_orders_in_the_free_field():
+    """Free field at the optimal height (momentum blocks of D_PV, Ls 8): the truncations c = (1),
+    (2, -1), (3, -3, 1) of D_PV^-1 = D_PV^dag [D_PV D_PV^dag]^-1 each gain two powers of p (App. A):
+    the error halving p shrinks by ~4, ~16, ~64."""
+    Ls = 8
+    orders = [(1.0,), (2.0, -1.0), (3.0, -3.0, 1.0)]
+
+    def err(p0, c):
+        B = dirac.free_dwf_symbol((p0, 0.7 * p0), Ls, 1.0, 1.0, 2)
+        N = B @ B.conj().T
+        poly = sum(ck * np.linalg.matrix_power(N, k) for k, ck in enumerate(c))
+        return np.linalg.norm(np.linalg.inv(B) - B.conj().T @ poly, 2)
+
+    for k, c in enumerate(orders):
+        r = err(0.1, c) / err(0.05, c)
+        assert abs(r / 4 ** (k + 1) - 1) < 0.1, (c, r)
+
+
+def test_pv_poly_operator_limits():
+    """c = (1) is D_PV^dag D_DW; with the exact polynomial of a tiny lattice's D_PV D_PV^dag (its
+    characteristic polynomial gives [D_PV D_PV^dag]^-1 exactly) the operator is D_PV^-1 D_DW."""
+    dims, Ls, m = (2, 2), 2, 0.05
+    U = _rand_u1(dims, 0.5, 9)
+    Dd = dirac.dwf_matrix(U, dims, Ls, 1.0, m)
+    Dp = dirac.pv_matrix(U, dims, Ls, 1.0)
+    assert abs(dirac.pv_poly_operator(Dd, Dp, (1.0,)) - dirac.pvdag_dwf_matrix(U, dims, Ls, 1.0, m)).max() < 1e-14
+    N = (Dp @ dirac.dagger(Dp)).toarray()
+    ch = np.poly(N)                       # N^n + a_1 N^(n-1) + ... + a_n = 0 (Cayley-Hamilton)
+    n = N.shape[0]
+    # N^-1 = -(N^(n-1) + a_1 N^(n-2) + ... + a_(n-1)) / a_n
+    coeffs = [-ch[n - 1 - k] / ch[n] for k in range(n - 1)] + [-1.0 / ch[n]]
+    got = dirac.pv_poly_operator(Dd, Dp, coeffs).toarray()
+    want = np.linalg.solve(Dp.toarray(), Dd.toarray())
+    assert np.abs(got - want).max() < 1e-6 * np.abs(want).max()

@@ -360,3 +360,35 @@ def test_three_level_kcycle_solves_to_tolerance(n_deflate):
     assert max(ml.l2_iters) <= 16 and len(ml.l3_iters) >= len(ml.l2_iters)
     _, it_cg, _ = solvers.cgnr(ml.Ddw, b, tol=1e-10)
     assert outer < it_cg / 4
+
+
+def test_transfer_diagnostics_limits():
+    """The transfer-study diagnostics: bulk restriction and prolongation are adjoint; with single-site
+    aggregates holding the full chiral spin space (P = 1) the bulk transfer keeps every vector
+    (colinearity 0) and its coarse operator is the fine one, so one exact coarse correction leaves no
+    error (oblique projector 0); the wall transfer keeps only the wall field, so its colinearity is
+    the bulk share of v."""
+    dims, Ls, M5, m = (4, 4), 4, 1.0, 0.05
+    V = 16
+    U = _u1(dims, 0.5, 41)
+    P, _ = mg.build_prolongator([np.ones(2 * V, dtype=complex)], dims, (1, 1), 2, 1)
+    rng = np.random.default_rng(42)
+    r = synth.gaussian_complex(rng, (Ls * 2 * V,))
+    ec = synth.gaussian_complex(rng, (Ls * P.shape[1],))
+    assert abs(np.vdot(ec, mg.restrict_bulk(r, P, Ls)) - np.vdot(mg.prolong_bulk(ec, P, Ls), r)) < 1e-12 * 100
+    A = dirac.pvdag_dwf_matrix(U, dims, Ls, M5, m)
+    Dhat = mg.galerkin_kernel(P, dirac.wilson_matrix(U, dims, -M5))
+    Ac = (dirac.dagger(mg.coarse_dwf(Dhat, Ls, 1.0, 1)) @ mg.coarse_dwf(Dhat, Ls, m, 1)).tocsr()
+    assert abs(Ac - A).max() < 1e-14
+    v = synth.gaussian_complex(rng, (Ls * 2 * V,))
+    R = lambda x: mg.restrict_bulk(x, P, Ls)
+    Pr = lambda x: mg.prolong_bulk(x, P, Ls)
+    assert mg.colinearity(v, R, Pr) < 1e-14
+    assert mg.oblique(v, A, Ac, R, Pr) < 1e-10
+    # wall transfer: P R v keeps P_- v_1 and P_+ v_Ls only
+    Rw = lambda x: mg.restrict(x, P, Ls, Ls, 2, 1, 1)
+    Pw = lambda x: mg.prolong(x, P, Ls, Ls, 2, 1, 1)
+    vv = v.reshape(Ls, V, 2)
+    kept = np.sum(np.abs(vv[0, :, 1]) ** 2) + np.sum(np.abs(vv[Ls - 1, :, 0]) ** 2)
+    want = np.sqrt(1 - kept / np.sum(np.abs(v) ** 2))
+    assert abs(mg.colinearity(v, Rw, Pw) - want) < 1e-13
