@@ -42,7 +42,7 @@ __device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc) {   
 // [coarse site][dir]: the Galerkin blocks of Dhat_W for the operator, or the
 // pre-transposed blocks of Dhat_W^dag (block (x, dir) = Y(x + dir, -dir)^dag)
 // for the adjoint, so both read B coalesced.  Lane l owns rows
-// i = (l & 15) + 16 k and slices s = (l >> 4) + 2 k'; the j loop is unrolled so
+// i = (l & 15) + 16 k and slices s = 8 g + (l >> 4) + 2 k' (g = 0, 1, .. for Ls_c > 8); the j loop is unrolled so
 // every block and input load of a direction is in flight together.  CG = true
 // reads the input through L2 (other blocks of a persistent launch wrote it).
 // Returns the lane's share of |out|^2.
@@ -55,11 +55,13 @@ __device__ __forceinline__ double warp_site_apply(const float2* __restrict__ B, 
     const long long bsz = (long long)ncd * ncd;
     const int sg = lane >> 4;
     double nrm = 0.0;
+    // slices in groups of 8 (the blocks of a later group come from L1/L2)
+    for (int s0 = 0; s0 < p.Ls_c; s0 += 8)
     for (int i = lane & 15; i < ncd; i += 16) {
         float2 acc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int s = sg + 2 * k;
+            const int s = s0 + sg + 2 * k;
             acc[k] = make_float2(0.f, 0.f);
             if (s < p.Ls_c) acc[k] = CG ? __ldcg(in + s * slice + xc * ncd + i) : __ldg(in + s * slice + xc * ncd + i);
         }
@@ -72,7 +74,7 @@ __device__ __forceinline__ double warp_site_apply(const float2* __restrict__ B, 
                 const float2 y = __ldg(Bb + (long long)j * ncd);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int s = sg + 2 * k;
+                    const int s = s0 + sg + 2 * k;
                     if (s < p.Ls_c) acc[k] = cfma(y, CG ? __ldcg(v + s * slice + j) : __ldg(v + s * slice + j), acc[k]);
                 }
             }
@@ -81,7 +83,7 @@ __device__ __forceinline__ double warp_site_apply(const float2* __restrict__ B, 
         const bool from_below = dag ? (c == 1) : (c == 0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int s = sg + 2 * k;
+            const int s = s0 + sg + 2 * k;
             if (s >= p.Ls_c) break;
             long long hi;
             float sc = 1.f;
@@ -575,7 +577,6 @@ static CoarseParams coarse_params(const dwf_mg* h, double mf) {
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger, const int* skip,
                             cudaStream_t st) {
     CoarseParams p = coarse_params(h, mf);
-    if (p.Ls_c > 8) { set_error("the coarse stencil supports Ls_c <= 8"); return DWF_ERR_UNSUPPORTED; }
     const int thr = 256;
     const unsigned grid = (unsigned)((p.Vc * 32 + thr - 1) / thr);
     const float2* B = dagger ? h->Yd32 : h->Y32;

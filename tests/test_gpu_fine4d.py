@@ -98,31 +98,50 @@ def test_dwf4d_adjoint_and_cgne(dw):
 
 
 def _packed_positions(dims, Ls):
-    """Float4 index in the packed layout of every (s, site, piece) in canonical order."""
+    """Float offsets in the slice-paired packed layout of the real and imaginary parts of every
+    (s, site, k) in canonical order: float4 ((s/2 NB + site/32) 12 + k) 32 + site%32 holds
+    (Re slice 2j, Re slice 2j+1, Im slice 2j, Im slice 2j+1)."""
     V = int(np.prod(dims))
     NB = (V + 31) // 32
-    s, site, k = np.meshgrid(np.arange(Ls), np.arange(V), np.arange(6), indexing="ij")
-    return ((s * NB + site // 32) * 6 + k) * 32 + site % 32, NB
+    s, site, k = np.meshgrid(np.arange(Ls), np.arange(V), np.arange(12), indexing="ij")
+    f4 = (((s // 2) * NB + site // 32) * 12 + k) * 32 + site % 32
+    return 4 * f4 + s % 2, 4 * f4 + 2 + s % 2, NB
 
 
-@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 4), ((3, 5, 2, 3), 3), ((2, 2, 2, 2), 2)])
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 4), ((3, 5, 2, 3), 2), ((2, 2, 2, 2), 2), ((3, 5, 2, 3), 6)])
 def test_pack_unpack_layout(dw, dims, Ls):
-    """Packing places piece k of (s, site) at ((s NB + site/32) 6 + k) 32 + site%32; unpacking inverts it."""
+    """Packing places (s, site, k) as above; padding sites are zero; unpacking inverts it."""
     rng = synth.rng_for(7)
     psi = synth.gaussian_spinor(rng, dims, Ls, "su3")
     g = dw.make_geom(dims, Ls, group="su3")
     pd = _dev(psi, torch.complex64)
     pk = dw.pack_spinor(g, pd)
-    pos, NB = _packed_positions(dims, Ls)
+    pre, pim, NB = _packed_positions(dims, Ls)
     assert pk.numel() == Ls * NB * 32 * 12
-    f4 = pk.cpu().numpy().view(np.float32).reshape(-1, 4)
-    canon = pd.cpu().numpy().view(np.float32).reshape(-1, 4)
-    assert np.array_equal(f4[pos.reshape(-1)], canon)
-    pad = np.ones(f4.shape[0], bool)
-    pad[pos.reshape(-1)] = False
-    assert not f4[pad].any()                         # padding sites are zero
+    fl = pk.cpu().numpy().view(np.float32)
+    canon = pd.cpu().numpy().reshape(-1)
+    assert np.array_equal(fl[pre.reshape(-1)], canon.real)
+    assert np.array_equal(fl[pim.reshape(-1)], canon.imag)
+    pad = np.ones(fl.shape[0], bool)
+    pad[pre.reshape(-1)] = False
+    pad[pim.reshape(-1)] = False
+    assert not fl[pad].any()                         # padding sites are zero
     back = dw.unpack_spinor(g, pk)
     assert torch.equal(back, pd)
+
+
+def test_packed_layout_needs_even_Ls(dw):
+    """Odd Ls has no slice-paired layout: size 0, and the C entry points return DWF_ERR_UNSUPPORTED."""
+    import ctypes
+    g = dw.make_geom((4, 4, 4, 4), 3, group="su3")
+    assert dw.packed_spinor_size(g) == 0
+    pd = torch.zeros(dw.spinor_size(g), dtype=torch.complex64, device="cuda")
+    out = torch.zeros(dw.spinor_size(g) * 2, dtype=torch.complex64, device="cuda")
+    st = dw.lib().dwf_pack_spinor(ctypes.byref(g), ctypes.c_void_p(pd.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), None)
+    assert st == 6                                   # DWF_ERR_UNSUPPORTED
+    with pytest.raises(ValueError):
+        dw.pack_spinor(g, pd, out=out)
 
 
 def test_pack_links_layout(dw):
@@ -138,8 +157,8 @@ def test_pack_links_layout(dw):
     assert np.array_equal(Up, want.reshape(4, NB, 32, 9).transpose(0, 1, 3, 2))
 
 
-@pytest.mark.parametrize("dims,Ls,anti", [((4, 4, 4, 4), 4, None), ((3, 5, 2, 3), 3, [0, 0, 0, 1]),
-                                          ((2, 2, 2, 2), 2, [1, 1, 1, 1]), ((6, 4, 4, 8), 5, None)])
+@pytest.mark.parametrize("dims,Ls,anti", [((4, 4, 4, 4), 4, None), ((3, 5, 2, 3), 6, [0, 0, 0, 1]),
+                                          ((2, 2, 2, 2), 2, [1, 1, 1, 1]), ((6, 4, 4, 8), 8, None)])
 @pytest.mark.parametrize("prec", ["f32", "f32_l16", "f32_lbf16"])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dwf4d_packed_apply_parity(dw, dims, Ls, anti, prec, dagger):
