@@ -6,7 +6,7 @@ include/dwf.h; this package only marshals torch tensors to device pointers.
 from ._lib import (  # noqa: F401
     DwfError, Geom, SolveStats, PREC, lib, make_geom, spinor_size, link_size, spinor_dtype,
     links_to, dwf_apply, pv_apply, dwf_pvdag_apply, dwf_pvdag_apply_noalloc, dwf_dot, cgne_solve, bicgstab_solve,
-    links_from_angles, gamma5_reflect, link_force, link_grad, dwf_apply_batched, check_wait_timeout, dwf_apply_host,
+    links_from_angles, gamma5_reflect, link_force, link_grad, dwf_apply_batched, BatchedApply, check_wait_timeout, dwf_apply_host,
     packed_spinor_size, packed_link_size, pack_links, pack_spinor, unpack_spinor, dwf_apply_packed,
     dwf_mobius_apply, dwf_pv_poly_apply,
 )

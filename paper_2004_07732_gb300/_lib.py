@@ -390,20 +390,35 @@ def bicgstab_solve(geom, U, b, x, M5, mf, ell=6, tol=1e-10, maxiter=100000, inne
     return st.as_dict(), status
 
 
+class BatchedApply:
+    """dwf_apply_batched with its argument arrays built once: a caller that applies the operator
+    to the same set of (geometry, links, psi, out) many times pays the marshalling once and each
+    call is a single C call.  Holds references to the tensors it was built from."""
+
+    def __init__(self, geoms, Us, psis, outs, prec="f32_l16"):
+        n = len(psis)
+        if not (len(geoms) == len(Us) == len(outs) == n):
+            raise ValueError("geoms, Us, psis and outs must have the same length")
+        for g, p, o in zip(geoms, psis, outs):
+            _check_spinor(p, g, prec, "psi")
+            _check_spinor(o, g, prec, "out")
+        self._keep = (list(Us), list(psis), list(outs))
+        self.n = n
+        self.prec = PREC[prec]
+        self.G = (Geom * n)(*geoms)
+        self.U = (_VP * n)(*[u.data_ptr() for u in Us])
+        self.P = (_VP * n)(*[p.data_ptr() for p in psis])
+        self.O = (_VP * n)(*[o.data_ptr() for o in outs])
+
+    def __call__(self, M5, mf, dagger=False, stream=None):
+        check(lib().dwf_apply_batched(self.n, self.G, self.U, self.P, self.O, float(M5), float(mf),
+                                      int(bool(dagger)), self.prec, _stream(stream)))
+        return self._keep[2]
+
+
 def dwf_apply_batched(geoms, Us, psis, outs, M5, mf, dagger=False, prec="f32_l16", stream=None):
     """One launch applying D_DW to every (geometry, links, psi) triple of the lists."""
-    n = len(psis)
-    if not (len(geoms) == len(Us) == len(outs) == n):
-        raise ValueError("geoms, Us, psis and outs must have the same length")
-    for g, p, o in zip(geoms, psis, outs):
-        _check_spinor(p, g, prec, "psi")
-        _check_spinor(o, g, prec, "out")
-    G = (Geom * n)(*geoms)
-    U = (_VP * n)(*[u.data_ptr() for u in Us])
-    P = (_VP * n)(*[p.data_ptr() for p in psis])
-    O = (_VP * n)(*[o.data_ptr() for o in outs])
-    check(lib().dwf_apply_batched(n, G, U, P, O, float(M5), float(mf), int(bool(dagger)), PREC[prec], _stream(stream)))
-    return outs
+    return BatchedApply(geoms, Us, psis, outs, prec)(M5, mf, dagger, stream)
 
 
 def dwf_apply_host(geom, U_host, psi_host, out_host, U_dev, psi_dev, out_dev, M5, mf, dagger=False,

@@ -24,6 +24,7 @@
 namespace dwf {
 namespace {
 
+
 // a complex value on two slices: re = (Re_s0, Re_s1), im = (Im_s0, Im_s1)
 struct CP {
     float2 re, im;
@@ -109,25 +110,87 @@ __device__ __forceinline__ void pair_lower(int mu, float t, const CP (&u)[2][3],
     }
 }
 
-// Block: 32 sites x 4 slice pairs; blocks numbered pair group fastest.
+// One hop direction: accumulate the Wilson hop from the neighbour spinor v (both slices of the
+// pair) into the upper / lower spin-pair accumulators.  Forward hops multiply by U_mu(x), backward
+// ones by U_mu(x - mu)^dag; l0 indexes the link's first plane, ph is the boundary phase.
 template <class LT, bool DAG>
-__global__ void __launch_bounds__(128, 3) k_dwf4d_pair(const typename LT::store* __restrict__ U,
+__device__ __forceinline__ void pair_hop(int mu, bool fwd, float ph, const CP (&v)[4][3],
+                                         const typename LT::store* __restrict__ U, long long l0, CP (&up)[2][3],
+                                         CP (&lo)[2][3]) {
+    const bool minus = (fwd != DAG);
+    CP h[2][3];
+    pair_project(mu, minus ? -1.f : 1.f, v, h);
+    CP uh[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uh[a][c] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float2 u = lk_val(U, l0 + (long long)(fwd ? (c * 3 + b) : (b * 3 + c)) * 32);
+            const float ur = u.x, ui = fwd ? u.y : -u.y;
+            const float2 UR = make_float2(ur, ur), UI = make_float2(ui, ui), NUI = make_float2(-ui, -ui);
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                CP& acc = uh[a][c];
+                acc.re = __ffma2_rn(UR, h[a][b].re, acc.re);
+                acc.re = __ffma2_rn(NUI, h[a][b].im, acc.re);
+                acc.im = __ffma2_rn(UR, h[a][b].im, acc.im);
+                acc.im = __ffma2_rn(UI, h[a][b].re, acc.im);
+            }
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) up[a][c] = cp_fma_s(ph, uh[a][c], up[a][c]);
+    pair_lower(mu, minus ? -ph : ph, uh, lo);
+}
+
+// Output element e of the pair: diag psi + s-hop - 1/2 (Wilson hops).  sv: the site's own value on
+// both slices; q: the element of the neighbouring pair that holds this half's s-hop source
+// (jb = the pair below for a hop from s - 1, ja = the pair above for one from s + 1).
+template <bool DAG>
+__device__ __forceinline__ CP pair_out(int e, CP sv, CP q, CP acc, float fb, float fa, float diag) {
+    const bool below = (e < 6) != DAG;                // this half's hop comes from s - 1
+    CP hop;
+    if (below) hop = CP{make_float2(fb * q.re.y, sv.re.x), make_float2(fb * q.im.y, sv.im.x)};
+    else       hop = CP{make_float2(sv.re.y, fa * q.re.x), make_float2(sv.im.y, fa * q.im.x)};
+    CP r = cp_fma_s(-0.5f, acc, hop);
+    return cp_fma_s(diag, sv, r);
+}
+
+// neighbour of `site` in direction d = 2 mu + (0 forward, 1 backward); cross: the hop wraps
+// around the lattice boundary
+__device__ __forceinline__ int pair_nb(const Fine4dParams& p, int site, int d, bool& cross) {
+    const int mu = d >> 1;
+    int st = 1;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (m < mu) st *= p.L[m];
+    const int L = p.L[mu];
+    const int c = (site / st) % L;
+    if ((d & 1) == 0) { cross = c == L - 1; return cross ? site - (L - 1) * st : site + st; }
+    cross = c == 0;
+    return cross ? site + (L - 1) * st : site - st;
+}
+
+constexpr int PAIR_THREADS = 128;           // 32 sites x 4 slice pairs
+
+// Block: 32 sites x 4 slice pairs; blocks numbered pair group fastest, so the blocks running at
+// one time cover a compact stretch of the lattice and the neighbour loads of one block find the
+// other blocks' spinors in L2.  128 registers give four blocks (16 warps) per SM; the neighbour
+// spinors of one direction are loaded together, and their latency is hidden across warps.
+template <class LT, bool DAG>
+__global__ void __launch_bounds__(PAIR_THREADS, 4) k_dwf4d_pair(const typename LT::store* __restrict__ U,
                                                        const float4* __restrict__ psi, float4* __restrict__ out,
                                                        Fine4dParams p, LayP2 lay, int ngroups) {
     const int site = (int)(blockIdx.x / ngroups) * 32 + threadIdx.x;
     const int j = (int)(blockIdx.x % ngroups) * 4 + threadIdx.y;
     if (site >= p.V || j >= lay.NP) return;
-    int stride[4], coord[4];
-    {
-        int st = 1, rem = site;
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            stride[mu] = st;
-            coord[mu] = rem % p.L[mu];
-            rem /= p.L[mu];
-            st *= p.L[mu];
-        }
-    }
+    const int jb = j > 0 ? j - 1 : lay.NP - 1;        // pair holding slice 2j - 1 (or the wall Ls - 1)
+    const int ja = j + 1 < lay.NP ? j + 1 : 0;        // pair holding slice 2j + 2 (or the wall 0)
     CP up[2][3], lo[2][3];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -137,84 +200,30 @@ __global__ void __launch_bounds__(128, 3) k_dwf4d_pair(const typename LT::store*
             lo[a][c] = up[a][c];
         }
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        const int L = p.L[mu];
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        bool cross;
+        const int nb = pair_nb(p, site, d, cross);
+        CP v[4][3];
 #pragma unroll
-        for (int dirn = 0; dirn < 2; ++dirn) {
-            const bool fwd = dirn == 0;
-            const bool cross = fwd ? (coord[mu] == L - 1) : (coord[mu] == 0);
-            const int nb = fwd ? (cross ? site - (L - 1) * stride[mu] : site + stride[mu])
-                               : (cross ? site + (L - 1) * stride[mu] : site - stride[mu]);
-            const float ph = (cross && p.anti[mu]) ? -1.f : 1.f;
-            const bool minus = (fwd != DAG);
-            CP v[4][3];
-#pragma unroll
-            for (int e = 0; e < 12; ++e) v[e / 3][e % 3] = ld_cp(psi, lay.idx(j, nb, e));
-            CP h[2][3];
-            pair_project(mu, minus ? -1.f : 1.f, v, h);
-            // colour multiply: forward U h, backward U^dag h; one link load per pair of slices
-            const long long l0 = lay.lk(mu, fwd ? site : nb);
-            CP uh[2][3];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) uh[a][c] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float2 u = lk_val(U, l0 + (long long)(fwd ? (c * 3 + b) : (b * 3 + c)) * 32);
-                    const float ur = u.x, ui = fwd ? u.y : -u.y;
-                    const float2 UR = make_float2(ur, ur), UI = make_float2(ui, ui), NUI = make_float2(-ui, -ui);
-#pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        CP& acc = uh[a][c];
-                        acc.re = __ffma2_rn(UR, h[a][b].re, acc.re);
-                        acc.re = __ffma2_rn(NUI, h[a][b].im, acc.re);
-                        acc.im = __ffma2_rn(UR, h[a][b].im, acc.im);
-                        acc.im = __ffma2_rn(UI, h[a][b].re, acc.im);
-                    }
-                }
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) up[a][c] = cp_fma_s(ph, uh[a][c], up[a][c]);
-            pair_lower(mu, minus ? -ph : ph, uh, lo);
-        }
+        for (int e = 0; e < 12; ++e) v[e / 3][e % 3] = ld_cp(psi, lay.idx(j, nb, e));
+        const float ph = (cross && p.anti[mu]) ? -1.f : 1.f;
+        pair_hop<LT, DAG>(mu, fwd, ph, v, U, lay.lk(mu, fwd ? site : nb), up, lo);
     }
-    // the site itself on both slices, and the s-hops
-    CP self[4][3];
-#pragma unroll
-    for (int e = 0; e < 12; ++e) self[e / 3][e % 3] = ld_cp(psi, lay.idx(j, site, e));
-    // D: upper pair from s - 1 (s = 0: -mf psi_{Ls-1}), lower pair from s + 1 (s = Ls-1: -mf psi_0);
-    // D^dag: the mirror.  For the pair (2j, 2j+1): "from below" gives (psi_{2j-1}, psi_{2j}),
-    // "from above" gives (psi_{2j+1}, psi_{2j+2}).
     const float mf = p.mf_f;
-    const int jb = j > 0 ? j - 1 : lay.NP - 1;        // pair holding slice 2j - 1 (or the wall Ls - 1)
-    const int ja = j + 1 < lay.NP ? j + 1 : 0;        // pair holding slice 2j + 2 (or the wall 0)
     const float fb = j > 0 ? 1.f : -mf, fa = j + 1 < lay.NP ? 1.f : -mf;
-    const float diag = p.diag_f;
-    float4* o = out;
+    CP self[12];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {            // half 0: spins 0, 1 (P_+); half 1: spins 2, 3 (P_-)
-        const bool below = (half == 0) != DAG;        // this half's hop comes from s - 1
+    for (int e = 0; e < 12; ++e) self[e] = ld_cp(psi, lay.idx(j, site, e));
 #pragma unroll
-        for (int e6 = 0; e6 < 6; ++e6) {
-            const int e = half * 6 + e6;
-            const CP sv = self[e / 3][e % 3];
-            CP hop;
-            if (below) {
-                const CP q = ld_cp(psi, lay.idx(jb, site, e));       // (psi_{2j-2}, psi_{2j-1}) of pair jb
-                hop = CP{make_float2(fb * q.re.y, sv.re.x), make_float2(fb * q.im.y, sv.im.x)};
-            } else {
-                const CP q = ld_cp(psi, lay.idx(ja, site, e));       // (psi_{2j+2}, psi_{2j+3}) of pair ja
-                hop = CP{make_float2(sv.re.y, fa * q.re.x), make_float2(sv.im.y, fa * q.im.x)};
-            }
-            const CP acc = half == 0 ? up[e6 / 3][e6 % 3] : lo[e6 / 3][e6 % 3];
-            CP r = cp_fma_s(-0.5f, acc, hop);
-            r = cp_fma_s(diag, sv, r);
-            __stcs(o + lay.idx(j, site, e), make_float4(r.re.x, r.re.y, r.im.x, r.im.y));
-        }
+    for (int e = 0; e < 12; ++e) {
+        const CP sv = self[e];
+        const CP q = ld_cp(psi, lay.idx(((e < 6) != DAG) ? jb : ja, site, e));
+        const int e6 = e % 6;
+        const CP acc = e < 6 ? up[e6 / 3][e6 % 3] : lo[e6 / 3][e6 % 3];
+        const CP r = pair_out<DAG>(e, sv, q, acc, fb, fa, p.diag_f);
+        __stcs(out + lay.idx(j, site, e), make_float4(r.re.x, r.re.y, r.im.x, r.im.y));
     }
 }
 

@@ -63,6 +63,16 @@ def test_batched_apply_equals_single_applies_on_the_64_source_workload(dw):
         single = torch.empty_like(p)
         dw.dwf_apply(g, U, p, single, M5, mf, prec="f32_l16")
         assert torch.equal(single, o)
+    # the prepared form (argument arrays built once), applied twice and with the adjoint
+    plan = dw.BatchedApply(geoms, Us, psis, outs, prec="f32_l16")
+    for o in outs:
+        o.fill_(float("nan"))
+    for dag in (False, True, False):
+        plan(M5, mf, dagger=dag)
+    for g, U, p, o in zip(geoms, Us, psis, outs):
+        single = torch.empty_like(p)
+        dw.dwf_apply(g, U, p, single, M5, mf, prec="f32_l16")
+        assert torch.equal(single, o)
 
 
 def test_batched_apply_rejects_bad_input(dw):
