@@ -176,10 +176,13 @@ DWF_API dwf_status dwf_pv_poly_apply(const dwf_geom* g, const void* U, const voi
  * site indices (NB = ceil(V / 32) blocks; sites past V pad the last block) and
  * slices in pairs (2j, 2j+1).  For pair j, block b and complex element k of a
  * site (spin-major, colour fastest, k < 12) a plane of 32 float4 holds, for
- * site 32 b + i, (Re psi_2j[k], Re psi_2j+1[k], Im psi_2j[k], Im psi_2j+1[k]) at
+ * site 32 b + i, (Re psi_2j[k], Im psi_2j[k], Re psi_2j+1[k], Im psi_2j+1[k]) at
  * float4 index ((j NB + b) 12 + k) 32 + i: every real operation of the hop
  * then runs as one packed FP32 instruction over the two slices, and a warp
- * reads each element of 32 neighbour spinors as one contiguous run.  A link
+ * reads each element of 32 neighbour spinors as one contiguous run.  Complex
+ * values stay (re, im) pairs, so a packed spinor is a permutation of the complex
+ * values of the canonical one (plus zero padding) and complex BLAS (dwf_dot)
+ * applies to it unchanged.  A link
  * block holds nine planes of 32 entries: entry e = 3 row + column of
  * U_mu(site) at ((mu NB + site / 32) 9 + e) 32 + site % 32, in the storage of
  * `prec` (complex64, half pairs or bfloat16 pairs).  4-d lattices with even Ls
@@ -349,6 +352,10 @@ typedef struct {
     int transfer;         /* 0 (default): the truncated wall transfer of Eq. TruncProjectInterpolate;
                              1: the bulk transfer the paper compares it with (Sec. 4.1), P^dag /
                              P on every slice, which needs Ls_c = Ls                           */
+    int fine_layout;      /* layout of the FP32 fine vectors inside the K-cycle: 0 (default) = the
+                             slice-paired packed layout (dwf_pack_spinor) wherever it applies
+                             (4-d, even Ls, V a multiple of 32), canonical elsewhere; 1 =
+                             canonical always.  The caller's b and x are canonical either way. */
 } dwf_mg_params;
 
 typedef struct dwf_mg dwf_mg;

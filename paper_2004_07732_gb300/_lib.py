@@ -52,7 +52,7 @@ class MgParams(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_restarts", ctypes.c_int),
                 ("coarse_persistent", ctypes.c_int), ("coarse_solver", ctypes.c_int),
                 ("coarse_restart", ctypes.c_int), ("coarse_block_prec", ctypes.c_int), ("cgs_passes", ctypes.c_int),
-                ("coarse_tc", ctypes.c_int), ("transfer", ctypes.c_int)]
+                ("coarse_tc", ctypes.c_int), ("transfer", ctypes.c_int), ("fine_layout", ctypes.c_int)]
 
 
 class LevelParams(ctypes.Structure):

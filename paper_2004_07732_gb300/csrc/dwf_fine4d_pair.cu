@@ -11,9 +11,12 @@
 // Layout (FP32 spinors; Ls even): sites in blocks of 32 (NB = ceil(V / 32)), slice
 // pairs j = 0 .. Ls/2 - 1.  For pair j, block b, complex element k (spin-major,
 // colour fastest, 12 per site) a plane of 32 float4 holds, for site 32 b + i,
-//   (Re psi_{2j}[k], Re psi_{2j+1}[k], Im psi_{2j}[k], Im psi_{2j+1}[k])
+//   (Re psi_{2j}[k], Im psi_{2j}[k], Re psi_{2j+1}[k], Im psi_{2j+1}[k])
 // at float4 index ((j NB + b) 12 + k) 32 + i.  A warp reads each element of 32
-// sites' spinors as one contiguous 512-byte run.  Links: nine planes of 32
+// sites' spinors as one contiguous 512-byte run.  Each complex value stays a
+// (re, im) pair in memory, so complex BLAS runs on packed vectors unchanged (the
+// layout only permutes complex elements); the kernel regroups a loaded float4 into
+// the (slice 2j, slice 2j+1) pairs of its real and imaginary parts.  Links: nine planes of 32
 // entries per (mu, block), entry 3 a + b of U_mu(32 b + i) at ((mu NB + b) 9 + e) 32 + i.
 // Padding sites (V not a multiple of 32) are zero and are not written by the apply.
 #include <algorithm>
@@ -50,7 +53,7 @@ struct LayP2 {
 
 __device__ __forceinline__ CP ld_cp(const float4* p, long long i) {
     const float4 a = __ldg(p + i);
-    return CP{make_float2(a.x, a.y), make_float2(a.z, a.w)};
+    return CP{make_float2(a.x, a.z), make_float2(a.y, a.w)};
 }
 
 // one link entry, as FP32 (re, im)
@@ -185,7 +188,8 @@ constexpr int PAIR_THREADS = 128;           // 32 sites x 4 slice pairs
 template <class LT, bool DAG>
 __global__ void __launch_bounds__(PAIR_THREADS, 4) k_dwf4d_pair(const typename LT::store* __restrict__ U,
                                                        const float4* __restrict__ psi, float4* __restrict__ out,
-                                                       Fine4dParams p, LayP2 lay, int ngroups) {
+                                                       Fine4dParams p, LayP2 lay, int ngroups, const int* skip) {
+    if (skip && *skip) return;
     const int site = (int)(blockIdx.x / ngroups) * 32 + threadIdx.x;
     const int j = (int)(blockIdx.x % ngroups) * 4 + threadIdx.y;
     if (site >= p.V || j >= lay.NP) return;
@@ -223,20 +227,20 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4) k_dwf4d_pair(const typename L
         const int e6 = e % 6;
         const CP acc = e < 6 ? up[e6 / 3][e6 % 3] : lo[e6 / 3][e6 % 3];
         const CP r = pair_out<DAG>(e, sv, q, acc, fb, fa, p.diag_f);
-        __stcs(out + lay.idx(j, site, e), make_float4(r.re.x, r.re.y, r.im.x, r.im.y));
+        __stcs(out + lay.idx(j, site, e), make_float4(r.re.x, r.im.x, r.re.y, r.im.y));
     }
 }
 
 template <class LT>
 dwf_status launch_pair(const void* U, const void* psi, void* out, const Fine4dParams& p, const LayP2& lay, bool dagger,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int* skip) {
     const long long ng = (lay.NP + 3) / 4;
     const long long blocks = lay.NB * ng;
     if (blocks > 0x7fffffffLL) { set_error("4-d lattice too large for one launch"); return DWF_ERR_ARG; }
     dim3 block(32, 4);
     auto Ut = reinterpret_cast<const typename LT::store*>(U);
-    if (dagger) k_dwf4d_pair<LT, true><<<(unsigned)blocks, block, 0, st>>>(Ut, (const float4*)psi, (float4*)out, p, lay, (int)ng);
-    else        k_dwf4d_pair<LT, false><<<(unsigned)blocks, block, 0, st>>>(Ut, (const float4*)psi, (float4*)out, p, lay, (int)ng);
+    if (dagger) k_dwf4d_pair<LT, true><<<(unsigned)blocks, block, 0, st>>>(Ut, (const float4*)psi, (float4*)out, p, lay, (int)ng, skip);
+    else        k_dwf4d_pair<LT, false><<<(unsigned)blocks, block, 0, st>>>(Ut, (const float4*)psi, (float4*)out, p, lay, (int)ng, skip);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }
@@ -255,7 +259,7 @@ __global__ void k_pack_pair(const float2* __restrict__ in, float4* __restrict__ 
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (site < V) {
             const float2 a = in[((2 * j) * V + site) * 12 + k], c = in[((2 * j + 1) * V + site) * 12 + k];
-            v = make_float4(a.x, c.x, a.y, c.y);
+            v = make_float4(a.x, a.y, c.x, c.y);
         }
         out[t] = v;
     }
@@ -269,8 +273,8 @@ __global__ void k_unpack_pair(const float4* __restrict__ in, float2* __restrict_
         const long long r = t / 12;
         const long long site = r % V, j = r / V;
         const float4 v = in[((j * NB + (site >> 5)) * 12 + k) * 32 + (site & 31)];
-        out[((2 * j) * V + site) * 12 + k] = make_float2(v.x, v.z);
-        out[((2 * j + 1) * V + site) * 12 + k] = make_float2(v.y, v.w);
+        out[((2 * j) * V + site) * 12 + k] = make_float2(v.x, v.y);
+        out[((2 * j + 1) * V + site) * 12 + k] = make_float2(v.z, v.w);
     }
 }
 
@@ -279,7 +283,7 @@ int pair_grid(long long n) { return (int)std::min<long long>((n + 255) / 256, 15
 }  // namespace
 
 dwf_status fine_apply_4d_paired(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
-                                bool dagger, int prec, cudaStream_t st) {
+                                bool dagger, int prec, cudaStream_t st, const int* skip) {
     if (g.Ls % 2) { set_error("the slice-paired layout needs an even Ls (got %d)", g.Ls); return DWF_ERR_UNSUPPORTED; }
     if (g.V > (1LL << 28)) { set_error("4-d lattices are limited to 2^28 sites"); return DWF_ERR_UNSUPPORTED; }
     Fine4dParams p;
@@ -293,9 +297,9 @@ dwf_status fine_apply_4d_paired(const Geom& g, const void* U, const void* psi, v
     p.s_chunk = 0;
     LayP2 lay{(g.V + 31) / 32, g.Ls / 2};
     switch (prec) {
-        case DWF_F32:       return launch_pair<LinkF32>(U, psi, out, p, lay, dagger, st);
-        case DWF_F32_L16:   return launch_pair<LinkH16>(U, psi, out, p, lay, dagger, st);
-        case DWF_F32_LBF16: return launch_pair<LinkBF16>(U, psi, out, p, lay, dagger, st);
+        case DWF_F32:       return launch_pair<LinkF32>(U, psi, out, p, lay, dagger, st, skip);
+        case DWF_F32_L16:   return launch_pair<LinkH16>(U, psi, out, p, lay, dagger, st, skip);
+        case DWF_F32_LBF16: return launch_pair<LinkBF16>(U, psi, out, p, lay, dagger, st, skip);
         default: set_error("the packed layout takes FP32 spinors (precision %d)", prec); return DWF_ERR_ARG;
     }
 }

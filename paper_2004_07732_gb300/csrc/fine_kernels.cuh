@@ -65,8 +65,9 @@ dwf_status fine_apply_4d(const Geom& g, const void* U, const void* psi, void* ou
                          bool dagger, int prec, int s_chunk, cudaStream_t st, const int* skip = nullptr);
 
 // the 4-d operator on the slice-paired packed layout (FP32 spinors, even Ls; dwf_fine4d_pair.cu)
+// (skip: optional device flag; nonzero leaves out untouched)
 dwf_status fine_apply_4d_paired(const Geom& g, const void* U, const void* psi, void* out, double M5, double mf,
-                                bool dagger, int prec, cudaStream_t st);
+                                bool dagger, int prec, cudaStream_t st, const int* skip = nullptr);
 dwf_status pack_spinor_paired(const Geom& g, const void* psi, void* packed, cudaStream_t st);
 dwf_status unpack_spinor_paired(const Geom& g, const void* packed, void* psi, cudaStream_t st);
 

@@ -78,6 +78,8 @@ struct dwf_mg {
     // device buffers (owned)
     void* U64;            // complex128 links
     void* Ulo;            // fine links in prm.fine_prec storage
+    void* Upk;            // the same links in the slice-paired layout (when pk), else nullptr
+    int pk;               // 1: the K-cycle keeps its FP32 fine vectors in the slice-paired layout
     double2* nullv;       // relaxed near-null vectors [vec][site][spin][color]
     double2* P64;         // prolongator [site][chir][l][k]
     float2* P32;
@@ -128,11 +130,12 @@ dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* o
 // one-time kernel attributes of the coarse stencil (outside any stream capture)
 dwf_status coarse_init_attributes();
 // Wall transfers (Eq. TruncProjectInterpolate) on nrhs vectors stored back to
-// back; skip: per right-hand-side device flags (may be null).
+// back; skip: per right-hand-side device flags (may be null).  packed: the fine
+// vectors are in the slice-paired 4-d layout (dwf_pack_spinor, V a multiple of 32).
 dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st,
-                         int nrhs = 1);
+                         int nrhs = 1, bool packed = false);
 dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st,
-                        int nrhs = 1);
+                        int nrhs = 1, bool packed = false);
 
 // One cooperative launch running the whole coarsest CGNR; vec6 = six coarse
 // work vectors, partials = 3 * grid doubles, bar = 16 bytes of barrier state.

@@ -116,6 +116,37 @@ __global__ void k_bd2f_scale(float2* __restrict__ out, const double2* __restrict
     ROW_LOOP(i, n) { const double2 u = a[i]; out[i] = make_float2((float)(u.x * s), (float)(u.y * s)); }
 }
 
+// Slice-paired packed FP32 fine vectors (4-d, one right-hand side): packed float4 i holds
+// element d of site x on slices 2j and 2j+1; pk_canon gives the canonical complex index of the
+// slice-2j value (the slice-2j+1 value is V dof further).
+struct PackIdx {
+    long long V, NB;
+    int dof;
+};
+__device__ __forceinline__ long long pk_canon(const PackIdx& q, long long i) {
+    const int lane = (int)(i & 31);
+    const long long t = i >> 5;
+    const int d = (int)(t % q.dof);
+    const long long t2 = t / q.dof;
+    const long long x = (t2 % q.NB) * 32 + lane;
+    const long long j = t2 / q.NB;
+    return ((2 * j) * q.V + x) * q.dof + d;
+}
+
+// out (packed FP32) = scale * a (canonical FP64)
+__global__ void k_bd2f_scale_pk(float2* __restrict__ out, const double2* __restrict__ a, const double* scale,
+                                long long n, const int* skip, PackIdx q) {
+    if (skip && skip[0]) return;
+    const double s = scale[0];
+    float4* o = reinterpret_cast<float4*>(out);
+    const long long sv = q.V * q.dof;
+    ROW_LOOP(i, n >> 1) {
+        const long long c = pk_canon(q, i);
+        const double2 u = a[c], w = a[c + sv];
+        o[i] = make_float4((float)(u.x * s), (float)(u.y * s), (float)(w.x * s), (float)(w.y * s));
+    }
+}
+
 // out[r] = |x_r|^2.  FP64 data: every product in FP64; FP32 data: per-thread
 // FP32 partials over a few elements, FP64 across threads.
 __global__ void __launch_bounds__(RED_THREADS) k_bnorm2_64(const double2* __restrict__ x, long long n, RedScratch rs,
@@ -404,6 +435,29 @@ __global__ void __launch_bounds__(RED_THREADS) k_bcombine64(double2* __restrict_
     }
 }
 
+// k_bcombine64 with the basis in the packed layout and X canonical (one right-hand side)
+__global__ void __launch_bounds__(RED_THREADS) k_bcombine64_pk(double2* __restrict__ X, float2* const* __restrict__ Z,
+                                                               const BGcr* g, const int* nsteps, const double* s,
+                                                               long long n, PackIdx q) {
+    const int m = nsteps[0];
+    if (m <= 0) return;
+    __shared__ float2 y[BK_MAX];
+    __shared__ const float4* Zp[BK_MAX];
+    if (threadIdx.x == 0) back_substitute(g[0], m, y);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) Zp[j] = reinterpret_cast<const float4*>(Z[j]);
+    __syncthreads();
+    const double sc = s[0];
+    const long long sv = q.V * q.dof;
+    ROW_LOOP(i, n >> 1) {
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < m; ++j) cadd4(e, Zp[j][i], y[j]);
+        const long long c = pk_canon(q, i);
+        double2 a = X[c], b = X[c + sv];
+        a.x += sc * e.x; a.y += sc * e.y; b.x += sc * e.z; b.y += sc * e.w;
+        X[c] = a; X[c + sv] = b;
+    }
+}
+
 // --------------------------------------------------------------------------
 // workspace: one arena per handle, sized for `cap` right-hand sides
 // --------------------------------------------------------------------------
@@ -563,6 +617,7 @@ struct BSolver {
     BView* v;
     cudaStream_t st;
     int nrhs;
+    bool pk = false;             // FP32 fine vectors in the slice-paired layout (4-d, one right-hand side)
     long long l3_iters = 0;      // coarsest iterations of a three-level hierarchy
     long long l3_solves = 0;     // and coarsest solves
 };
@@ -576,6 +631,10 @@ static dim3 row_grid(long long n2, int nrhs, int cap = 1216) {
 
 static dwf_status bapply_A(BSolver& s, const float2* in, float2* out, const int* skip) {
     dwf_mg* h = s.h;
+    if (s.pk) {
+        DWF_TRY(fine_apply_4d_paired(h->G, h->Upk, in, s.v->tmp, h->M5, h->mf, false, h->prm.fine_prec, s.st, skip));
+        return fine_apply_4d_paired(h->G, h->Upk, s.v->tmp, out, h->M5, 1.0, true, h->prm.fine_prec, s.st, skip);
+    }
     DWF_TRY(fine_apply_rhs(h->G, h->Ulo, in, s.v->tmp, h->M5, h->mf, false, h->prm.fine_prec, s.nrhs, skip, s.st));
     DWF_TRY(fine_apply_rhs(h->G, h->Ulo, s.v->tmp, out, h->M5, 1.0, true, h->prm.fine_prec, s.nrhs, skip, s.st));
     return DWF_OK;
@@ -733,7 +792,7 @@ static dwf_status bprecondition(BSolver& s, const float2* res, float2* zout, flo
     BView& v = *s.v;
     const long long n = v.nf;
     const dim3 eg = row_grid(n >> 1, s.nrhs);
-    DWF_TRY(restrict_wall(h, res, v.rc, v.idone, s.st, s.nrhs));
+    DWF_TRY(restrict_wall(h, res, v.rc, v.idone, s.st, s.nrhs, s.pk));
     if (h->lvl3) {
         // three levels: flexible GCR on the intermediate level, preconditioned by the coarsest solve
         int l2 = 0, l3 = 0;
@@ -744,7 +803,7 @@ static dwf_status bprecondition(BSolver& s, const float2* res, float2* zout, flo
     } else {
         DWF_TRY(bcoarse_solve(s, citers_out));
     }
-    DWF_TRY(prolong_wall(h, v.ec, zout, v.idone, s.st, s.nrhs));
+    DWF_TRY(prolong_wall(h, v.ec, zout, v.idone, s.st, s.nrhs, s.pk));
     const int S = h->prm.post_smooth;
     if (S == 0) return bapply_A(s, zout, wout, v.idone);
     DWF_TRY(bapply_A(s, zout, v.ps, v.idone));
@@ -799,6 +858,8 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
     s.v = &s.bs->v;
     s.st = h->st;
     s.nrhs = nrhs;
+    s.pk = h->pk != 0 && nrhs == 1;
+    const PackIdx pq{h->G.V, (h->G.V + 31) / 32, (int)site_dof(h->G)};
     BView& v = *s.v;
     BatchedState& bs = *s.bs;
     const long long n = v.nf;
@@ -869,9 +930,15 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
         DWF_CHECK_CUDA(cudaMemcpyAsync(v.scale, hscale, nrhs * sizeof(double), cudaMemcpyHostToDevice, s.st));
         DWF_CHECK_CUDA(cudaMemcpyAsync(v.rn, hrn, nrhs * sizeof(double), cudaMemcpyHostToDevice, s.st));
         // correction system in FP32: A e = D_PV^dag r / |r|
-        k_bd2f_scale<<<eg64, 256, 0, s.st>>>(v.ps, v.r64, v.scale, n, v.idone);
-        DWF_CHECK_LAUNCH();
-        DWF_TRY(fine_apply_rhs(h->G, h->Ulo, v.ps, v.rA, h->M5, 1.0, true, h->prm.fine_prec, nrhs, v.idone, s.st));
+        if (s.pk) {
+            k_bd2f_scale_pk<<<eg32, 256, 0, s.st>>>(v.ps, v.r64, v.scale, n, v.idone, pq);
+            DWF_CHECK_LAUNCH();
+            DWF_TRY(fine_apply_4d_paired(h->G, h->Upk, v.ps, v.rA, h->M5, 1.0, true, h->prm.fine_prec, s.st, v.idone));
+        } else {
+            k_bd2f_scale<<<eg64, 256, 0, s.st>>>(v.ps, v.r64, v.scale, n, v.idone);
+            DWF_CHECK_LAUNCH();
+            DWF_TRY(fine_apply_rhs(h->G, h->Ulo, v.ps, v.rA, h->M5, 1.0, true, h->prm.fine_prec, nrhs, v.idone, s.st));
+        }
         k_bcopy<<<eg32, 256, 0, s.st>>>(v.r, v.rA, n, v.idone);
         k_bnorm2_32<<<rg32, RED_THREADS, 0, s.st>>>(v.rA, n, v.red, v.rA2, v.idone);
         DWF_CHECK_LAUNCH();
@@ -905,8 +972,12 @@ dwf_status mg_solve_batched_impl(dwf_mg* h, int nrhs, const double2* B, double2*
             DWF_CHECK_CUDA(cudaMemcpyAsync(v.idone, hid, nrhs * sizeof(int), cudaMemcpyHostToDevice, s.st));
         }
         // x += |r| sum_k y_k Z_k over the iters[r] steps of this cycle
-        k_bcombine64<<<row_grid(n >> 1, nrhs), RED_THREADS, 0, s.st>>>(X, v.dptr + 0 * BK_MAX, v.outer, v.iters, v.rn,
-                                                                        n);
+        if (s.pk)
+            k_bcombine64_pk<<<row_grid(n >> 1, 1), RED_THREADS, 0, s.st>>>(X, v.dptr + 0 * BK_MAX, v.outer, v.iters,
+                                                                            v.rn, n, pq);
+        else
+            k_bcombine64<<<row_grid(n >> 1, nrhs), RED_THREADS, 0, s.st>>>(X, v.dptr + 0 * BK_MAX, v.outer, v.iters,
+                                                                            v.rn, n);
         DWF_CHECK_LAUNCH();
     }
     (void)hit;

@@ -650,7 +650,16 @@ struct TransferParams {
     long long V, Vc;
     int Ls, Ls_c, nvec, ncd, nchd, dof, ncol, nb;
     int bulk;            // 1: P^dag / P on every slice (Lhat_s = Ls) instead of the walls
+    int packed;          // 1: fine vectors in the slice-paired 4-d layout
+    long long NB;        // blocks of 32 sites of the packed layout
 };
+
+// complex index of fine element (s, site, d) in the canonical or the slice-paired layout
+// (float4 ((s/2 NB + site/32) dof + d) 32 + site%32 holds slices 2j and 2j+1 as two complex values)
+__device__ __forceinline__ long long fine_idx(const TransferParams& p, int s, long long x, int d) {
+    if (!p.packed) return ((long long)s * p.V + x) * p.dof + d;
+    return 2 * (((((long long)(s >> 1)) * p.NB + (x >> 5)) * p.dof + d) * 32 + (x & 31)) + (s & 1);
+}
 
 __device__ __forceinline__ long long agg_of(const TransferParams& p, long long site) {
     long long xc = 0, stride = 1;
@@ -704,11 +713,11 @@ __global__ void k_restrict(const float2* __restrict__ P, const float2* __restric
     if (c == 0 && s == p.Ls_c - 1) sf = p.Ls - 1; // Phat_+ P^dag P_+ r_Ls on coarse slice Lhat_s
     if (p.bulk) sf = s;                           // bulk: every slice
     if (sf >= 0) {
-        const float2* rs = r + (long long)sf * p.V * p.dof;
         for (int l = 0; l < p.nb; ++l) {
             const long long x = agg_site(p, xc, l);
             for (int cd = 0; cd < p.nchd; ++cd)
-                acc = cfma_conj(P[((x * 2 + c) * p.nchd + cd) * p.nvec + k], rs[x * p.dof + chir_dof(p, c, cd)], acc);
+                acc = cfma_conj(P[((x * 2 + c) * p.nchd + cd) * p.nvec + k], r[fine_idx(p, sf, x, chir_dof(p, c, cd))],
+                                acc);
         }
     }
     out[t] = acc;
@@ -722,10 +731,24 @@ __global__ void k_prolong(const float2* __restrict__ P, const float2* __restrict
     if (t >= total) return;
     e += (long long)blockIdx.y * p.Vc * p.Ls_c * p.ncd;
     out += (long long)blockIdx.y * total;
-    const int d = (int)(t % p.dof);
-    const long long rest = t / p.dof;
-    const long long x = rest % p.V;
-    const int s = (int)(rest / p.V);
+    // thread t writes element t of the output layout: (s, site, d) from the canonical or packed order
+    int d, s;
+    long long x;
+    if (!p.packed) {
+        d = (int)(t % p.dof);
+        const long long rest = t / p.dof;
+        x = rest % p.V;
+        s = (int)(rest / p.V);
+    } else {
+        const int s1 = (int)(t & 1);
+        const long long q = t >> 1;
+        const int i = (int)(q & 31);
+        const long long q2 = q >> 5;
+        d = (int)(q2 % p.dof);
+        const long long q3 = q2 / p.dof;
+        x = (q3 % p.NB) * 32 + i;
+        s = (int)(q3 / p.NB) * 2 + s1;
+    }
     int c, cd;
     if (p.nd == 2) { c = d; cd = 0; }
     else { const int spin = d / p.ncol; c = spin / 2; cd = (spin % 2) * p.ncol + d % p.ncol; }
@@ -758,12 +781,23 @@ static TransferParams transfer_params(const dwf_mg* h) {
     p.ncol = h->G.ncol;
     p.nb = h->mg.nb;
     p.bulk = h->prm.transfer == 1 ? 1 : 0;
+    p.packed = 0;
+    p.NB = (p.V + 31) / 32;
     return p;
 }
 
+static dwf_status check_packed_transfer(const TransferParams& p) {
+    if (p.nd != 4 || p.Ls % 2 || p.V % 32) {
+        set_error("packed transfers need a 4-d lattice, even Ls and a multiple of 32 sites");
+        return DWF_ERR_UNSUPPORTED;
+    }
+    return DWF_OK;
+}
+
 dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse, const int* skip, cudaStream_t st,
-                         int nrhs) {
+                         int nrhs, bool packed) {
     TransferParams p = transfer_params(h);
+    if (packed) { DWF_TRY(check_packed_transfer(p)); p.packed = 1; }
     const long long total = p.Vc * p.Ls_c * p.ncd;
     if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
     k_restrict<<<dim3((unsigned)((total + 255) / 256), (unsigned)nrhs), 256, 0, st>>>(h->P32, r_fine, r_coarse, p,
@@ -773,8 +807,9 @@ dwf_status restrict_wall(const dwf_mg* h, const float2* r_fine, float2* r_coarse
 }
 
 dwf_status prolong_wall(const dwf_mg* h, const float2* e_coarse, float2* e_fine, const int* skip, cudaStream_t st,
-                        int nrhs) {
+                        int nrhs, bool packed) {
     TransferParams p = transfer_params(h);
+    if (packed) { DWF_TRY(check_packed_transfer(p)); p.packed = 1; }
     const long long total = p.V * p.Ls * p.dof;
     if (nrhs < 1 || nrhs > 65535) { set_error("nrhs must be in [1, 65535]"); return DWF_ERR_ARG; }
     k_prolong<<<dim3((unsigned)((total + 255) / 256), (unsigned)nrhs), 256, 0, st>>>(h->P32, e_coarse, e_fine, p,

@@ -493,6 +493,12 @@ static dwf_status setup_impl(dwf_mg* h, const void* U, const void* starts) {
         g.nd = G.nd; g.Ls = G.Ls; g.group = G.group;
         for (int mu = 0; mu < 4; ++mu) { g.L[mu] = G.L[mu]; g.antiperiodic[mu] = G.anti[mu]; }
         DWF_TRY(dwf_convert_links(&g, h->U64, h->Ulo, h->prm.fine_prec, st));
+        // the K-cycle's FP32 fine vectors in the slice-paired layout: links packed once
+        h->pk = h->prm.fine_layout == 0 && G.nd == 4 && G.Ls % 2 == 0 && G.V % 32 == 0;
+        if (h->pk) {
+            DWF_TRY(mg_alloc(h, &h->Upk, dwf_packed_link_size(&g) * lo_b));
+            DWF_TRY(dwf_pack_links(&g, h->U64, h->Upk, h->prm.fine_prec, st));
+        }
     }
     DWF_TRY(mg_alloc(h, (void**)&h->nullv, m.nvec * n1 * sizeof(double2)));
     DWF_CHECK_CUDA(cudaMemcpyAsync(h->nullv, starts, m.nvec * n1 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -613,6 +619,7 @@ void dwf_mg_default_params(dwf_mg_params* p) {
     p->cgs_passes = 1;
     p->coarse_tc = 0;
     p->transfer = 0;
+    p->fine_layout = 0;
 }
 
 dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, const dwf_mg_params* p,
@@ -636,6 +643,7 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
         set_error("coarse_block_prec must be DWF_F32 or DWF_F32_L16"); return DWF_ERR_ARG;
     }
     if (prm.transfer != 0 && prm.transfer != 1) { set_error("transfer must be 0 (walls) or 1 (bulk)"); return DWF_ERR_ARG; }
+    if (prm.fine_layout != 0 && prm.fine_layout != 1) { set_error("fine_layout must be 0 or 1"); return DWF_ERR_ARG; }
     if (prm.transfer == 1 && prm.Ls_c != G.Ls) {
         set_error("the bulk transfer keeps every slice: Ls_c must equal Ls (%d)", G.Ls); return DWF_ERR_ARG;
     }

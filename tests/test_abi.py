@@ -82,3 +82,27 @@ def test_packed_layout_sizes_and_checks(dw):
     assert L.dwf_pack_links(ctypes.byref(g4), fake, fake2, 0, None) == 1                        # F64 not packed
     assert L.dwf_pack_spinor(ctypes.byref(g4), fake, fake, None) == 1
     assert L.dwf_unpack_spinor(ctypes.byref(g2), fake, fake2, None) == 6
+
+
+def _struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/dwf.h (comments removed)."""
+    src = open(os.path.join(ROOT, "include", "dwf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            fields.append(re.sub(r"\[.*?\]", "", part).split()[-1].lstrip("*"))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("dwf_mg_params", "MgParams"), ("dwf_solve_stats", "SolveStats"),
+                                          ("dwf_mg_level_params", "LevelParams"), ("dwf_geom", "Geom")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    """The ctypes mirrors of the ABI structs list the header's fields in the header's order."""
+    import paper_2004_07732_gb300._lib as L
+    assert [f for f, _ in getattr(L, pyname)._fields_] == _struct_fields(cname)

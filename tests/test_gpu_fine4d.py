@@ -100,12 +100,12 @@ def test_dwf4d_adjoint_and_cgne(dw):
 def _packed_positions(dims, Ls):
     """Float offsets in the slice-paired packed layout of the real and imaginary parts of every
     (s, site, k) in canonical order: float4 ((s/2 NB + site/32) 12 + k) 32 + site%32 holds
-    (Re slice 2j, Re slice 2j+1, Im slice 2j, Im slice 2j+1)."""
+    (Re slice 2j, Im slice 2j, Re slice 2j+1, Im slice 2j+1)."""
     V = int(np.prod(dims))
     NB = (V + 31) // 32
     s, site, k = np.meshgrid(np.arange(Ls), np.arange(V), np.arange(12), indexing="ij")
     f4 = (((s // 2) * NB + site // 32) * 12 + k) * 32 + site % 32
-    return 4 * f4 + s % 2, 4 * f4 + 2 + s % 2, NB
+    return 4 * f4 + 2 * (s % 2), 4 * f4 + 2 * (s % 2) + 1, NB
 
 
 @pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 4), ((3, 5, 2, 3), 2), ((2, 2, 2, 2), 2), ((3, 5, 2, 3), 6)])
