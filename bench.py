@@ -613,11 +613,14 @@ def time_solves(dw, dev, args, wl=SOLVE_WL):
     if hasattr(dw, "mg_setup") and not args.skip_mg:
         res["mg"] = time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2)
         res["mg3_deflated"] = time_mg(dw, dev, wl, U64, b, g, t_cg, levels=3)
+        res["mg3_deflated_gcr"] = time_mg(dw, dev, wl, U64, b, g, t_cg, levels=3, coarsest_solver=1)
         res["mg_speedup_vs_cgne"] = res["mg"]["speedup_vs_cgne"]
     return res
 
 
-def time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2):
+def time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2, coarsest_solver=0):
+    """Two-level K-cycle (Table kcycle defaults), or three levels with 128 deflated coarsest
+    eigenvectors: coarsest_solver 0 = CGNR (the paper's), 1 = GCR(8)."""
     import torch
     params = dw.mg_default_params()
     params["setup_mass"] = SETUP_MASS[wl.sigma]
@@ -632,7 +635,8 @@ def time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2):
         lp = dw.mg_default_level_params()
         s2 = np.stack([synth.gaussian_complex(rng, (Vc * 16,)) for _ in range(lp["nvec"])])
         ls = synth.gaussian_complex(rng, ((Vc // 4) * lp["Ls_c"] * 2 * lp["nvec"],))
-        dw.mg_add_level(mg, {"setup_mass": SETUP_MASS[wl.sigma]}, torch.from_numpy(s2.reshape(-1)).to(dev),
+        dw.mg_add_level(mg, {"setup_mass": SETUP_MASS[wl.sigma], "coarsest_solver": coarsest_solver},
+                        torch.from_numpy(s2.reshape(-1)).to(dev),
                         torch.from_numpy(ls).to(dev))
     torch.cuda.synchronize(dev)
     t_setup = time.perf_counter() - t0
@@ -652,6 +656,7 @@ def time_mg(dw, dev, wl, U64, b, g, t_cg, levels=2):
     if levels == 3:
         out["coarsest_avg_iters"] = st["coarsest_avg_iters"]
         out["deflated_modes"] = 128
+        out["coarsest_solver"] = "GCR(8)" if coarsest_solver else "CGNR"
     return out
 
 
@@ -830,7 +835,8 @@ def time_coarse_multi(dw, dev, nrhs=64, reps=20):
     return {"workload": f"{wl.name} hierarchy (default FP16 blocks), coarse D_DW(m) on {nrhs} vectors",
             "nrhs": nrhs, "coarse_sites": Vc, "Ls_c": Ls_c, "useful_flops": flops, "algorithmic_bytes": nbytes,
             "autotuned_form": {1: "mma.sync, 1 tile/warp", 2: "mma.sync, 2 tiles/warp", 4: "mma.sync, 4 tiles/warp",
-                               256: "tcgen05"}.get(form, str(form)),
+                               256: "tcgen05, one item per CTA", 257: "tcgen05, persistent warp-specialised"}
+                               .get(form, str(form)),
             "tensor_core_ms": t_tc * 1e3, "tensor_core_TFLOPs": flops / t_tc / 1e12,
             "tensor_core_GBps": nbytes / t_tc / 1e9, "per_vector_launches_ms": t_one * 1e3,
             "speedup": t_one / t_tc}

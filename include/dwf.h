@@ -345,10 +345,12 @@ typedef struct {
     int coarse_tc;        /* form of the many-right-hand-side coarse contraction: 0 (default) =
                              autotuned -- the first use for a given nrhs times mma.sync with 1, 2
                              and 4 column tiles per warp and, with FP16 blocks and >= 128
-                             columns, tcgen05 with the accumulator in tensor memory, and keeps
-                             the fastest; 1 = tcgen05 wherever eligible (mma.sync with 4
-                             tiles elsewhere); 2, 3, 4 = mma.sync with 1, 2, 4 column tiles
-                             per warp (fixed forms, for testing each one)                     */
+                             columns, the two tcgen05 forms (accumulator in tensor memory), and
+                             keeps the fastest; 1 = the persistent warp-specialised tcgen05
+                             form wherever eligible (mma.sync with 4 tiles elsewhere); 2, 3, 4
+                             = mma.sync with 1, 2, 4 column tiles per warp; 5 = tcgen05 with
+                             one (site, column tile) per thread block (fixed forms, for testing
+                             each one)                                                         */
     int transfer;         /* 0 (default): the truncated wall transfer of Eq. TruncProjectInterpolate;
                              1: the bulk transfer the paper compares it with (Sec. 4.1), P^dag /
                              P on every slice, which needs Ls_c = Ls                           */

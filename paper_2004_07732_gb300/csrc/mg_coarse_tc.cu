@@ -12,6 +12,9 @@
 // Vectors: [rhs][s][coarse site][16] complex64; blocks: the FP32 column-major
 // Galerkin blocks.  With FP16 blocks, at least 128 columns and coarse_tc = 1
 // the contraction runs on tcgen05 instead (k_coarse_umma below).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "mg.cuh"
 #include "async_copy.cuh"
 #include "mma_tf32.cuh"
@@ -239,8 +242,9 @@ __device__ __forceinline__ void um_load_a(float4 (&v)[4], const float2* __restri
     }
 }
 
-// the held values as TF32 high and low parts in the operand layout of buffer `buf`
-__device__ __forceinline__ void um_store_a(UmSmem& sm, int buf, const float4 (&v)[4], const TcParams& p) {
+// the held values as TF32 high and low parts in the operand layout (hi, lo: one operand buffer each)
+__device__ __forceinline__ void um_store_ab(float* __restrict__ ahi, float* __restrict__ alo, const float4 (&v)[4],
+                                            const TcParams& p) {
     const int t = threadIdx.x, m = t >> 1, jh = t & 1;
     const float sg = (p.dag && jh == 1) ? -1.f : 1.f;       // sigma_3 on input components 8..15
     float re[8], im[8];
@@ -262,9 +266,24 @@ __device__ __forceinline__ void um_store_a(UmSmem& sm, int buf, const float4 (&v
                 lo[u] = x[4 * g + u] - hi[u];
             }
             const int o = um_off(m, k0 + 4 * g);
-            *reinterpret_cast<float4*>(&sm.a[buf][0][o]) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<float4*>(&sm.a[buf][1][o]) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<float4*>(&ahi[o]) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<float4*>(&alo[o]) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
+    }
+}
+
+// weights of the five directions: B_d[n][k] (real form of the FP16 block Y[xc][d], column-major
+// j * 16 + i), written by threads t0 of nt
+__device__ __forceinline__ void um_build_b(float (*b)[UM_N * UM_K], const __half2* __restrict__ Y, long long xc, int t0,
+                                           int nt) {
+    for (int e = t0; e < UM_DIRS * 256; e += nt) {
+        const int d = e >> 8, j = (e >> 4) & 15, i = e & 15;
+        const float2 y = __half22float2(__ldg(Y + (xc * UM_DIRS + d) * 256 + e % 256));
+        float* bd = b[d];
+        bd[um_off(i, j)] = y.x;
+        bd[um_off(i, 16 + j)] = -y.y;
+        bd[um_off(16 + i, j)] = y.y;
+        bd[um_off(16 + i, 16 + j)] = y.x;
     }
 }
 
@@ -290,17 +309,8 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
     float4 va[UM_DIRS][4];
 #pragma unroll
     for (int d = 0; d < UM_DIRS; ++d) um_load_a(va[d], in, pp, nbr2d(pp, xc, d), col0, skip_rhs);
-    // weights of the five directions: B_d[n][k] from the FP16 block Y[xc][d] (column-major: j * 16 + i)
-    for (int e = t; e < UM_DIRS * 256; e += UM_THREADS) {
-        const int d = e >> 8, j = (e >> 4) & 15, i = e & 15;
-        const float2 y = __half22float2(__ldg(Y + (xc * UM_DIRS + d) * 256 + e % 256));
-        float* b = sm.b[d];
-        b[um_off(i, j)] = y.x;
-        b[um_off(i, 16 + j)] = -y.y;
-        b[um_off(16 + i, j)] = y.y;
-        b[um_off(16 + i, 16 + j)] = y.x;
-    }
-    um_store_a(sm, 0, va[0], pp);
+    um_build_b(sm.b, Y, xc, t, UM_THREADS);
+    um_store_ab(sm.a[0][0], sm.a[0][1], va[0], pp);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
             const int nb_buf = (d + 1) & 1;
             if (d + 1 >= 2)                                   // the MMAs of direction d - 1 have read the buffer
                 ok = ok && mbar_wait_bounded(&sm.mbar[nb_buf], (unsigned)(((d - 1) >> 1) & 1), UM_WAIT_NS);
-            um_store_a(sm, nb_buf, va[d + 1 < UM_DIRS ? d + 1 : 0], pp);
+            um_store_ab(sm.a[nb_buf][0], sm.a[nb_buf][1], va[d + 1 < UM_DIRS ? d + 1 : 0], pp);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
         }
@@ -380,15 +390,458 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dt), "r"(UM_N) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised tcgen05 form.  One CTA per SM walks the work
+// items (coarse site, tile of 128 columns) item = blockIdx.x + k gridDim.x, so
+// the CTAs together sweep the lattice in site order and a site's inputs, read
+// by the items of its four neighbours, are found in L2.
+//
+// Here the K index of the real form runs over (Re v_j, Im v_j) pairs, k = 2 j
+// and 2 j + 1: the order of the complex inputs in memory.  One tensor copy (TMA)
+// per (item, direction) stage then brings the tile's 128 column rows straight
+// into the K-major operand layout with the 128-byte swizzle, where the tensor core
+// reads them as TF32 (the high part, mantissa truncated); the producer threads
+// add the low part x - trunc(x) as a second operand in the same layout.  The weight matrices take the same K order,
+// and the sigma_3 signs of the adjoint (on input components 8..15 and output
+// components 8..15) are folded into them.
+//
+// Roles:
+//   warps 0-7   producers: thread 0 issues the tensor copy of each stage UP_DIST
+//               stages ahead into a ring of UP_OPS operand stages; every thread
+//               writes the low parts of its share once a stage has landed; per
+//               item the five weight matrices (double-buffered by item) from FP16
+//               blocks loaded one item ahead;
+//   warp 12     lane 0 issues the 8 MMAs of each direction into that direction's
+//               TMEM accumulator (32 columns; 2 items x 5 directions) and commits
+//               each stage back to the producers and each finished item to the
+//               epilogue;
+//   warps 8-11  epilogue: the sum of the previous item's five accumulators from
+//               TMEM, plus the identity and the s-hops (the item's own inputs, by
+//               tensor copy), staged through shared memory so that each warp
+//               stores whole 128-byte column rows, while the next item's MMAs run.
+// Every mbarrier wait is bounded by %globaltimer; a wait that runs out sets the
+// status word and an abort flag that ends every role's loop; thread 0 then waits
+// (bounded) for its tensor copies in flight, the issuing thread for its MMAs,
+// and the TMEM is freed.
+// ---------------------------------------------------------------------------
+constexpr int UP_HI = 6;                       // stages of raw inputs (the TF32 high parts), filled by TMA
+constexpr int UP_LO = 2;                       // stages of low parts
+constexpr int UP_DIST = UP_HI - 2;             // tensor copies in flight ahead of the current stage
+constexpr int UP_PROD = 256, UP_EPI = 128, UP_THREADS = UP_PROD + UP_EPI + 32;
+constexpr uint32_t UP_STAGE_BYTES = UM_M * UM_K * 4;
+constexpr int UP_OROW = UM_K + 4;              // floats per row of the padded output staging tile
+// one 32-column TMEM accumulator per (item parity, direction): the 8 MMAs of a direction form
+// the only dependent chain, so the directions' MMAs overlap in the tensor pipe
+constexpr int UP_TMEM_COLS = 512;
+struct UpSmem {
+    float hi[UP_HI][UM_M * UM_K];                // raw FP32 inputs of a stage (core-matrix order)
+    float lo[UP_LO][UM_M * UM_K];                // x - trunc_tf32(x) of a stage
+    float b[2][UM_DIRS][UM_N * UM_K];            // weights, double-buffered by item
+    float e[2][UM_M * UM_K];                     // the item's own inputs for the epilogue (core-matrix order)
+    float o[UM_M * UP_OROW];                     // output staging, [column][32 floats + pad]
+    unsigned long long tma[UP_HI], ehi[UP_HI], full[UP_LO], elo[UP_LO];
+    unsigned long long wfull[2], wempty[2], tfull[2], tempty[2], efull[2], done;
+    uint32_t tmem;
+    int abort;
+};
+
+// Bounded wait that also gives up once another role has aborted.  SLEEP > 0 backs off
+// between polls (roles whose wait is not on the critical path).
+template <int SLEEP>
+__device__ __forceinline__ bool up_wait(UpSmem& sm, unsigned long long* bar, unsigned parity, int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 1;; ++it) {
+        if (SLEEP > 0) __nanosleep(SLEEP);
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int*)&sm.abort) return false;
+            if (now_ns() - t0 > UM_WAIT_NS) {
+                *(volatile int*)&sm.abort = 1;
+                atomicExch(status, 3);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void up_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// named barrier 1 over the 128 epilogue threads; epi_any also returns the OR of v over them
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 128, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v) : "memory");
+    return r != 0;
+}
+// bounded wait for a tensor copy that nobody else waits for (before the CTA ends)
+__device__ __forceinline__ void up_drain(unsigned long long* bar, unsigned parity) {
+    const unsigned long long t0 = now_ns();
+    while (!mbar_try_wait(bar, parity) && now_ns() - t0 < UM_WAIT_NS) {}
+}
+
+// Operand A of the persistent form in the K-major layout with the 128-byte swizzle: row r
+// (a column of the tile) holds its 32 K values in 128 bytes, 16-byte chunk c of the row at
+// chunk position c ^ (r & 7); 8-row groups are 1024 bytes apart.  Float offset of (r, k):
+__device__ __forceinline__ int sw_off(int r, int k) { return r * 32 + ((((k >> 2) ^ r) & 7) << 2) + (k & 3); }
+// its shared-memory descriptor (the K position within the row advances the start address)
+__device__ __forceinline__ uint64_t sw_desc(const void* base) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(base) >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                                  // leading byte offset: unused with the swizzle
+    d |= (uint64_t)(1024 >> 4) << 32;                        // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;                                  // descriptor version
+    d |= (uint64_t)2 << 61;                                  // 128-byte swizzle
+    return d;
+}
+
+// Inputs of one tile at one site as one tensor copy.  The tensor map views the input vectors
+// as 3-d FP32 data (k, column, site) with strides (4 B, one column, 128 B), k = 2 j + (0: Re,
+// 1: Im) of input component j, column = rhs Ls_c + s; the box (32, 128, 1) of columns
+// 128 t .. 128 t + 127 at site nb lands in shared memory as 128 rows of 128 bytes with the
+// 128-byte swizzle, the layout of operand A.  Columns past the last one are filled with zeros.
+__device__ __forceinline__ void up_tma(float* dst, unsigned long long* bar, const CUtensorMap* tmap, int tile,
+                                       long long nb) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(UP_STAGE_BYTES)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(UM_M * tile), "r"((int)nb),
+                   "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(UP_THREADS, 1) k_coarse_umma_p(const __half2* __restrict__ Y,
+                                                                const float2* __restrict__ in,
+                                                                float2* __restrict__ out, TcParams p,
+                                                                const int* __restrict__ skip_rhs, int* status,
+                                                                const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(1024) unsigned char up_raw[];
+    UpSmem& sm = *reinterpret_cast<UpSmem*>(up_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int ntile = (p.ncols + UM_M - 1) / UM_M;
+    const long long nitems = p.Vc * ntile;
+    if (t == 0) {
+        for (int i = 0; i < UP_HI; ++i) { mbar_init(&sm.tma[i], 1); mbar_init(&sm.ehi[i], 1); }
+        for (int i = 0; i < UP_LO; ++i) { mbar_init(&sm.full[i], UP_PROD); mbar_init(&sm.elo[i], 1); }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.wfull[i], UP_PROD);
+            mbar_init(&sm.wempty[i], 1);
+            mbar_init(&sm.tfull[i], 1);
+            mbar_init(&sm.tempty[i], UP_EPI);
+            mbar_init(&sm.efull[i], 1);
+        }
+        mbar_init(&sm.done, 1);
+        // the swizzled tensor copies and operands need 1024-byte aligned buffers
+        sm.abort = ((smem_u32(sm.hi) | smem_u32(sm.lo) | smem_u32(sm.e)) & 1023u) != 0;
+        if (sm.abort) atomicExch(status, 3);
+    }
+    if (warp == 12) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(UP_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sm.tmem;
+    // items of this CTA: il = 0 .. nmine - 1, item = blockIdx.x + il gridDim.x
+    const long long nmine = (blockIdx.x < nitems && !sm.abort) ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long nstages = nmine * UM_DIRS;
+    auto item_of = [&](long long il) { return blockIdx.x + il * gridDim.x; };
+
+    if (warp < 8) {
+        // ---------------- producers ----------------
+        // thread t writes the low parts of chunk c = t & 7 of rows (t >> 3) + 32 i (a quarter-warp
+        // covers one whole 128-byte row)
+        const int cq = t & 7, rb = t >> 3;
+        auto stage_tma = [&](long long g) {
+            const long long item = item_of(g / UM_DIRS);
+            const int s = (int)(g % UP_HI);
+            up_tma(sm.hi[s], &sm.tma[s], &tmap, (int)(item % ntile), nbr2d(p, item / ntile, (int)(g % UM_DIRS)));
+        };
+        long long issued = 0, landed = 0;             // tensor copies issued (thread 0) and waited for
+        if (t == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+            for (; issued < UP_DIST && issued < nstages; ++issued) stage_tma(issued);
+        }
+        __half2 yv[UM_DIRS];
+        if (nmine > 0) {
+            const long long xc0 = blockIdx.x / ntile;
+#pragma unroll
+            for (int k = 0; k < UM_DIRS; ++k) yv[k] = __ldg(Y + xc0 * (UM_DIRS * 256) + t + 256 * k);
+        }
+        for (long long g = 0; g < nstages; ++g) {
+            const long long il = g / UM_DIRS;
+            const int d = (int)(g % UM_DIRS);
+            if (d == 0) {
+                // the weights of item il (Y loaded one item ahead): B[n][k] with k = 2 j (Re v_j),
+                // 2 j + 1 (Im v_j); rows n < 16: Re out_n, n = 16 + i: Im out_i
+                const int bb = (int)(il & 1);
+                const long long ub = il >> 1;
+                if (ub >= 1 && !up_wait<0>(sm, &sm.wempty[bb], (unsigned)((ub - 1) & 1), status)) break;
+#pragma unroll
+                for (int k = 0; k < UM_DIRS; ++k) {
+                    const int e = t + 256 * k;
+                    const int j = (e >> 4) & 15, i = e & 15;
+                    float2 y = __half22float2(yv[k]);
+                    if (p.dag && ((i >= 8) != (j >= 8))) { y.x = -y.x; y.y = -y.y; }   // sigma_3 Y sigma_3
+                    float* bd = sm.b[bb][k];
+                    bd[um_off(i, 2 * j)] = y.x;
+                    bd[um_off(i, 2 * j + 1)] = -y.y;
+                    bd[um_off(16 + i, 2 * j)] = y.y;
+                    bd[um_off(16 + i, 2 * j + 1)] = y.x;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                up_arrive(&sm.wfull[bb]);
+                if (il + 1 < nmine) {
+                    const long long xn = item_of(il + 1) / ntile;
+#pragma unroll
+                    for (int k = 0; k < UM_DIRS; ++k) yv[k] = __ldg(Y + xn * (UM_DIRS * 256) + t + 256 * k);
+                }
+            }
+            // the tensor copy of stage g has landed and the low-part slot is free: x - trunc_tf32(x)
+            const int s = (int)(g % UP_HI), l = (int)(g % UP_LO);
+            if (!up_wait<0>(sm, &sm.tma[s], (unsigned)((g / UP_HI) & 1), status)) break;
+            landed = g + 1;
+            if (g >= UP_LO && !up_wait<0>(sm, &sm.elo[l], (unsigned)(((g - UP_LO) / UP_LO) & 1), status)) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int o = sw_off(rb + 32 * q, 4 * cq);
+                const float4 v = *reinterpret_cast<const float4*>(&sm.hi[s][o]);
+                float4 lo;
+                lo.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+                lo.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+                lo.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+                lo.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+                *reinterpret_cast<float4*>(&sm.lo[l][o]) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            up_arrive(&sm.full[l]);
+            // stage g + UP_DIST goes into the raw slot of stage g - 2 once its MMAs are done
+            if (t == 0 && g + UP_DIST < nstages) {
+                const long long gn = g + UP_DIST;
+                if (gn >= UP_HI && !up_wait<0>(sm, &sm.ehi[gn % UP_HI], (unsigned)(((gn - UP_HI) / UP_HI) & 1), status))
+                    break;
+                stage_tma(gn);
+                issued = gn + 1;
+            }
+        }
+        // after an early exit: the tensor copies still in flight land before the CTA ends
+        if (t == 0)
+            for (long long g = landed; g < issued; ++g) up_drain(&sm.tma[g % UP_HI], (unsigned)((g / UP_HI) & 1));
+    } else if (warp < 12) {
+        // ---------------- epilogue ----------------
+        const int te = t - UP_PROD;                  // row of the accumulator = column of the tile
+        const int wq = warp & 3;                     // TMEM lanes 32 wq .. 32 wq + 31
+        const long long slice = p.Vc * 16;
+        long long eissued = 0, elanded = 0;          // own-input copies issued (te == 0) and waited for
+        auto item_tma = [&](long long il) {
+            const long long item = item_of(il);
+            up_tma(sm.e[il & 1], &sm.efull[il & 1], &tmap, (int)(item % ntile), item / ntile);
+        };
+        if (te == 0)
+            for (; eissued < 2 && eissued < nmine; ++eissued) item_tma(eissued);
+        for (long long il = 0; il < nmine; ++il) {
+            const int acc = (int)(il & 1), eb = (int)(il & 1);
+            const unsigned par = (unsigned)((il >> 1) & 1);
+            bool ok = up_wait<64>(sm, &sm.tfull[acc], par, status);
+            ok = ok && up_wait<64>(sm, &sm.efull[eb], par, status);
+            if (epi_any(!ok)) break;                  // all epilogue threads leave together
+            if (te == 0) elanded = il + 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // the sum of the item's five direction accumulators
+            float racc[32];
+#pragma unroll
+            for (int d = 0; d < UM_DIRS; ++d) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + (uint32_t)((acc * UM_DIRS + d) * UM_N) + ((uint32_t)(32 * wq) << 16);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                             "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                               "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                               "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                               "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 32; ++i) racc[i] = d == 0 ? __uint_as_float(r[i]) : racc[i] + __uint_as_float(r[i]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            up_arrive(&sm.tempty[acc]);               // the accumulators may be overwritten
+            const long long item = item_of(il);
+            const long long xc = item / ntile;
+            const int tile = (int)(item % ntile);
+            const int col = tile * UM_M + te;
+            // identity and s-hop terms from the item's own inputs (the s-hop partner column of the
+            // same right-hand side lies in the same tile: Ls_c divides 128)
+            float4 res[8];
+            if (col < p.ncols) {
+                const int sl = col % p.Ls_c;
+                int mh[2];
+                float sc[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {           // components 8 h .. 8 h + 7 share one s-hop
+                    const bool from_below = p.dag ? (h == 1) : (h == 0);
+                    int sh;
+                    sc[h] = 1.f;
+                    if (from_below) { if (sl > 0) sh = sl - 1; else { sh = p.Ls_c - 1; sc[h] = -p.mf; } }
+                    else            { if (sl < p.Ls_c - 1) sh = sl + 1; else { sh = 0; sc[h] = -p.mf; } }
+                    mh[h] = te - sl + sh;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int h = q >> 2;
+                    const float4 a = *reinterpret_cast<const float4*>(&sm.e[eb][sw_off(te, 4 * q)]);
+                    const float4 v = *reinterpret_cast<const float4*>(&sm.e[eb][sw_off(mh[h], 4 * q)]);
+                    res[q] = make_float4(racc[2 * q] + a.x + sc[h] * v.x, racc[16 + 2 * q] + a.y + sc[h] * v.y,
+                                         racc[2 * q + 1] + a.z + sc[h] * v.z, racc[17 + 2 * q] + a.w + sc[h] * v.w);
+                }
+            }
+            epi_sync();                               // every thread has read e[eb]
+            if (te == 0 && il + 2 < nmine) {          // e[eb] takes the inputs of item il + 2
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                item_tma(il + 2);
+                eissued = il + 3;
+            }
+            // results into the padded staging tile (own row), then whole column rows to memory
+            if (col < p.ncols) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) *reinterpret_cast<float4*>(&sm.o[te * UP_OROW + 4 * q]) = res[q];
+            }
+            epi_sync();
+            {
+                const int q = te & 7;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int mm = (te >> 3) + 16 * i;
+                    const int c = tile * UM_M + mm;
+                    if (c < p.ncols && !(skip_rhs && skip_rhs[c / p.Ls_c])) {
+                        float4* o4 = reinterpret_cast<float4*>(out + (long long)(c / p.Ls_c) * slice * p.Ls_c +
+                                                               (long long)(c % p.Ls_c) * slice + xc * 16);
+                        o4[q] = *reinterpret_cast<const float4*>(&sm.o[mm * UP_OROW + 4 * q]);
+                    }
+                }
+            }
+            epi_sync();                               // the staging tile is read before the next item
+        }
+        if (te == 0)
+            for (long long g = elanded; g < eissued; ++g) up_drain(&sm.efull[g & 1], (unsigned)((g >> 1) & 1));
+    } else if (t == 32 * 12) {
+        // ---------------- MMA issue ----------------
+        // D F32, A and B TF32, both K-major, N = 32, M = 128
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UM_N >> 3) << 17) |
+                               ((uint32_t)(UM_M >> 4) << 24);
+        bool ok = true;
+        for (long long il = 0; ok && il < nmine; ++il) {
+            const int acc = (int)(il & 1), bb = (int)(il & 1);
+            const long long ua = il >> 1;
+            if (ua >= 1 && !up_wait<0>(sm, &sm.tempty[acc], (unsigned)((ua - 1) & 1), status)) break;
+            if (!up_wait<0>(sm, &sm.wfull[bb], (unsigned)(ua & 1), status)) break;
+            for (int d = 0; d < UM_DIRS; ++d) {
+                const uint32_t dt = tmem + (uint32_t)((acc * UM_DIRS + d) * UM_N);
+                const long long g = il * UM_DIRS + d;
+                const int s = (int)(g % UP_HI), l = (int)(g % UP_LO);
+                if (!up_wait<0>(sm, &sm.full[l], (unsigned)((g / UP_LO) & 1), status) ||
+                    !up_wait<0>(sm, &sm.tma[s], (unsigned)((g / UP_HI) & 1), status)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int ks = 0; ks < UM_K / 8; ++ks) {
+                    const uint64_t db = um_desc(reinterpret_cast<const char*>(sm.b[bb][d]) + ks * 2 * UM_LBO);
+                    const uint64_t dah = sw_desc(reinterpret_cast<const char*>(sm.hi[s]) + ks * 32);
+                    const uint64_t dal = sw_desc(reinterpret_cast<const char*>(sm.lo[l]) + ks * 32);
+                    um_mma(dt, dah, db, idesc, ks > 0 ? 1u : 0u);
+                    um_mma(dt, dal, db, idesc, 1u);
+                }
+                um_commit(&sm.ehi[s]);
+                um_commit(&sm.elo[l]);
+            }
+            if (!ok) break;
+            um_commit(&sm.tfull[acc]);
+            um_commit(&sm.wempty[bb]);
+        }
+        // every MMA issued by this thread has finished before the TMEM is released
+        um_commit(&sm.done);
+        up_drain(&sm.done, 0u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 12)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UP_TMEM_COLS) : "memory");
+}
+
 }  // namespace
 
-// forms of the contraction: 1, 2, 4 = mma.sync with that many column tiles per warp; TC_UMMA = tcgen05
+// forms of the contraction: 1, 2, 4 = mma.sync with that many column tiles per warp; TC_UMMA = tcgen05,
+// one item per CTA; TC_UMMA_P = tcgen05, persistent and warp-specialised
 constexpr int TC_UMMA = 0x100;
+constexpr int TC_UMMA_P = 0x101;
 
 static bool umma_eligible(const dwf_mg* h, int ncols) { return h->ytile_half && ncols >= UM_M; }
+// the persistent form's epilogue finds each column's s-hop partner in the same 128-column tile
+// (Ls_c divides 128)
+static bool umma_p_eligible(const dwf_mg* h, int ncols) { return umma_eligible(h, ncols) && UM_M % h->mg.Ls_c == 0; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// the 5-d view of the input vectors read by the persistent form (see up_tma)
+static dwf_status input_tensor_map(CUtensorMap* tm, const float2* in, const TcParams& p) {
+    auto enc = tensor_map_encoder();
+    if (!enc) { set_error("cuTensorMapEncodeTiled is not available from the driver"); return DWF_ERR_CUDA; }
+    if ((reinterpret_cast<uintptr_t>(in) & 15u) != 0) { set_error("coarse vectors must be 16-byte aligned"); return DWF_ERR_ARG; }
+    const cuuint64_t col_bytes = (cuuint64_t)p.Vc * 16 * sizeof(float2);
+    const cuuint64_t dims[3] = {32, (cuuint64_t)p.ncols, (cuuint64_t)p.Vc};
+    const cuuint64_t strides[2] = {col_bytes, 16 * sizeof(float2)};
+    const cuuint32_t box[3] = {32, (cuuint32_t)UM_M, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(in), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return DWF_ERR_CUDA; }
+    return DWF_OK;
+}
 
 static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, const float2* in, float2* out,
                               const int* skip_rhs, cudaStream_t st) {
+    if (form == TC_UMMA_P) {
+        static unsigned long long attr_set = 0;      // per device
+        static int sms_of[64] = {0};
+        int dev = 0;
+        DWF_CHECK_CUDA(cudaGetDevice(&dev));
+        if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
+            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma_p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)sizeof(UpSmem)));
+            if (dev < 64) {
+                DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev));
+                attr_set |= 1ull << dev;
+            }
+        }
+        int sms = dev < 64 ? sms_of[dev] : 0;
+        if (sms <= 0) DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long nitems = p.Vc * ((p.ncols + UM_M - 1) / UM_M);
+        const long long grid = nitems < sms ? nitems : sms;
+        if (grid < 1) return DWF_OK;
+        alignas(64) CUtensorMap tm;
+        DWF_TRY(input_tensor_map(&tm, in, p));
+        k_coarse_umma_p<<<(unsigned)grid, UP_THREADS, sizeof(UpSmem), st>>>((const __half2*)h->Ytile, in, out, p,
+                                                                           skip_rhs, h->status + 1, tm);
+        DWF_CHECK_LAUNCH();
+        return DWF_OK;
+    }
     if (form == TC_UMMA) {
         static bool attr = false;
         if (!attr) {
@@ -437,9 +890,10 @@ dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* o
     if (h->mg.nd != 2 || h->mg.ncd != 16 || nrhs < 1) return DWF_OK;
     if (h->tc_choice.count(nrhs)) return DWF_OK;
     const TcParams p = tc_params(h, nrhs, h->mf, false);
-    int forms[4] = {1, 2, 4, 0};
+    int forms[5] = {1, 2, 4, 0, 0};
     int nforms = 3;
     if (umma_eligible(h, p.ncols)) forms[nforms++] = TC_UMMA;
+    if (umma_p_eligible(h, p.ncols)) forms[nforms++] = TC_UMMA_P;
     cudaEvent_t a, b;
     DWF_CHECK_CUDA(cudaEventCreate(&a));
     DWF_CHECK_CUDA(cudaEventCreate(&b));
@@ -471,8 +925,10 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
     }
     const TcParams p = tc_params(h, nrhs, mf, dagger);
     int form = 4;
-    if (h->prm.coarse_tc == 1 && umma_eligible(h, p.ncols)) form = TC_UMMA;
-    else if (h->prm.coarse_tc >= 2) form = h->prm.coarse_tc == 2 ? 1 : h->prm.coarse_tc == 3 ? 2 : 4;
+    if (h->prm.coarse_tc == 1 && umma_p_eligible(h, p.ncols)) form = TC_UMMA_P;
+    else if (h->prm.coarse_tc == 1 && umma_eligible(h, p.ncols)) form = TC_UMMA;
+    else if (h->prm.coarse_tc == 5 && umma_eligible(h, p.ncols)) form = TC_UMMA;
+    else if (h->prm.coarse_tc >= 2 && h->prm.coarse_tc <= 4) form = h->prm.coarse_tc == 2 ? 1 : h->prm.coarse_tc == 3 ? 2 : 4;
     else if (h->prm.coarse_tc == 0) {
         auto it = h->tc_choice.find(nrhs);
         if (it != h->tc_choice.end()) form = it->second;

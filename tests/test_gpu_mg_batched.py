@@ -149,12 +149,13 @@ def test_batched_full_size_256(dw):
     h.close()
 
 
-def test_batched_solve_with_tcgen05_coarse(dw):
-    """33 right-hand sides (132 coarse columns: one full and one partial 128-column tile) with
-    the tcgen05 form of the coarse contraction (coarse_tc = 1); every system reaches 1e-10."""
+@pytest.mark.parametrize("tc,nrhs", [(1, 34), (5, 33)])
+def test_batched_solve_with_tcgen05_coarse(dw, tc, nrhs):
+    """33 or 34 right-hand sides (132 / 136 coarse columns: one full and one partial 128-column
+    tile) with the tcgen05 forms of the coarse contraction (coarse_tc = 1: persistent, 5: one item
+    per thread block); every system reaches 1e-10."""
     dims, Ls, M5, mf = (16, 16), 8, 1.0, 0.01
-    h, U, rng = _hierarchy(dw, dims, Ls, 0.4, 81, M5, mf, -0.12, {"coarse_tc": 1})
-    nrhs = 33
+    h, U, rng = _hierarchy(dw, dims, Ls, 0.4, 81, M5, mf, -0.12, {"coarse_tc": tc})
     B = np.stack([synth.gaussian_spinor(rng, dims, Ls).reshape(-1) for _ in range(nrhs)])
     X = torch.empty(B.size, dtype=torch.complex128, device="cuda")
     stats, status = dw.mg_solve_batched(h, _dev(B), X, nrhs, tol=1e-10)
