@@ -349,7 +349,11 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
         mbar_wait_bounded(&sm.mbar[2], 0u, UM_WAIT_NS);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp < 4) {
+    // After a timed-out wait the accumulator is not read (its warp skips the tensor-memory load
+    // together), no output is written, status 3 reports the failure, and the TMEM is freed at the
+    // end without further waiting.
+    const bool warp_ok = __all_sync(0xffffffffu, ok);
+    if (warp < 4 && warp_ok) {
         // row m = t of D: column col0 + t
         uint32_t r[32];
         const uint32_t taddr = dt + ((uint32_t)(32 * warp) << 16);
