@@ -520,6 +520,9 @@ typedef struct {
                              GCR on Dhat2_PV^dag Dhat2_DW itself (valid by the right-half-plane
                              property, App. B), same tolerance and start                      */
     int coarsest_restart; /* restart length of that GCR (8)                                    */
+    int block_prec;       /* storage of the new level's Galerkin blocks for its stencil:
+                             DWF_F32 (default) or DWF_F32_L16 (FP16); the arithmetic is FP32
+                             either way                                                        */
 } dwf_mg_level_params;
 
 DWF_API void dwf_mg_default_level_params(dwf_mg_level_params* p);

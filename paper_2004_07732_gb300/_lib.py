@@ -61,7 +61,7 @@ class LevelParams(ctypes.Structure):
                 ("gcr_maxiter", ctypes.c_int), ("tol", ctypes.c_double), ("post_smooth", ctypes.c_int),
                 ("coarsest_tol", ctypes.c_double), ("coarsest_maxiter", ctypes.c_int), ("n_deflate", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("filter_degree", ctypes.c_int), ("coarsest_solver", ctypes.c_int),
-                ("coarsest_restart", ctypes.c_int)]
+                ("coarsest_restart", ctypes.c_int), ("block_prec", ctypes.c_int)]
 
 
 _lib = None
@@ -701,6 +701,8 @@ def mg_add_level(mg: Multigrid, params=None, null_starts=None, lanczos_start=Non
         if k == "block":
             for i, b in enumerate(v):
                 p.block[i] = int(b)
+        elif k == "block_prec" and isinstance(v, str):
+            p.block_prec = PREC[v]
         else:
             setattr(p, k, v)
     if null_starts is None:

@@ -160,6 +160,8 @@ dwf_status coarse_gcr_persistent(const dwf_mg* h, const float2* rc, float2* ec, 
 
 // per-site kernel of the coarse stencil on FP32 column-major blocks (any
 // coarse lattice with 24 <= ncd, ncd * Ls_c <= 512); the adjoint uses sigma_3
+dwf_status coarse_site_apply(const CoarseParams& p, const __half2* B, const float2* in, float2* out, bool dagger,
+                             const int* skip, int* status, cudaStream_t st);
 dwf_status coarse_site_apply(const CoarseParams& p, const float2* B, const float2* in, float2* out, bool dagger,
                              const int* skip, int* status, cudaStream_t st);
 
@@ -180,6 +182,7 @@ __global__ void k_nv_p(double2* __restrict__ p, const double2* __restrict__ r, l
 __global__ void k_block_ortho(const double2* __restrict__ vecs, double2* __restrict__ P, AggIndex ai, int nchd,
                               int ncol, int dof, int nvec, long long V, int nb, int* status, int cblock);
 __global__ void k_blocks_to_f32(const double2* __restrict__ Y, float2* __restrict__ Y32, long long nblocks, int ncd);
+__global__ void k_blocks_to_f16(const double2* __restrict__ Y, __half2* __restrict__ Y16, long long nblocks, int ncd);
 __global__ void k_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long n);
 
 // the third level: the level-2 solve of the K-cycle (FGCR preconditioned by the

@@ -421,18 +421,32 @@ __global__ void __launch_bounds__(512) k_coarse_site(const BT* __restrict__ B, c
     const int i = threadIdx.x % ncd, s = threadIdx.x / ncd;
     if (s >= Ls_c) return;
     const int nvec = p.nvec;
-    float2 a_lo = make_float2(0.f, 0.f), a_hi = make_float2(0.f, 0.f);    // inputs j < nvec / j >= nvec
+    // inputs j < nvec / j >= nvec, each summed in four independent chains (j mod 4)
+    float2 a_lo[4], a_hi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { a_lo[u] = make_float2(0.f, 0.f); a_hi[u] = a_lo[u]; }
     for (int dir = 0; dir < ndir; ++dir) {
         const BT* yd = yb + (size_t)dir * ncd * ncd + i;
         const float2* v = vs + (dir * Ls_c + s) * ncd;
-#pragma unroll 4
-        for (int j = 0; j < nvec; ++j) a_lo = cfma(to_f2(yd[j * ncd]), v[j], a_lo);
-#pragma unroll 4
-        for (int j = nvec; j < ncd; ++j) a_hi = cfma(to_f2(yd[j * ncd]), v[j], a_hi);
+        int j = 0;
+        for (; j + 4 <= nvec; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a_lo[u] = cfma(to_f2(yd[(j + u) * ncd]), v[j + u], a_lo[u]);
+        }
+        for (; j < nvec; ++j) a_lo[0] = cfma(to_f2(yd[j * ncd]), v[j], a_lo[0]);
+        for (; j + 4 <= ncd; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a_hi[u] = cfma(to_f2(yd[(j + u) * ncd]), v[j + u], a_hi[u]);
+        }
+        for (; j < ncd; ++j) a_hi[0] = cfma(to_f2(yd[j * ncd]), v[j], a_hi[0]);
     }
+    const float2 lo = make_float2((a_lo[0].x + a_lo[1].x) + (a_lo[2].x + a_lo[3].x),
+                                  (a_lo[0].y + a_lo[1].y) + (a_lo[2].y + a_lo[3].y));
+    const float2 hi = make_float2((a_hi[0].x + a_hi[1].x) + (a_hi[2].x + a_hi[3].x),
+                                  (a_hi[0].y + a_hi[1].y) + (a_hi[2].y + a_hi[3].y));
     const float sj = dag ? -1.f : 1.f;                   // sigma_3 on the inputs
     const float si = (dag && i >= nvec) ? -1.f : 1.f;    // sigma_3 on the output
-    float2 acc = make_float2(si * (a_lo.x + sj * a_hi.x), si * (a_lo.y + sj * a_hi.y));
+    float2 acc = make_float2(si * (lo.x + sj * hi.x), si * (lo.y + sj * hi.y));
     const float2* v0 = vs;                               // dir 0 = the site itself
     const float2 self = v0[s * ncd + i];
     const int c = i / nvec;
@@ -601,6 +615,16 @@ dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, doub
                 (const float2*)h->Ytile, in, out, p, dagger, skip, h->status + 1);
     } else if (p.ncd == 16) k_coarse_dwf<16><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
     else             k_coarse_dwf<0><<<grid, thr, 0, st>>>(B, in, out, p, dagger, skip);
+    DWF_CHECK_LAUNCH();
+    return DWF_OK;
+}
+
+dwf_status coarse_site_apply(const CoarseParams& p, const __half2* B, const float2* in, float2* out, bool dagger,
+                             const int* skip, int* status, cudaStream_t st) {
+    if (!site_ok(p, 1)) { set_error("the per-site coarse stencil does not take %d dof on %d slices", p.ncd, p.Ls_c);
+                          return DWF_ERR_UNSUPPORTED; }
+    k_coarse_site<__half2><<<(unsigned)p.Vc, p.ncd * p.Ls_c, site_smem_bytes<__half2>(p.ndir, p.ncd, p.Ls_c), st>>>(
+        B, in, out, p, dagger, skip, status);
     DWF_CHECK_LAUNCH();
     return DWF_OK;
 }

@@ -71,7 +71,8 @@ struct Level3 {
     CoarseParams p3;                 // level-3 stencil (mf set per call)
     std::vector<void*> allocs;
     double2 *nullv2, *P2_64, *Y3_64;
-    float2 *P2_32, *Y3_32;
+    float2 *P2_32, *Y3_32;           // Y3_32: the stencil's FP32 blocks (block_prec DWF_F32)
+    __half2* Y3_16;                  // the stencil's FP16 blocks (block_prec DWF_F32_L16), else nullptr
     // deflation
     int ndefl;                       // columns of V in use
     float2* Vd;                      // [ndefl][n3]
@@ -840,6 +841,7 @@ dwf_status l3_apply(const Level3& L, const float2* in, float2* out, double mf, b
                     cudaStream_t st) {
     CoarseParams p = L.p3;
     p.mf = (float)mf;
+    if (L.Y3_16) return coarse_site_apply(p, L.Y3_16, in, out, dagger, skip, L.status, st);
     return coarse_site_apply(p, L.Y3_32, in, out, dagger, skip, L.status, st);
 }
 
@@ -1441,9 +1443,14 @@ dwf_status add_level_impl(dwf_mg* h, Level3& L, const double2* starts, const dou
     // 3. Galerkin kernel of level 3
     const long long nblk = L.V3 * 5;
     DWF_TRY(l3_alloc(&L, (void**)&L.Y3_64, nblk * L.ncd3 * L.ncd3 * sizeof(double2)));
-    DWF_TRY(l3_alloc(&L, (void**)&L.Y3_32, nblk * L.ncd3 * L.ncd3 * sizeof(float2)));
     k_galerkin_l3<<<dim3((unsigned)L.V3, 5), 256, 0, st>>>(h->Y64, L.P2_64, L.Y3_64, ai, L.nvec1, L.nvec2);
-    k_blocks_to_f32<<<level_ew_grid(nblk * L.ncd3 * L.ncd3), 256, 0, st>>>(L.Y3_64, L.Y3_32, nblk, L.ncd3);
+    if (L.prm.block_prec == DWF_F32_L16) {
+        DWF_TRY(l3_alloc(&L, (void**)&L.Y3_16, nblk * L.ncd3 * L.ncd3 * sizeof(__half2)));
+        k_blocks_to_f16<<<level_ew_grid(nblk * L.ncd3 * L.ncd3), 256, 0, st>>>(L.Y3_64, L.Y3_16, nblk, L.ncd3);
+    } else {
+        DWF_TRY(l3_alloc(&L, (void**)&L.Y3_32, nblk * L.ncd3 * L.ncd3 * sizeof(float2)));
+        k_blocks_to_f32<<<level_ew_grid(nblk * L.ncd3 * L.ncd3), 256, 0, st>>>(L.Y3_64, L.Y3_32, nblk, L.ncd3);
+    }
     DWF_CHECK_LAUNCH();
     int hstat = 0;
     DWF_CHECK_CUDA(cudaMemcpyAsync(&hstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1512,6 +1519,7 @@ void dwf_mg_default_level_params(dwf_mg_level_params* p) {
     p->filter_degree = 64;
     p->coarsest_solver = 0;
     p->coarsest_restart = 8;
+    p->block_prec = DWF_F32;
 }
 
 dwf_status mg_add_level(dwf_mg* h, const dwf_mg_level_params* p, const void* null_starts, const void* lanczos_start,
@@ -1533,7 +1541,7 @@ dwf_status mg_add_level(dwf_mg* h, const dwf_mg_level_params* p, const void* nul
         prm.lanczos_steps < 0 || prm.lanczos_steps > LANCZOS_MAX || prm.filter_degree < 0 ||
         prm.filter_degree > 4096 || !(prm.tol > 0.0) || !(prm.coarsest_tol > 0.0) ||
         (prm.coarsest_solver != 0 && prm.coarsest_solver != 1) || prm.coarsest_restart < 1 ||
-        prm.coarsest_restart > L2_MAXK) {
+        prm.coarsest_restart > L2_MAXK || (prm.block_prec != DWF_F32 && prm.block_prec != DWF_F32_L16)) {
         set_error("bad level parameters");
         return DWF_ERR_ARG;
     }

@@ -61,7 +61,7 @@ class Hier:
 
 @pytest.fixture(scope="module")
 def hier(dw):
-    return Hier(dw, level={"setup_maxiter": 12, "n_deflate": 32, "lanczos_steps": 2048})
+    return Hier(dw, level={"setup_maxiter": 12, "n_deflate": 32, "lanczos_steps": 2048, "block_prec": "f32"})
 
 
 def test_level2_relaxation_matches_oracle(dw, hier):
@@ -121,6 +121,31 @@ def test_level3_operator_and_transfers_match_oracle(dw, hier):
     dw.mg_level_prolong(h, vd, e2)
     want = omg.prolong_walls(v.astype(np.complex128), P2, 4, 4, p2[0], p2[1], *p3)
     assert np.linalg.norm(e2.cpu().numpy() - want) / np.linalg.norm(want) < 1e-5
+
+
+def _round16(Y):
+    return Y.real.astype(np.float16).astype(np.float64) + 1j * Y.imag.astype(np.float16).astype(np.float64)
+
+
+def test_level3_fp16_blocks_match_oracle_on_rounded_blocks(dw):
+    """FP16 storage of the third level's blocks (block_prec): the stencil equals the oracle's coarse
+    operator built from the GPU's FP64 Galerkin blocks rounded to FP16, at FP32 accuracy."""
+    hh = Hier(dw, seed=905, level={"setup_maxiter": 12, "n_deflate": 0, "block_prec": "f32_l16"})
+    h = hh.h
+    cd3 = tuple(d // 2 for d in hh.cdims)
+    Y = dw.mg_level_get(h, 2).cpu().numpy().reshape(-1, 5, 24, 24)
+    K = omg.kernel_from_blocks(_round16(Y), cd3)
+    rng = np.random.default_rng(6)
+    v = synth.gaussian_complex(rng, (h.level_size,)).astype(np.complex64)
+    vd = _dev(v, torch.complex64)
+    out = torch.full_like(vd, float("nan"))
+    for m in (hh.mf, 1.0):
+        for dag in (False, True):
+            C = omg.coarse_dwf_dagger_g5(K, 4, m, 12) if dag else omg.coarse_dwf(K, 4, m, 12)
+            want = C @ v.astype(np.complex128)
+            dw.mg_level_apply(h, vd, out, m, dagger=dag)
+            assert np.linalg.norm(out.cpu().numpy() - want) / np.linalg.norm(want) < 1e-5, (m, dag)
+    h.close()
 
 
 def test_deflation_space_matches_dense_eigendecomposition(dw, hier):
@@ -200,4 +225,6 @@ def test_add_level_rejects_bad_arguments(dw, hier):
         dw.mg_add_level(h, {"block": [3, 3, 1, 1]}, _dev(np.zeros((12, 256))), _dev(np.zeros(1536)))
     with pytest.raises(dw.DwfError):     # deflation needs a Lanczos start
         dw.mg_add_level(h, {}, _dev(np.zeros((12, 256))), None)
+    with pytest.raises(dw.DwfError):     # the blocks are stored in FP32 or FP16 only
+        dw.mg_add_level(h, {"block_prec": "f64"}, _dev(np.zeros((12, 256))), _dev(np.zeros(1536)))
     h.close()
