@@ -341,7 +341,13 @@ typedef struct {
     int coarse_restart;   /* restart length of the coarse GCR (8)                         */
     int coarse_block_prec;/* storage of the Galerkin blocks read by the coarse stencil:
                              DWF_F32 or DWF_F32_L16 (FP16 blocks, FP32 arithmetic; default) */
-    int cgs_passes;       /* classical Gram-Schmidt passes per GCR step: 1, or 2 (re-orthogonalised) */
+    int cgs_passes;       /* classical Gram-Schmidt passes per GCR step: 1 (default), or 2
+                             (re-orthogonalised).  With 1, a coarse GCR step takes its
+                             projections, |w'|^2, alpha and the next |r|^2 from one reduction
+                             pass (the orthogonality of the basis and of r to it gives |w'|^2
+                             and the next |r|^2 by Pythagoras) followed by one element-wise
+                             pass; a step whose |w'|^2 falls below 1e-5 |w|^2 ends that
+                             right-hand side's coarse solve                                  */
     int coarse_tc;        /* form of the many-right-hand-side coarse contraction: 0 (default) =
                              autotuned -- the first use for a given nrhs times mma.sync with 1, 2
                              and 4 column tiles per warp and, with FP16 blocks and >= 128

@@ -365,6 +365,154 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmaxpy(float2* __restrict__ w, 
     }
 }
 
+// One GCR step of the coarse solve with a single classical Gram-Schmidt pass,
+// in one reduction pass and one element-wise pass.  The reduction reads the
+// image w = A p_k, the residual r and the orthogonalised images W_j (j < k)
+// once and sums d_j = <W_j, w>, |w|^2, <w, r> and |r|^2.  The W_j are mutually
+// orthogonal and r is orthogonal to every W_j, so with w' = w - sum_j c_j W_j:
+//   c_j = d_j / |W_j|^2,   |w'|^2 = |w|^2 - sum_j |d_j|^2 / |W_j|^2,
+//   alpha = <w', r> / |w'|^2 = <w, r> / |w'|^2,
+//   |r - alpha w'|^2 = |r|^2 - |<w, r>|^2 / |w'|^2,
+// and the element-wise pass forms w' and r - alpha w' without a reduction.
+// The residual norm is exact at every step (|r|^2 is summed afresh); only the
+// one-step prediction decides convergence.  A direction with |w'|^2 below
+// BSTEP_BREAK |w|^2 is not resolved by FP32 sums: its row stops (alpha = 0).
+constexpr int BSTEP_BLOCKS = 512;     // bound on the blocks per row of the reduction pass
+constexpr double BSTEP_BREAK = 1e-5;
+
+template <int KM>
+__global__ void __launch_bounds__(RED_THREADS) k_bstep_dots(float2* const* __restrict__ W, const float2* __restrict__ w,
+                                                            const float2* __restrict__ res, long long n, int k,
+                                                            double* __restrict__ part, unsigned* counters, BGcr* g,
+                                                            int* steps, int* done, const double* ref2, double tol2,
+                                                            int* iters, int maxit) {
+    constexpr int NQ = 2 * KM + 4;     // |w|^2, Re / Im <w, r>, |r|^2, then Re / Im d_j
+    const int r = blockIdx.y;
+    if (done[r]) return;
+    __shared__ const float4* Wp[KM];
+    __shared__ double sh[NQ][RED_THREADS / 32];
+    __shared__ double tot[NQ];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) Wp[j] = reinterpret_cast<const float4*>(W[j] + r * n);
+    __syncthreads();
+    const float4* w4 = reinterpret_cast<const float4*>(w + r * n);
+    const float4* r4 = reinterpret_cast<const float4*>(res + r * n);
+    float re[KM], im[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) { re[j] = 0.f; im[j] = 0.f; }
+    float ww = 0.f, wr = 0.f, wi = 0.f, rr = 0.f;
+    ROW_LOOP(i, n >> 1) {
+        const float4 a = w4[i], b = r4[i];
+#pragma unroll
+        for (int j = 0; j < KM; ++j)
+            if (j < k) cdot4(Wp[j][i], a, re[j], im[j]);
+        ww += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+        cdot4(a, b, wr, wi);
+        rr += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
+    }
+    const int nq = 2 * k + 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[NQ];
+    v[0] = ww; v[1] = wr; v[2] = wi; v[3] = rr;
+#pragma unroll
+    for (int j = 0; j < KM; ++j) { v[4 + 2 * j] = re[j]; v[5 + 2 * j] = im[j]; }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (q < nq) {                                             // block-uniform
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+            if (lane == 0) sh[q][warp] = v[q];
+        }
+    }
+    __syncthreads();
+    const int B = gridDim.x;
+    double* pr = part + (size_t)r * BK_MAX * 2 * BMDOT_BLOCKS;       // [quantity][block]
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        double s = 0.0;
+        for (int u = 0; u < RED_THREADS / 32; ++u) s += sh[q][u];
+        pr[(size_t)q * B + blockIdx.x] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (!grid_last_block(counters + (size_t)r * BK_MAX * CROW)) return;
+    __threadfence();
+    for (int q = warp; q < nq; q += RED_THREADS / 32) {
+        double s = 0.0;
+        for (int b = lane; b < B; b += 32) s += __ldcg(pr + (size_t)q * B + b);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) tot[q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    BGcr& G = g[r];
+    double proj = 0.0;
+    for (int j = 0; j < k; ++j) {
+        const double nn = G.nrm[j], dr = tot[4 + 2 * j], di = tot[5 + 2 * j];
+        const double cr = nn > 0 ? dr / nn : 0.0, ci = nn > 0 ? di / nn : 0.0;
+        G.coef[j][0] = cr; G.coef[j][1] = ci;
+        G.C[k][j][0] = cr; G.C[k][j][1] = ci;
+        if (nn > 0) proj += (dr * dr + di * di) / nn;
+    }
+    const double wp = tot[0] - proj;
+    const bool ok = wp > BSTEP_BREAK * tot[0];
+    const double ar = ok ? tot[1] / wp : 0.0, ai = ok ? tot[2] / wp : 0.0;
+    const double rn = ok ? tot[3] - (tot[1] * tot[1] + tot[2] * tot[2]) / wp : tot[3];
+    G.nrm[k] = ok ? wp : 0.0;
+    G.alpha[0] = ar; G.alpha[1] = ai;
+    G.A[k][0] = ar; G.A[k][1] = ai;
+    G.rr2 = rn;
+    steps[r] = k + 1;
+    iters[r] += 1;
+    if (!ok || rn <= tol2 * ref2[r] || iters[r] >= maxit) done[r] = 1;
+}
+
+static void launch_bstep_dots(dim3 grid, float2* const* W, const float2* w, const float2* res, long long n, int k,
+                              double* part, unsigned* counters, BGcr* g, int* steps, int* done, const double* ref2,
+                              double tol2, int* iters, int maxit, cudaStream_t st) {
+#define DWF_BSTEP(KM) k_bstep_dots<KM><<<grid, RED_THREADS, 0, st>>>(W, w, res, n, k, part, counters, g, steps, done, \
+                                                                     ref2, tol2, iters, maxit)
+    if (k <= 4)       DWF_BSTEP(4);
+    else if (k <= 8)  DWF_BSTEP(8);
+    else if (k <= 16) DWF_BSTEP(16);
+    else              DWF_BSTEP(32);
+#undef DWF_BSTEP
+}
+
+// The element-wise pass of the step: w' = w - sum_{j<k} coef_j W_j (stored in
+// place) and rout = rin - alpha w'.  Rows whose solve ended at this step skip.
+__global__ void __launch_bounds__(RED_THREADS) k_bstep_update(float2* __restrict__ w, float2* const* __restrict__ W,
+                                                              const BGcr* g, int k, const float2* __restrict__ rin,
+                                                              float2* __restrict__ rout, long long n,
+                                                              const int* skip) {
+    const int r = blockIdx.y;
+    if (skip[r]) return;
+    __shared__ float2 c[BK_MAX];
+    __shared__ const float4* Wp[BK_MAX];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        c[j] = make_float2((float)g[r].coef[j][0], (float)g[r].coef[j][1]);
+        Wp[j] = reinterpret_cast<const float4*>(W[j] + r * n);
+    }
+    __syncthreads();
+    const float2 al = make_float2((float)g[r].alpha[0], (float)g[r].alpha[1]);
+    float4* w4 = reinterpret_cast<float4*>(w + r * n);
+    const float4* a4 = reinterpret_cast<const float4*>(rin + r * n);
+    float4* o4 = reinterpret_cast<float4*>(rout + r * n);
+    ROW_LOOP(i, n >> 1) {
+        float4 wi = w4[i];
+        const float4 ri0 = a4[i];
+        int j = 0;
+        for (; j + 3 < k; j += 4) {
+            const float4 b0 = Wp[j][i], b1 = Wp[j + 1][i], b2 = Wp[j + 2][i], b3 = Wp[j + 3][i];
+            csub4(wi, b0, c[j]); csub4(wi, b1, c[j + 1]); csub4(wi, b2, c[j + 2]); csub4(wi, b3, c[j + 3]);
+        }
+        for (; j < k; ++j) csub4(wi, Wp[j][i], c[j]);
+        if (k > 0) w4[i] = wi;
+        float4 ri = ri0;
+        csub4(ri, wi, al);
+        o4[i] = ri;
+    }
+}
+
 // y of the deferred solution update for the first m steps: (I + C)^T y = A,
 // y_j = A_j - sum_{k>j} C[k][j] y_k (one thread, FP64)
 __device__ __forceinline__ void back_substitute(const BGcr& g, int m, float2* y) {
@@ -707,10 +855,19 @@ static dwf_status bcoarse_cycle(BSolver& s) {
             DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.Zc[k], v.ct, h->mf, false, v.cdone, s.st));
             DWF_TRY(coarse_apply_multi_tc(h, s.nrhs, v.ct, v.Wc[k], 1.0, true, v.cdone, s.st));
         }
-        DWF_TRY(borthogonalise(s, v.cgcr, v.Wc, k, v.Zc[k], n, v.dptr + 5 * BK_MAX, v.csteps, v.cdone));
-        k_bres_update<<<rg, RED_THREADS, 0, s.st>>>(v.Zc[k], k + 1 < KC ? v.Zc[k + 1] : v.crr, v.Wc[k], v.cgcr, n,
-                                                    v.red, v.cdone, v.cdone, v.cref2, tol2, v.citers,
-                                                    h->prm.coarse_maxiter);
+        float2* rnext = k + 1 < KC ? v.Zc[k + 1] : v.crr;
+        if (h->prm.cgs_passes == 1) {
+            // one reduction pass and one element-wise pass per step
+            const dim3 dg((unsigned)(rg.x < BSTEP_BLOCKS ? rg.x : BSTEP_BLOCKS), (unsigned)s.nrhs);
+            launch_bstep_dots(dg, v.dptr + 5 * BK_MAX, v.Wc[k], v.Zc[k], n, k, v.mpart, v.mcount, v.cgcr, v.csteps,
+                              v.cdone, v.cref2, tol2, v.citers, h->prm.coarse_maxiter, s.st);
+            k_bstep_update<<<eg, RED_THREADS, 0, s.st>>>(v.Wc[k], v.dptr + 5 * BK_MAX, v.cgcr, k, v.Zc[k], rnext, n,
+                                                         v.cdone);
+        } else {
+            DWF_TRY(borthogonalise(s, v.cgcr, v.Wc, k, v.Zc[k], n, v.dptr + 5 * BK_MAX, v.csteps, v.cdone));
+            k_bres_update<<<rg, RED_THREADS, 0, s.st>>>(v.Zc[k], rnext, v.Wc[k], v.cgcr, n, v.red, v.cdone, v.cdone,
+                                                        v.cref2, tol2, v.citers, h->prm.coarse_maxiter);
+        }
         DWF_CHECK_LAUNCH();
     }
     k_bcombine32<<<eg, RED_THREADS, 0, s.st>>>(v.ec, v.dptr + 4 * BK_MAX, v.cgcr, v.csteps, 0, n, nullptr, nullptr,

@@ -139,7 +139,8 @@ def test_coarse_operator_and_transfers_match_oracle(dw, Ls, Ls_c):
 
 @pytest.mark.parametrize("dims,Ls,sigma,mset", [((16, 16), 8, 0.3, -0.08), ((32, 32), 8, 0.5, -0.19),
                                                  ((24, 16), 6, 0.5, -0.19)])
-@pytest.mark.parametrize("coarse", [{"coarse_solver": 1}, {"coarse_solver": 1, "coarse_persistent": 2},
+@pytest.mark.parametrize("coarse", [{"coarse_solver": 1}, {"coarse_solver": 1, "cgs_passes": 2},
+                                    {"coarse_solver": 1, "coarse_persistent": 2},
                                     {"coarse_solver": 0, "coarse_persistent": 1},
                                     {"coarse_solver": 0, "coarse_persistent": 0}])
 def test_mg_solve_reaches_tolerance(dw, dims, Ls, sigma, mset, coarse):
