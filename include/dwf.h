@@ -350,13 +350,16 @@ typedef struct {
                              right-hand side's coarse solve                                  */
     int coarse_tc;        /* form of the many-right-hand-side coarse contraction: 0 (default) =
                              autotuned -- the first use for a given nrhs times mma.sync with 1, 2
-                             and 4 column tiles per warp and, with FP16 blocks and >= 128
-                             columns, the two tcgen05 forms (accumulator in tensor memory), and
-                             keeps the fastest; 1 = the persistent warp-specialised tcgen05
-                             form wherever eligible (mma.sync with 4 tiles elsewhere); 2, 3, 4
-                             = mma.sync with 1, 2, 4 column tiles per warp; 5 = tcgen05 with
-                             one (site, column tile) per thread block (fixed forms, for testing
-                             each one)                                                         */
+                             and 4 column tiles per warp and, with FP16 blocks, the tcgen05 forms
+                             (accumulator in tensor memory; the one with the data operand in
+                             tensor memory from 64 columns, the two with both operands in shared
+                             memory from 128), and keeps the fastest; 1 = the persistent
+                             warp-specialised tcgen05 form wherever
+                             eligible (mma.sync with 4 tiles elsewhere); 2, 3, 4 = mma.sync with
+                             1, 2, 4 column tiles per warp; 5 = tcgen05 with one (site, column
+                             tile) per thread block; 6 = the tcgen05 form with the data
+                             operand in tensor memory wherever eligible (fixed forms, for
+                             testing each one)                                                 */
     int transfer;         /* 0 (default): the truncated wall transfer of Eq. TruncProjectInterpolate;
                              1: the bulk transfer the paper compares it with (Sec. 4.1), P^dag /
                              P on every slice, which needs Ls_c = Ls                           */
@@ -468,10 +471,33 @@ DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, d
 DWF_API dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
                                          int dagger, void* stream);
 
+/* Layouts of a block of nrhs coarse vectors (complex64; column c = rhs * Ls_c + s;
+ * the 16 dof of one (column, coarse site) pair are contiguous):
+ *   DWF_COARSE_SLICE_MAJOR  [rhs][s][site][dof]: the vectors back to back (the
+ *                           layout of mg_coarse_apply_multi and of the batched
+ *                           solver);
+ *   DWF_COARSE_SITE_MAJOR   [site][rhs][s][dof]: all columns of one coarse site
+ *                           in one contiguous run (nrhs * Ls_c * 128 bytes), so
+ *                           the contraction reads each neighbour's columns as
+ *                           one stream instead of one 128-byte row per column. */
+enum { DWF_COARSE_SLICE_MAJOR = 0, DWF_COARSE_SITE_MAJOR = 1 };
+
+/* mg_coarse_apply_multi on vectors in the given layout (Eq. coarsenDW, the same
+ * operator and arithmetic).  The autotuner keeps one choice per (nrhs, layout).
+ * in and out: distinct, 16-byte aligned device buffers of nrhs coarse vectors.
+ * Errors: DWF_ERR_ARG for an unknown layout, NULL, misaligned or aliased
+ * buffers or nrhs < 1; DWF_ERR_UNSUPPORTED off 2-d / 16 dof. */
+DWF_API dwf_status mg_coarse_apply_multi_layout(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
+                                                int dagger, int layout, void* stream);
+
 /* The form the autotuner chose for nrhs right-hand sides: 1, 2 or 4 (mma.sync
- * with that many 8-column tiles per warp) or 256 (tcgen05); 0 before the first
- * tuned call for that nrhs. */
+ * with that many 8-column tiles per warp), 256 (tcgen05, one (site, column
+ * tile) per thread block), 257 (persistent warp-specialised tcgen05) or 258
+ * (tcgen05 with the data operand in tensor memory); 0
+ * before the first tuned call for that nrhs.  _layout: the choice for vectors
+ * in that layout. */
 DWF_API int mg_coarse_tc_form(const dwf_mg* h, int nrhs);
+DWF_API int mg_coarse_tc_form_layout(const dwf_mg* h, int nrhs, int layout);
 
 /* Batched K-cycle: nrhs right-hand sides that share the hierarchy h (one
  * gauge field) solved together (the multi-right-hand-side form of the solve

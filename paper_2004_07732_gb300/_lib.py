@@ -136,6 +136,8 @@ def _setup_signatures(L):
         "mg_coarse_solve": [_VP, _VP, _VP, _D, _I, ctypes.POINTER(ctypes.c_int), _VP],
         "mg_coarse_apply_multi": [_VP, _I, _VP, _VP, _D, _I, _VP],
         "mg_coarse_tc_form": [_VP, _I],
+        "mg_coarse_apply_multi_layout": [_VP, _I, _VP, _VP, _D, _I, _I, _VP],
+        "mg_coarse_tc_form_layout": [_VP, _I, _I],
         "mg_add_level": [_VP, ctypes.POINTER(LevelParams), _VP, _VP, _VP],
         "mg_level_geom": [_VP, G, ctypes.POINTER(ctypes.c_int)],
         "mg_level_get": [_VP, _I, _VP, _VP],
@@ -664,19 +666,24 @@ def mg_coarse_apply(mg: Multigrid, vin, vout, mf, dagger=False, stream=None):
     return vout
 
 
-def mg_coarse_apply_multi(mg: Multigrid, vin, vout, nrhs, mf, dagger=False, stream=None):
-    """Tensor-core coarse operator on nrhs coarse vectors stored back to back."""
+COARSE_LAYOUTS = {"slice_major": 0, "site_major": 1}
+
+
+def mg_coarse_apply_multi(mg: Multigrid, vin, vout, nrhs, mf, dagger=False, stream=None, layout="slice_major"):
+    """Tensor-core coarse operator on nrhs coarse vectors: stored back to back ("slice_major",
+    [rhs][s][site][dof]) or with all columns of a coarse site together ("site_major",
+    [site][rhs][s][dof])."""
     for t in (vin, vout):
         if t.dtype != torch.complex64 or t.numel() != nrhs * mg.coarse_size or not t.is_cuda:
             raise ValueError("coarse vectors must be complex64 CUDA tensors of nrhs x the coarse size")
-    check(lib().mg_coarse_apply_multi(mg.ptr, int(nrhs), _ptr(vin), _ptr(vout), float(mf), int(bool(dagger)),
-                                      _stream(stream)))
+    check(lib().mg_coarse_apply_multi_layout(mg.ptr, int(nrhs), _ptr(vin), _ptr(vout), float(mf),
+                                             int(bool(dagger)), COARSE_LAYOUTS[layout], _stream(stream)))
     return vout
 
 
-def mg_coarse_tc_form(mg: Multigrid, nrhs) -> int:
+def mg_coarse_tc_form(mg: Multigrid, nrhs, layout="slice_major") -> int:
     """Form of the coarse contraction the autotuner chose for nrhs (0: not tuned yet)."""
-    return int(lib().mg_coarse_tc_form(mg.ptr, int(nrhs)))
+    return int(lib().mg_coarse_tc_form_layout(mg.ptr, int(nrhs), COARSE_LAYOUTS[layout]))
 
 
 # ---------------------------------------------------------------------------

@@ -106,7 +106,8 @@ struct dwf_mg {
     cudaStream_t cap_stream;              // private stream used only to record graphs
     void* batched;                        // workspace and graphs of the batched solver (mg_batched.cu)
     void* lvl3;                           // third level and coarsest deflation (mg_level3.cu), or nullptr
-    mutable std::map<int, int> tc_choice; // autotuned form of the many-right-hand-side coarse contraction, by nrhs
+    mutable std::map<int, int> tc_choice; // autotuned form of the many-right-hand-side coarse contraction, by
+                                          // nrhs (slice-major vectors) or -nrhs (site-major vectors)
 };
 
 namespace dwf {
@@ -118,15 +119,17 @@ dwf_status mg_alloc(dwf_mg* h, void** p, size_t bytes);
 dwf_status coarse_dwf_apply(const dwf_mg* h, const float2* in, float2* out, double mf, bool dagger,
                             const int* skip, cudaStream_t st);
 dwf_status build_adjoint_blocks(dwf_mg* h, cudaStream_t st);
-// tensor-core coarse stencil on nrhs right-hand sides ([rhs][s][site][dof]);
-// skip_rhs: per right-hand-side device flags (may be null)
+// tensor-core coarse stencil on nrhs right-hand sides, vectors in `layout`
+// (DWF_COARSE_SLICE_MAJOR: [rhs][s][site][dof]; DWF_COARSE_SITE_MAJOR:
+// [site][rhs][s][dof]); skip_rhs: per right-hand-side device flags (may be null)
 dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
-                                 const int* skip_rhs, cudaStream_t st);
+                                 const int* skip_rhs, cudaStream_t st, int layout = DWF_COARSE_SLICE_MAJOR);
 // Autotuner of that contraction: times every eligible form (mma.sync with 1, 2 or 4
 // column tiles of 8 per warp; tcgen05 with FP16 blocks from 128 columns) on in -> out
 // (scratch: contents are overwritten) and keeps the fastest for nrhs.  Synchronises
-// `st`; must not run during stream capture.  No-op once nrhs is tuned.
-dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* out, cudaStream_t st);
+// `st`; must not run during stream capture.  No-op once (nrhs, layout) is tuned.
+dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* out, cudaStream_t st,
+                          int layout = DWF_COARSE_SLICE_MAJOR);
 // one-time kernel attributes of the coarse stencil (outside any stream capture)
 dwf_status coarse_init_attributes();
 // Wall transfers (Eq. TruncProjectInterpolate) on nrhs vectors stored back to

@@ -9,9 +9,14 @@
 // FP32.  Operands are FP32 data split into TF32 high and low parts (three
 // products per term: hi*hi + hi*lo + lo*hi), which keeps FP32-level accuracy.
 // The adjoint uses gamma_5-hermiticity, Dhat_W^dag = sigma_3 Dhat_W sigma_3.
-// Vectors: [rhs][s][coarse site][16] complex64; blocks: the FP32 column-major
-// Galerkin blocks.  With FP16 blocks, at least 128 columns and coarse_tc = 1
-// the contraction runs on tcgen05 instead (k_coarse_umma below).
+// Vectors: the 16 complex64 values of one (column, coarse site) pair are
+// contiguous; pair (c, x) starts at c * cs + x * ss complex values.  Two
+// layouts: slice-major [rhs][s][coarse site][16] (cs = Vc * 16, ss = 16; the
+// batched solver's) and site-major [coarse site][rhs][s][16] (cs = 16,
+// ss = ncols * 16), where the 128 columns of one site are one contiguous
+// 16 KB run.  Blocks: the FP32 column-major Galerkin blocks.  With FP16
+// blocks, at least 128 columns and coarse_tc = 1 the contraction runs on
+// tcgen05 instead (k_coarse_umma below).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -28,6 +33,7 @@ struct TcParams {
     int Ls_c, nrhs, ncols;
     float mf;
     int dag;
+    long long cs, ss;     // complex values between columns and between coarse sites
 };
 
 __device__ __forceinline__ long long nbr2d(const TcParams& p, long long xc, int dir) {
@@ -63,15 +69,13 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const BT* __restrict__ Y, 
     const int cg = (int)(wid % ngroup);
     if (xc >= p.Vc) return;
     const int g = lane >> 2, t = lane & 3;
-    const long long slice = p.Vc * 16;                   // one slice of one right-hand side
-    const long long rhs_stride = slice * p.Ls_c;
     long long baseB[NT];
     bool okB[NT];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
         const int col = (cg * NT + k) * 8 + g;           // B column owned by this lane in tile k
         okB[k] = col < p.ncols && !(skip_rhs && skip_rhs[col / p.Ls_c]);
-        baseB[k] = okB[k] ? (long long)(col / p.Ls_c) * rhs_stride + (long long)(col % p.Ls_c) * slice : 0;
+        baseB[k] = okB[k] ? (long long)col * p.cs : 0;
     }
     bool any = false;
 #pragma unroll
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const BT* __restrict__ Y, 
                 // B fragments: b0 = k-row t, b1 = k-row t + 4 of column g
                 float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
                 if (okB[k]) {
-                    const float2* src = in + baseB[k] + nb * 16 + 8 * half + t;
+                    const float2* src = in + baseB[k] + nb * p.ss + 8 * half + t;
                     v0 = __ldg(src);
                     v1 = __ldg(src + 4);
                 }
@@ -152,16 +156,15 @@ __global__ void __launch_bounds__(256, 2) k_coarse_tc(const BT* __restrict__ Y, 
                 if (col >= p.ncols) continue;
                 const int r = col / p.Ls_c, s = col % p.Ls_c;
                 if (skip_rhs && skip_rhs[r]) continue;
-                const long long rb = (long long)r * rhs_stride;
+                const long long rb = (long long)r * p.Ls_c * p.cs + xc * p.ss + i;
                 const float hr = so * acc[k][0][2 * h + w], hi = so * acc[k][1][2 * h + w];
-                const float2 self = __ldg(in + rb + (long long)s * slice + xc * 16 + i);
+                const float2 self = __ldg(in + rb + (long long)s * p.cs);
                 int sh;
                 float sc = 1.f;
                 if (from_below) { if (s > 0) sh = s - 1; else { sh = p.Ls_c - 1; sc = -p.mf; } }
                 else            { if (s < p.Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
-                const float2 hv = __ldg(in + rb + (long long)sh * slice + xc * 16 + i);
-                out[rb + (long long)s * slice + xc * 16 + i] =
-                    make_float2(hr + self.x + sc * hv.x, hi + self.y + sc * hv.y);
+                const float2 hv = __ldg(in + rb + (long long)sh * p.cs);
+                out[rb + (long long)s * p.cs] = make_float2(hr + self.x + sc * hv.x, hi + self.y + sc * hv.y);
             }
         }
 }
@@ -228,12 +231,10 @@ __device__ __forceinline__ void um_load_a(float4 (&v)[4], const float2* __restri
                                           int col0, const int* skip_rhs) {
     const int t = threadIdx.x, m = t >> 1, jh = t & 1;
     const int col = col0 + m;
-    const long long slice = p.Vc * 16, rhs_stride = slice * p.Ls_c;
     bool ok = col < p.ncols;
     if (ok && skip_rhs) ok = skip_rhs[col / p.Ls_c] == 0;
     if (ok) {
-        const float4* src = reinterpret_cast<const float4*>(in + (long long)(col / p.Ls_c) * rhs_stride +
-                                                            (long long)(col % p.Ls_c) * slice + nb * 16 + 8 * jh);
+        const float4* src = reinterpret_cast<const float4*>(in + (long long)col * p.cs + nb * p.ss + 8 * jh);
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = __ldg(src + q);
     } else {
@@ -371,8 +372,7 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
         if (live && skip_rhs) live = skip_rhs[col / p.Ls_c] == 0;
         if (live) {
             const int rr = col / p.Ls_c, s = col % p.Ls_c;
-            const long long slice = p.Vc * 16;
-            const long long rb = (long long)rr * slice * p.Ls_c;
+            const long long rb = (long long)rr * p.Ls_c * p.cs + xc * p.ss;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const float so = (p.dag && i >= 8) ? -1.f : 1.f;
@@ -381,9 +381,9 @@ __global__ void __launch_bounds__(UM_THREADS) k_coarse_umma(const __half2* __res
                 float sc = 1.f;
                 if (from_below) { if (s > 0) sh = s - 1; else { sh = p.Ls_c - 1; sc = -p.mf; } }
                 else            { if (s < p.Ls_c - 1) sh = s + 1; else { sh = 0; sc = -p.mf; } }
-                const float2 self = __ldg(in + rb + (long long)s * slice + xc * 16 + i);
-                const float2 hv = __ldg(in + rb + (long long)sh * slice + xc * 16 + i);
-                out[rb + (long long)s * slice + xc * 16 + i] =
+                const float2 self = __ldg(in + rb + (long long)s * p.cs + i);
+                const float2 hv = __ldg(in + rb + (long long)sh * p.cs + i);
+                out[rb + (long long)s * p.cs + i] =
                     make_float2(so * __uint_as_float(r[i]) + self.x + sc * hv.x,
                                 so * __uint_as_float(r[16 + i]) + self.y + sc * hv.y);
             }
@@ -502,8 +502,8 @@ __device__ __forceinline__ uint64_t sw_desc(const void* base) {
 }
 
 // Inputs of one tile at one site as one tensor copy.  The tensor map views the input vectors
-// as 3-d FP32 data (k, column, site) with strides (4 B, one column, 128 B), k = 2 j + (0: Re,
-// 1: Im) of input component j, column = rhs Ls_c + s; the box (32, 128, 1) of columns
+// as 3-d FP32 data (k, column, site) with strides (4 B, cs, ss), k = 2 j + (0: Re, 1: Im) of
+// input component j, column = rhs Ls_c + s; the box (32, 128, 1) of columns
 // 128 t .. 128 t + 127 at site nb lands in shared memory as 128 rows of 128 bytes with the
 // 128-byte swizzle, the layout of operand A.  Columns past the last one are filled with zeros.
 __device__ __forceinline__ void up_tma(float* dst, unsigned long long* bar, const CUtensorMap* tmap, int tile,
@@ -640,7 +640,6 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_coarse_umma_p(const __half2* 
         // ---------------- epilogue ----------------
         const int te = t - UP_PROD;                  // row of the accumulator = column of the tile
         const int wq = warp & 3;                     // TMEM lanes 32 wq .. 32 wq + 31
-        const long long slice = p.Vc * 16;
         long long eissued = 0, elanded = 0;          // own-input copies issued (te == 0) and waited for
         auto item_tma = [&](long long il) {
             const long long item = item_of(il);
@@ -724,8 +723,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_coarse_umma_p(const __half2* 
                     const int mm = (te >> 3) + 16 * i;
                     const int c = tile * UM_M + mm;
                     if (c < p.ncols && !(skip_rhs && skip_rhs[c / p.Ls_c])) {
-                        float4* o4 = reinterpret_cast<float4*>(out + (long long)(c / p.Ls_c) * slice * p.Ls_c +
-                                                               (long long)(c % p.Ls_c) * slice + xc * 16);
+                        float4* o4 = reinterpret_cast<float4*>(out + (long long)c * p.cs + xc * p.ss);
                         o4[q] = *reinterpret_cast<const float4*>(&sm.o[mm * UP_OROW + 4 * q]);
                     }
                 }
@@ -777,17 +775,308 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_coarse_umma_p(const __half2* 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UP_TMEM_COLS) : "memory");
 }
 
+
+// ---------------------------------------------------------------------------
+// tcgen05 form with the data operand in tensor memory.
+//
+// Same transposed contraction as above (rows c: 128 columns of a tile; per
+// direction K = 32 real values in the (Re v_j, Im v_j) order of memory; the
+// weights B[n][k] the real form of the FP16 block with the sigma_3 signs of the
+// adjoint folded in).  The shared-memory-fed forms above keep both parts of A
+// in shared memory, where the tensor core reads them for each K step and a
+// producer pass reads the high part again to write the low part; with N = 32
+// the A operand dominates their shared-memory traffic.  Here the tensor core
+// reads A from tensor memory: per (item, direction) stage one tensor copy
+// (TMA, 128-byte swizzle) lands the tile's 128 column rows in a ring slot of
+// the group; each thread of the 4-warp group reads its row (conflict-free
+// thanks to the swizzle), splits it into TF32 high and low parts and writes
+// both into tensor memory (tcgen05.st); one thread of the group issues the 8
+// MMAs (tcgen05.mma kind::tf32, A from tensor memory, B from shared memory).
+// The row's own inputs (the last of the five stages) stay in registers for the
+// epilogue: identity and s-hops (the s-hop partner column lies in the same
+// warp, Ls_c | 32) plus the accumulator read back with tcgen05.ld, stored as
+// whole 128-byte rows.
+//
+// Three groups per CTA, one CTA per SM (persistent; CTA items
+// item = blockIdx.x + il gridDim.x, group q takes il = q, q + 3, ...).  Per
+// group: a ring of UT_RING input slots (the copy of stage g + 2 is issued when
+// stage g starts: its slot was read by every thread of the group before the
+// barrier that ended stage g - 1), two tensor-memory A slots (hi 32 + lo 32
+// columns; stage g waits for the MMAs of stage g - 2 through the slot's
+// `empty` mbarrier) and a 32-column accumulator (`full`: the item's MMAs are
+// done; then the epilogue, then the next item's weights).  All waits are
+// bounded; a timeout sets the status word and an abort flag, each group leaves
+// its loop together (bar.red votes), its copy issuer waits (bounded) for the
+// copies in flight and its MMA issuer for its MMAs before the tensor memory is
+// freed.
+// ---------------------------------------------------------------------------
+constexpr int UT_GCOLS = 160;                 // 2 x (hi 32 + lo 32) + accumulator 32
+constexpr int UT_TMEM_COLS = 512;
+constexpr int UT_YPT = UM_DIRS * 256 / 128;   // FP16 block entries per thread per item
+
+// NG groups of 128 threads; RING input slots per group (copies RING - 1 stages ahead).  Measured
+// at 64^2 x 4 coarse sites and 64 right-hand sides: 3 groups x 3 slots 194 us, 2 groups x 5 slots
+// 244 us (the number of groups working at once counts, not how far the copies run ahead)
+constexpr int UT_NG = 3, UT_NR = 3;
+template <int NG, int RING>
+struct UtSmem {
+    float in[NG][RING][UM_M * UM_K];            // swizzled input rows (1024-byte aligned slots)
+    float w[NG][UM_DIRS][UM_N * UM_K];          // weights of the group's current item
+    unsigned long long tma[NG][RING], empty[NG][2], full[NG], done[NG];
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ bool ut_wait(int* abort_flag, unsigned long long* bar, unsigned parity, int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int*)abort_flag) return false;
+            if (now_ns() - t0 > UM_WAIT_NS) {
+                *(volatile int*)abort_flag = 1;
+                atomicExch(status, 3);
+                return false;
+            }
+        }
+    }
+}
+// named barrier 1 + q over the 128 threads of group q; ut_all: the AND of v over them
+__device__ __forceinline__ void ut_sync(int q) { asm volatile("bar.sync %0, 128;" ::"r"(1 + q) : "memory"); }
+__device__ __forceinline__ bool ut_all(int q, bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, r;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred r, %2, 128, p;\n\t"
+                 "selp.u32 %0, 1, 0, r;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v), "r"(1 + q) : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void um_mma_ta(uint32_t dt, uint32_t at, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+                 ::"r"(dt), "r"(at), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void tm_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+// direction of stage d: the four hops first, the site itself last (its inputs stay in registers
+// for the epilogue)
+__device__ __forceinline__ int ut_dir(int d) { return d < 4 ? d + 1 : 0; }
+
+template <int UT_GROUPS, int UT_RING>
+__global__ void __maxnreg__(128) k_coarse_umma_t(const __half2* __restrict__ Y,
+                                                                     float2* __restrict__ out, TcParams p,
+                                                                     const int* __restrict__ skip_rhs, int* status,
+                                                                     const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(1024) unsigned char ut_raw[];
+    UtSmem<UT_GROUPS, UT_RING>& sm = *reinterpret_cast<UtSmem<UT_GROUPS, UT_RING>*>(ut_raw);
+    const int t = threadIdx.x, warp = t >> 5, q = warp >> 2, tr = t & 127;
+    if (t == 0) {
+        for (int g = 0; g < UT_GROUPS; ++g) {
+            for (int r = 0; r < UT_RING; ++r) mbar_init(&sm.tma[g][r], 1);
+            mbar_init(&sm.empty[g][0], 1);
+            mbar_init(&sm.empty[g][1], 1);
+            mbar_init(&sm.full[g], 1);
+            mbar_init(&sm.done[g], 1);
+        }
+        // the swizzled copies need 1024-byte aligned slots
+        sm.abort = (smem_u32(sm.in) & 1023u) != 0;
+        if (sm.abort) atomicExch(status, 3);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(UT_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tq = sm.tmem + (uint32_t)(q * UT_GCOLS);              // group's columns, lane 0
+    const uint32_t tl = tq + ((uint32_t)(32 * (warp & 3)) << 16);        // this warp's lanes
+    const int ntile = (p.ncols + UM_M - 1) / UM_M;
+    const int nitems = (int)(p.Vc * ntile);
+    const int ncta = (blockIdx.x < nitems && !sm.abort) ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nli = ncta > q ? (ncta - 1 - q) / UT_GROUPS + 1 : 0;      // this group's items
+    const long long G = (long long)nli * UM_DIRS;                        // and stages
+    auto item_of = [&](int li) { return (int)blockIdx.x + (q + UT_GROUPS * li) * (int)gridDim.x; };
+    // D F32, A and B TF32, K-major, N = 32, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UM_N >> 3) << 17) |
+                           ((uint32_t)(UM_M >> 4) << 24);
+    long long issued = 0, landed = 0;          // copies issued by thread tr == 0 and waited for
+
+    auto copy_stage = [&](long long g) {       // thread tr == 0
+        const int item = item_of((int)(g / UM_DIRS));
+        const int d = (int)(g % UM_DIRS), r = (int)(g % UT_RING);
+        up_tma(sm.in[q][r], &sm.tma[q][r], &tmap, item % ntile, nbr2d(p, item / ntile, ut_dir(d)));
+        issued = g + 1;
+    };
+    __half2 yv[UT_YPT];
+    auto load_y = [&](int li) {
+        const long long xc = item_of(li) / ntile;
+#pragma unroll
+        for (int k = 0; k < UT_YPT; ++k) {
+            const int e = tr + 128 * k, d = e >> 8;
+            yv[k] = __ldg(Y + (xc * UM_DIRS + ut_dir(d)) * 256 + (e & 255));
+        }
+    };
+
+    auto stage = [&](long long g) -> bool {
+        if (tr == 0 && g + UT_RING - 1 < G) copy_stage(g + UT_RING - 1);
+        const int li = (int)(g / UM_DIRS), d = (int)(g % UM_DIRS), s = (int)(g & 1), r = (int)(g % UT_RING);
+        bool ok = ut_wait(&sm.abort, &sm.tma[q][r], (unsigned)((g / UT_RING) & 1), status);
+        if (g >= 2)                                          // the MMAs of stage g - 2 have read A slot s
+            ok = ok && ut_wait(&sm.abort, &sm.empty[q][s], (unsigned)(((g - 2) >> 1) & 1), status);
+        if (!ut_all(q, ok)) return false;
+        if (tr == 0) landed = g + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float4 cur[8];                                       // this row's 32 K values
+        {
+            const float* row = sm.in[q][r];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cur[c] = *reinterpret_cast<const float4*>(&row[sw_off(tr, 4 * c)]);
+        }
+        if (d == 0) {
+            // weights of item li (the MMAs of item li - 1, which read them, are done: its epilogue
+            // waited for them): B[n][k], k = 2 j (Re v_j), 2 j + 1 (Im v_j); n < 16: Re out_n,
+            // n = 16 + i: Im out_i; sigma_3 Y sigma_3 for the adjoint
+#pragma unroll
+            for (int k = 0; k < UT_YPT; ++k) {
+                const int e = tr + 128 * k, dd = e >> 8, j = (e >> 4) & 15, i = e & 15;
+                float2 y = __half22float2(yv[k]);
+                if (p.dag && ((i >= 8) != (j >= 8))) { y.x = -y.x; y.y = -y.y; }
+                float* bd = sm.w[q][dd];
+                bd[um_off(i, 2 * j)] = y.x;
+                bd[um_off(i, 2 * j + 1)] = -y.y;
+                bd[um_off(16 + i, 2 * j)] = y.y;
+                bd[um_off(16 + i, 2 * j + 1)] = y.x;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (li + 1 < nli) load_y(li + 1);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {                       // K values 8 c .. 8 c + 7
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 v4 = cur[2 * c + (u >> 2)];
+                const float x = (u & 3) == 0 ? v4.x : (u & 3) == 1 ? v4.y : (u & 3) == 2 ? v4.z : v4.w;
+                hi[u] = __float_as_uint(x) & 0xffffe000u;
+                lo[u] = __float_as_uint(x - __uint_as_float(hi[u]));
+            }
+            tm_st8(tl + (uint32_t)(64 * s + 8 * c), hi);
+            tm_st8(tl + (uint32_t)(64 * s + 32 + 8 * c), lo);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        ut_sync(q);                                          // also: every thread has read input slot r
+        if (tr == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < UM_K / 8; ++ks) {
+                const uint64_t db = um_desc(reinterpret_cast<const char*>(sm.w[q][d]) + ks * 2 * UM_LBO);
+                const uint32_t ah = tq + (uint32_t)(64 * s + 8 * ks), al = ah + 32u;
+                um_mma_ta(tq + 128u, ah, db, idesc, (d > 0 || ks > 0) ? 1u : 0u);
+                um_mma_ta(tq + 128u, al, db, idesc, 1u);
+            }
+            um_commit(&sm.empty[q][s]);
+            if (d == UM_DIRS - 1) um_commit(&sm.full[q]);
+        }
+        if (d == UM_DIRS - 1) {
+            // epilogue of item li: cur holds the site's own inputs
+            ok = ut_wait(&sm.abort, &sm.full[q], (unsigned)(li & 1), status);
+            if (!ut_all(q, ok)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int item = item_of(li);
+            const long long xc = item / ntile;
+            const int col = (item % ntile) * UM_M + tr;
+            const int sl = col % p.Ls_c, lane = tr & 31;
+            int pl[2];
+            float sc[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {                // components 8 h .. 8 h + 7 share one s-hop
+                const bool from_below = p.dag ? (h == 1) : (h == 0);
+                int sh;
+                sc[h] = 1.f;
+                if (from_below) { if (sl > 0) sh = sl - 1; else { sh = p.Ls_c - 1; sc[h] = -p.mf; } }
+                else            { if (sl < p.Ls_c - 1) sh = sl + 1; else { sh = 0; sc[h] = -p.mf; } }
+                pl[h] = lane - sl + sh;
+            }
+            bool live = col < p.ncols;
+            if (live && skip_rhs) live = skip_rhs[col / p.Ls_c] == 0;
+            float4* o4 = reinterpret_cast<float4*>(out + (long long)(live ? col : 0) * p.cs + xc * p.ss);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {                // output components 8 h .. 8 h + 7
+                uint32_t re[8], im[8];
+                tm_ld8(tl + 128u + (uint32_t)(8 * h), re);
+                tm_ld8(tl + 128u + (uint32_t)(16 + 8 * h), im);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int k = 4 * h + kk;
+                    const float4 a = cur[k];
+                    float4 v;
+                    v.x = __shfl_sync(0xffffffffu, a.x, pl[h]);
+                    v.y = __shfl_sync(0xffffffffu, a.y, pl[h]);
+                    v.z = __shfl_sync(0xffffffffu, a.z, pl[h]);
+                    v.w = __shfl_sync(0xffffffffu, a.w, pl[h]);
+                    const float4 res = make_float4(__uint_as_float(re[2 * kk]) + a.x + sc[h] * v.x,
+                                                   __uint_as_float(im[2 * kk]) + a.y + sc[h] * v.y,
+                                                   __uint_as_float(re[2 * kk + 1]) + a.z + sc[h] * v.z,
+                                                   __uint_as_float(im[2 * kk + 1]) + a.w + sc[h] * v.w);
+                    if (live) o4[k] = res;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        return true;
+    };
+
+    if (tr == 0)
+        for (long long g = 0; g < UT_RING - 1 && g < G; ++g) copy_stage(g);
+    if (G > 0) load_y(0);
+    for (long long g = 0; g < G; ++g)
+        if (!stage(g)) break;
+    if (tr == 0) {
+        // copies still in flight after an early exit land before the CTA ends
+        for (long long g = landed; g < issued; ++g) up_drain(&sm.tma[q][g % UT_RING], (unsigned)((g / UT_RING) & 1));
+        // every MMA this group issued has finished before the tensor memory is released
+        if (G > 0) {
+            um_commit(&sm.done[q]);
+            up_drain(&sm.done[q], 0u);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem), "r"(UT_TMEM_COLS) : "memory");
+}
+
 }  // namespace
 
 // forms of the contraction: 1, 2, 4 = mma.sync with that many column tiles per warp; TC_UMMA = tcgen05,
 // one item per CTA; TC_UMMA_P = tcgen05, persistent and warp-specialised
 constexpr int TC_UMMA = 0x100;
 constexpr int TC_UMMA_P = 0x101;
+constexpr int TC_UMMA_T = 0x102;
 
 static bool umma_eligible(const dwf_mg* h, int ncols) { return h->ytile_half && ncols >= UM_M; }
 // the persistent form's epilogue finds each column's s-hop partner in the same 128-column tile
 // (Ls_c divides 128)
 static bool umma_p_eligible(const dwf_mg* h, int ncols) { return umma_eligible(h, ncols) && UM_M % h->mg.Ls_c == 0; }
+// the tensor-memory-operand form's epilogue takes the s-hop partner column from a lane of the same
+// warp (Ls_c divides 32); partial tiles are fine (their rows are independent), so it starts at 64
+// columns
+static bool umma_t_eligible(const dwf_mg* h, int ncols) {
+    return h->ytile_half && ncols >= UM_M / 2 && 32 % h->mg.Ls_c == 0;
+}
 
 // cuTensorMapEncodeTiled from the driver, looked up once
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -807,9 +1096,8 @@ static dwf_status input_tensor_map(CUtensorMap* tm, const float2* in, const TcPa
     auto enc = tensor_map_encoder();
     if (!enc) { set_error("cuTensorMapEncodeTiled is not available from the driver"); return DWF_ERR_CUDA; }
     if ((reinterpret_cast<uintptr_t>(in) & 15u) != 0) { set_error("coarse vectors must be 16-byte aligned"); return DWF_ERR_ARG; }
-    const cuuint64_t col_bytes = (cuuint64_t)p.Vc * 16 * sizeof(float2);
     const cuuint64_t dims[3] = {32, (cuuint64_t)p.ncols, (cuuint64_t)p.Vc};
-    const cuuint64_t strides[2] = {col_bytes, 16 * sizeof(float2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)p.cs * sizeof(float2), (cuuint64_t)p.ss * sizeof(float2)};
     const cuuint32_t box[3] = {32, (cuuint32_t)UM_M, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(in), dims, strides, box, estr,
@@ -821,6 +1109,33 @@ static dwf_status input_tensor_map(CUtensorMap* tm, const float2* in, const TcPa
 
 static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, const float2* in, float2* out,
                               const int* skip_rhs, cudaStream_t st) {
+    if (form == TC_UMMA_T) {
+        static unsigned long long attr_set = 0;      // per device
+        static int sms_of[64] = {0};
+        int dev = 0;
+        DWF_CHECK_CUDA(cudaGetDevice(&dev));
+        if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
+            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma_t<UT_NG, UT_NR>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)sizeof(UtSmem<UT_NG, UT_NR>)));
+            if (dev < 64) {
+                DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev));
+                attr_set |= 1ull << dev;
+            }
+        }
+        int sms = dev < 64 ? sms_of[dev] : 0;
+        if (sms <= 0) DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long nitems = p.Vc * ((p.ncols + UM_M - 1) / UM_M);
+        if (nitems > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
+        const long long grid = nitems < sms ? nitems : sms;
+        if (grid < 1) return DWF_OK;
+        alignas(64) CUtensorMap tm;
+        DWF_TRY(input_tensor_map(&tm, in, p));
+        k_coarse_umma_t<UT_NG, UT_NR><<<(unsigned)grid, 128 * UT_NG, sizeof(UtSmem<UT_NG, UT_NR>), st>>>(
+            (const __half2*)h->Ytile, out, p, skip_rhs, h->status + 1, tm);
+        DWF_CHECK_LAUNCH();
+        return DWF_OK;
+    }
     if (form == TC_UMMA_P) {
         static unsigned long long attr_set = 0;      // per device
         static int sms_of[64] = {0};
@@ -877,7 +1192,7 @@ static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, cons
     return DWF_OK;
 }
 
-static TcParams tc_params(const dwf_mg* h, int nrhs, double mf, bool dagger) {
+static TcParams tc_params(const dwf_mg* h, int nrhs, double mf, bool dagger, int layout) {
     TcParams p;
     p.Vc = h->mg.Vc;
     p.Lc0 = h->mg.Lc[0];
@@ -887,17 +1202,23 @@ static TcParams tc_params(const dwf_mg* h, int nrhs, double mf, bool dagger) {
     p.ncols = nrhs * h->mg.Ls_c;
     p.mf = (float)mf;
     p.dag = dagger ? 1 : 0;
+    if (layout == DWF_COARSE_SITE_MAJOR) { p.cs = 16; p.ss = (long long)p.ncols * 16; }
+    else { p.cs = p.Vc * 16; p.ss = 16; }
     return p;
 }
 
-dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* out, cudaStream_t st) {
+// autotuner key: nrhs for the slice-major layout, -nrhs for the site-major one
+static int tc_key(int nrhs, int layout) { return layout == DWF_COARSE_SITE_MAJOR ? -nrhs : nrhs; }
+
+dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* out, cudaStream_t st, int layout) {
     if (h->mg.nd != 2 || h->mg.ncd != 16 || nrhs < 1) return DWF_OK;
-    if (h->tc_choice.count(nrhs)) return DWF_OK;
-    const TcParams p = tc_params(h, nrhs, h->mf, false);
-    int forms[5] = {1, 2, 4, 0, 0};
+    if (h->tc_choice.count(tc_key(nrhs, layout))) return DWF_OK;
+    const TcParams p = tc_params(h, nrhs, h->mf, false, layout);
+    int forms[6] = {1, 2, 4, 0, 0, 0};
     int nforms = 3;
     if (umma_eligible(h, p.ncols)) forms[nforms++] = TC_UMMA;
     if (umma_p_eligible(h, p.ncols)) forms[nforms++] = TC_UMMA_P;
+    if (umma_t_eligible(h, p.ncols)) forms[nforms++] = TC_UMMA_T;
     cudaEvent_t a, b;
     DWF_CHECK_CUDA(cudaEventCreate(&a));
     DWF_CHECK_CUDA(cudaEventCreate(&b));
@@ -917,24 +1238,25 @@ dwf_status coarse_tc_tune(const dwf_mg* h, int nrhs, const float2* in, float2* o
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (status == DWF_OK) h->tc_choice[nrhs] = best;
+    if (status == DWF_OK) h->tc_choice[tc_key(nrhs, layout)] = best;
     return status;
 }
 
 dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, float2* out, double mf, bool dagger,
-                                 const int* skip_rhs, cudaStream_t st) {
+                                 const int* skip_rhs, cudaStream_t st, int layout) {
     if (h->mg.nd != 2 || h->mg.ncd != 16) {
         set_error("the tensor-core coarse stencil supports 2-d lattices with 16 coarse dof");
         return DWF_ERR_UNSUPPORTED;
     }
-    const TcParams p = tc_params(h, nrhs, mf, dagger);
+    const TcParams p = tc_params(h, nrhs, mf, dagger, layout);
     int form = 4;
-    if (h->prm.coarse_tc == 1 && umma_p_eligible(h, p.ncols)) form = TC_UMMA_P;
+    if (h->prm.coarse_tc == 6 && umma_t_eligible(h, p.ncols)) form = TC_UMMA_T;
+    else if (h->prm.coarse_tc == 1 && umma_p_eligible(h, p.ncols)) form = TC_UMMA_P;
     else if (h->prm.coarse_tc == 1 && umma_eligible(h, p.ncols)) form = TC_UMMA;
     else if (h->prm.coarse_tc == 5 && umma_eligible(h, p.ncols)) form = TC_UMMA;
     else if (h->prm.coarse_tc >= 2 && h->prm.coarse_tc <= 4) form = h->prm.coarse_tc == 2 ? 1 : h->prm.coarse_tc == 3 ? 2 : 4;
     else if (h->prm.coarse_tc == 0) {
-        auto it = h->tc_choice.find(nrhs);
+        auto it = h->tc_choice.find(tc_key(nrhs, layout));
         if (it != h->tc_choice.end()) form = it->second;
     }
     return launch_form(h, form, p, in, out, skip_rhs, st);
@@ -944,20 +1266,35 @@ dwf_status coarse_apply_multi_tc(const dwf_mg* h, int nrhs, const float2* in, fl
 
 using namespace dwf;
 
-extern "C" dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf, int dagger,
-                                            void* stream) {
+extern "C" dwf_status mg_coarse_apply_multi_layout(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
+                                                   int dagger, int layout, void* stream) {
     clear_error();
     if (!h || !in || !out) { set_error("NULL argument"); return DWF_ERR_ARG; }
     if (nrhs < 1) { set_error("nrhs must be >= 1"); return DWF_ERR_ARG; }
     if (in == out) { set_error("in and out must be distinct buffers"); return DWF_ERR_ARG; }
+    if (layout != DWF_COARSE_SLICE_MAJOR && layout != DWF_COARSE_SITE_MAJOR) {
+        set_error("unknown coarse vector layout %d", layout);
+        return DWF_ERR_ARG;
+    }
+    if (!aligned16(in) || !aligned16(out)) { set_error("coarse vectors must be 16-byte aligned"); return DWF_ERR_ARG; }
     cudaStream_t st = as_stream(stream);
-    // the first call for a new nrhs picks the fastest form of the contraction (using in / out as scratch)
-    if (h->prm.coarse_tc == 0) DWF_TRY(coarse_tc_tune(h, nrhs, (const float2*)in, (float2*)out, st));
-    return coarse_apply_multi_tc(h, nrhs, (const float2*)in, (float2*)out, mf, dagger != 0, nullptr, st);
+    // the first call for a new (nrhs, layout) picks the fastest form of the contraction (using in / out
+    // as scratch)
+    if (h->prm.coarse_tc == 0) DWF_TRY(coarse_tc_tune(h, nrhs, (const float2*)in, (float2*)out, st, layout));
+    return coarse_apply_multi_tc(h, nrhs, (const float2*)in, (float2*)out, mf, dagger != 0, nullptr, st, layout);
+}
+
+extern "C" dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf, int dagger,
+                                            void* stream) {
+    return mg_coarse_apply_multi_layout(h, nrhs, in, out, mf, dagger, DWF_COARSE_SLICE_MAJOR, stream);
+}
+
+extern "C" int mg_coarse_tc_form_layout(const dwf_mg* h, int nrhs, int layout) {
+    if (!h) return 0;
+    auto it = h->tc_choice.find(tc_key(nrhs, layout));
+    return it == h->tc_choice.end() ? 0 : it->second;
 }
 
 extern "C" int mg_coarse_tc_form(const dwf_mg* h, int nrhs) {
-    if (!h) return 0;
-    auto it = h->tc_choice.find(nrhs);
-    return it == h->tc_choice.end() ? 0 : it->second;
+    return mg_coarse_tc_form_layout(h, nrhs, DWF_COARSE_SLICE_MAJOR);
 }

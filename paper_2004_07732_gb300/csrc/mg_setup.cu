@@ -638,7 +638,7 @@ dwf_status mg_setup(const dwf_geom* g, const void* U, double M5, double mf, cons
         set_error("fine_prec must be one of the FP32 precisions"); return DWF_ERR_ARG;
     }
     if (prm.cgs_passes != 1 && prm.cgs_passes != 2) { set_error("cgs_passes must be 1 or 2"); return DWF_ERR_ARG; }
-    if (prm.coarse_tc < 0 || prm.coarse_tc > 5) { set_error("coarse_tc must be in [0, 5]"); return DWF_ERR_ARG; }
+    if (prm.coarse_tc < 0 || prm.coarse_tc > 6) { set_error("coarse_tc must be in [0, 6]"); return DWF_ERR_ARG; }
     if (prm.coarse_block_prec != DWF_F32 && prm.coarse_block_prec != DWF_F32_L16) {
         set_error("coarse_block_prec must be DWF_F32 or DWF_F32_L16"); return DWF_ERR_ARG;
     }

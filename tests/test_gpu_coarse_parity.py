@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 NRHS = (1, 7, 32, 33, 34, 64)
 FORMS = {0: "autotuned", 1: "tcgen05 persistent", 2: "mma.sync x1", 3: "mma.sync x2", 4: "mma.sync x4",
-         5: "tcgen05 per item"}
+         5: "tcgen05 per item", 6: "tcgen05, A in tensor memory"}
 
 
 @pytest.fixture(scope="module")
@@ -99,23 +99,40 @@ def test_tile_stencil_fp16_blocks_match_oracle(dw, case2d):
     h.close()
 
 
+def _to_site_major(v, Ls_c, Vc):
+    """[rhs][s][site][dof] -> [site][rhs][s][dof]"""
+    nrhs = v.shape[0]
+    return np.ascontiguousarray(v.reshape(nrhs, Ls_c, Vc, 16).transpose(2, 0, 1, 3))
+
+
+def _from_site_major(v, nrhs, Ls_c, Vc):
+    return np.ascontiguousarray(v.reshape(Vc, nrhs, Ls_c, 16).transpose(1, 2, 0, 3)).reshape(nrhs, -1)
+
+
+@pytest.mark.parametrize("layout", ["slice_major", "site_major"])
 @pytest.mark.parametrize("tc", sorted(FORMS))
-def test_multi_rhs_contraction_forms_match_oracle(dw, case2d, tc):
+def test_multi_rhs_contraction_forms_match_oracle(dw, case2d, tc, layout):
     """Every form of the many-right-hand-side contraction at nrhs = 1, 7, 32, 33, 64, both
-    operators (m_f and m = 1) and both daggers.  tcgen05 runs from 128 columns (32 right-hand
-    sides x 4 slices; 33 and 34 leave a partial tile); below 128 columns coarse_tc = 1 and 5 fall
-    back to mma.sync."""
+    operators (m_f and m = 1) and both daggers, on both vector layouts.  tcgen05 runs from 128
+    columns (32 right-hand sides x 4 slices; 33 and 34 leave a partial tile); below 128 columns
+    coarse_tc = 1 and 5 fall back to mma.sync; the tensor-memory-operand form (coarse_tc = 6) runs from 64 columns."""
     c = case2d
     h = c.setup(dw, tc)
+    Vc = int(np.prod(c.cdims))
     for nrhs in NRHS:
-        vd = _dev(c.v[:nrhs], torch.complex64).reshape(nrhs, c.nc)
+        v = c.v[:nrhs]
+        if layout == "site_major":
+            v = _to_site_major(v, c.Ls_c, Vc)
+        vd = _dev(v, torch.complex64)
         out = torch.full_like(vd, float("nan"))
         for (m, dag), want in c.want.items():
-            dw.mg_coarse_apply_multi(h, vd, out, nrhs, m, dagger=dag)
-            _check(out.cpu().numpy(), want[:nrhs], (FORMS[tc], nrhs, m, dag))
-        form = dw.mg_coarse_tc_form(h, nrhs)
+            dw.mg_coarse_apply_multi(h, vd, out, nrhs, m, dagger=dag, layout=layout)
+            got = out.cpu().numpy()
+            got = _from_site_major(got, nrhs, c.Ls_c, Vc) if layout == "site_major" else got.reshape(nrhs, c.nc)
+            _check(got, want[:nrhs], (FORMS[tc], layout, nrhs, m, dag))
+        form = dw.mg_coarse_tc_form(h, nrhs, layout=layout)
         if tc == 0:
-            assert form in (1, 2, 4, 256, 257)
+            assert form in (1, 2, 4, 256, 257, 258)
     h.close()
 
 
