@@ -427,3 +427,16 @@ def pv_poly_operator(Ddw, Dpv, coeffs):
         P = P + c * Nk
         Nk = (Nk @ N).tocsr()
     return (Dpvd @ P @ Ddw).tocsr()
+
+
+def pv_poly_apply(Ddw, Dpv, coeffs, psi):
+    """The operator of pv_poly_operator applied to the vector psi by matrix-vector
+    products only (no matrix powers): y = D_DW psi, z = p(N) y with N = D_PV D_PV^dag
+    by Horner's rule (z = c_K y, then z = c_k y + N z for k = K-1 .. 0), and
+    D_PV^dag z.  Same mathematics in another order of the products."""
+    Dpvd = dagger(Dpv)
+    y = Ddw @ psi
+    z = coeffs[-1] * y
+    for c in reversed(coeffs[:-1]):
+        z = c * y + Dpv @ (Dpvd @ z)
+    return Dpvd @ z

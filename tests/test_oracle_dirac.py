@@ -341,3 +341,30 @@ def test_pv_poly_operator_limits():
     got = dirac.pv_poly_operator(Dd, Dp, coeffs).toarray()
     want = np.linalg.solve(Dp.toarray(), Dd.toarray())
     assert np.abs(got - want).max() < 1e-6 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("coeffs", [(1.0,), (2.0, -1.0), (3.0, -3.0, 1.0), (0.5, 0.25, -0.125, 2.0)])
+def test_pv_poly_apply_is_the_operator_on_a_vector(coeffs):
+    """The matrix-vector (Horner) form gives the assembled polynomial operator times the vector;
+    with the Cayley-Hamilton coefficients of a tiny lattice it gives D_PV^-1 D_DW psi."""
+    dims, Ls, m = (4, 4), 4, 0.05
+    U = _rand_u1(dims, 0.5, 11)
+    Dd = dirac.dwf_matrix(U, dims, Ls, 1.0, m)
+    Dp = dirac.pv_matrix(U, dims, Ls, 1.0)
+    psi = np.random.default_rng(3).standard_normal(Dd.shape[0]) * (1 + 0.5j)
+    want = dirac.pv_poly_operator(Dd, Dp, coeffs) @ psi
+    got = dirac.pv_poly_apply(Dd, Dp, coeffs, psi)
+    assert np.linalg.norm(got - want) < 1e-13 * np.linalg.norm(want)
+    dims, Ls = (2, 2), 2
+    U = _rand_u1(dims, 0.5, 9)
+    Dd = dirac.dwf_matrix(U, dims, Ls, 1.0, m)
+    Dp = dirac.pv_matrix(U, dims, Ls, 1.0)
+    N = (Dp @ dirac.dagger(Dp)).toarray()
+    ch = np.poly(N)
+    n = N.shape[0]
+    ck = [-ch[n - 1 - k] / ch[n] for k in range(n - 1)] + [-1.0 / ch[n]]
+    x = np.random.default_rng(4).standard_normal(n) + 0j
+    exact = np.linalg.solve(Dp.toarray(), Dd.toarray() @ x)
+    # the Cayley-Hamilton coefficients are large and alternate, so rounding in either order of the
+    # products leaves ~1e-6 of the result
+    assert np.linalg.norm(dirac.pv_poly_apply(Dd, Dp, ck, x) - exact) < 1e-5 * np.linalg.norm(exact)
