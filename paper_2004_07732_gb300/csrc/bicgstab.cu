@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bs_rho(const C* __restrict__ rt
         re += a.x * b.x + a.y * b.y;
         im += a.x * b.y - a.y * b.x;
     }
-    double v[2] = {(double)re, (double)im};
-    grid_reduce<2>(v, rs, [=] __device__(double* t) {
+    const A v[2] = {re, im};
+    grid_reduce_any<2>(v, rs, [=] __device__(double* t) {
         const double2 rho1 = make_double2(t[0], t[1]);
         if (S->rho0.x == 0.0 && S->rho0.y == 0.0) { S->breakdown = 1; S->beta = make_double2(0.0, 0.0); }
         else S->beta = zdiv(zmul(S->alpha, rho1), S->rho0);
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bs_alpha(const C* __restrict__ 
         re += a.x * b.x + a.y * b.y;
         im += a.x * b.y - a.y * b.x;
     }
-    double v[2] = {(double)re, (double)im};
-    grid_reduce<2>(v, rs, [=] __device__(double* t) {
+    const A v[2] = {re, im};
+    grid_reduce_any<2>(v, rs, [=] __device__(double* t) {
         const double2 gam = make_double2(t[0], t[1]);
         if (gam.x == 0.0 && gam.y == 0.0) { S->breakdown = 1; S->alpha = make_double2(0.0, 0.0); }
         else S->alpha = zdiv(S->rho0, gam);
@@ -156,10 +156,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_bs_proj(VecSet R, int j, long l
                 im[i] += a.x * b.y - a.y * b.x;
             }
     }
-    double v[2 * JM];
+    A v[2 * JM];
 #pragma unroll
-    for (int i = 0; i < JM; ++i) { v[2 * i] = (double)re[i]; v[2 * i + 1] = (double)im[i]; }
-    grid_reduce<2 * JM>(v, rs, [=] __device__(double* t) {
+    for (int i = 0; i < JM; ++i) { v[2 * i] = re[i]; v[2 * i + 1] = im[i]; }
+    grid_reduce_any<2 * JM>(v, rs, [=] __device__(double* t) {
         for (int i = 1; i < j; ++i) {
             const double s = S->sigma[i];
             S->tau[i][j] = s > 0.0 ? make_double2(t[2 * (i - 1)] / s, t[2 * (i - 1) + 1] / s) : make_double2(0.0, 0.0);
@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bs_gs(VecSet R, int j, long lon
         gr += b.x * a.x + b.y * a.y;
         gi += b.x * a.y - b.y * a.x;
     }
-    double v[3] = {(double)s2, (double)gr, (double)gi};
-    grid_reduce<3>(v, rs, [=] __device__(double* t) {
+    const A v[3] = {s2, gr, gi};
+    grid_reduce_any<3>(v, rs, [=] __device__(double* t) {
         S->sigma[j] = t[0];
         if (t[0] > 0.0) S->gp[j] = make_double2(t[1] / t[0], t[2] / t[0]);
         else { S->gp[j] = make_double2(0.0, 0.0); S->breakdown = 1; }
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bs_mr(VecSet R, VecSet U, C* __
         r0[e] = r; u0[e] = u; x[e] = xx;
         acc += r.x * r.x + r.y * r.y;
     }
-    double v[1] = {(double)acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) { S->rr2 = t[0]; });
+    const A v[1] = {acc};
+    grid_reduce_any<1>(v, rs, [=] __device__(double* t) { S->rr2 = t[0]; });
 }
 
 // inner start: r_0 = rt = f (copied by the host), u_0 = 0, x = 0; scalars rho0 = alpha = omega = 1
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bs_norm(const C* __restrict__ a
     using A = typename Acc<C>::T;
     A acc = 0;
     BS_LOOP(i) { const C z = a[i]; acc += z.x * z.x + z.y * z.y; }
-    double v[1] = {(double)acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) { *out = t[0]; });
+    const A v[1] = {acc};
+    grid_reduce_any<1>(v, rs, [=] __device__(double* t) { *out = t[0]; });
 }
 
 template <class C>

@@ -74,6 +74,39 @@ __device__ __forceinline__ void block_sum(double (&v)[N]) {
     }
 }
 
+// Block-wide sum of FP32 per-thread partials: the tree over each warp in FP32
+// (five shuffle-adds in a fixed order), the per-warp sums in FP64 (thread q < N
+// adds quantity q over the warps in order); every thread ends with the totals.
+// GB300 runs FP64 at a small fraction of its FP32 rate, and a tree of FP64
+// shuffle-adds per thread and quantity made the many-quantity solver
+// reductions FP64-bound.
+template <int N>
+__device__ __forceinline__ void block_sum_f(const float (&vin)[N], double (&v)[N]) {
+    __shared__ double sh[N][RED_THREADS / 32];
+    __shared__ double tot[N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float f[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        f[k] = vin[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f[k] += __shfl_down_sync(0xffffffffu, f[k], off);
+    }
+    __syncthreads();                                  // the shared arrays may be in use from a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[k][warp] = (double)f[k];
+    __syncthreads();
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        double s = 0.0;
+        for (int u = 0; u < RED_THREADS / 32; ++u) s += sh[k][u];
+        tot[k] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = tot[k];
+}
+
 // Completion counters: RED_GROUPS group counters and one top counter, each
 // on its own 128-byte line, so that the blocks of a grid do not all contend
 // for one address (a single counter serialised ~1000 atomics per reduction).
@@ -102,6 +135,42 @@ __device__ __forceinline__ bool grid_last_block(unsigned* counters) {
     return last;
 }
 
+// Sum over the blocks of a grid, in the grid's last block: quantity k of block
+// b at part[k * stride + b].  Warp w sums quantities w, w + 8, ...: lane l adds
+// blocks l, l + 32, ... in FP64, then a fixed FP64 shuffle tree.  Every thread
+// of the block ends with the totals.
+template <int N>
+__device__ __forceinline__ void grid_final_sum(const double* part, size_t stride, double (&v)[N]) {
+    __shared__ double tot[N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < N; k += RED_THREADS / 32) {
+        double s = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)k * stride + b);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) tot[k] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = tot[k];
+}
+
+// grid_reduce for FP32 per-thread partials: block_sum_f, then grid_final_sum.
+template <int N, class Fin>
+__device__ __forceinline__ void grid_reduce_f(const float (&vf)[N], RedScratch rs, Fin fin) {
+    double v[N];
+    block_sum_f<N>(vf, v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) rs.partials[k * RED_BLOCKS + blockIdx.x] = v[k];
+    }
+    if (!grid_last_block(rs.counter)) return;
+    __threadfence();
+    double w[N];
+    grid_final_sum<N>(rs.partials, RED_BLOCKS, w);
+    if (threadIdx.x == 0) fin(w);
+}
+
 // Grid-wide reduction with a finaliser fin(double* totals) run by one thread.
 template <int N, class Fin>
 __device__ __forceinline__ void grid_reduce(double (&v)[N], RedScratch rs, Fin fin) {
@@ -113,13 +182,22 @@ __device__ __forceinline__ void grid_reduce(double (&v)[N], RedScratch rs, Fin f
     if (!grid_last_block(rs.counter)) return;
     __threadfence();
     double w[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        w[k] = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) w[k] += __ldcg(rs.partials + k * RED_BLOCKS + b);
-    }
-    block_sum<N>(w);
+    grid_final_sum<N>(rs.partials, RED_BLOCKS, w);
     if (threadIdx.x == 0) fin(w);
+}
+
+// Either reduction by the type of the per-thread partials: FP32 partials take
+// grid_reduce_f, FP64 partials (FP64 data) keep every sum in FP64.
+template <int N, class Fin>
+__device__ __forceinline__ void grid_reduce_any(const float (&v)[N], RedScratch rs, Fin fin) {
+    grid_reduce_f<N>(v, rs, fin);
+}
+template <int N, class Fin>
+__device__ __forceinline__ void grid_reduce_any(const double (&v)[N], RedScratch rs, Fin fin) {
+    double w[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = v[k];
+    grid_reduce<N>(w, rs, fin);
 }
 
 // <x, y> over n complex values into out[0..1] (device).  FP64 data, or exact =

@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bnorm2_32(const float2* __restr
     const float4* a = reinterpret_cast<const float4*>(x + r * n);
     float acc = 0.f;
     ROW_LOOP(i, n >> 1) { const float4 u = a[i]; acc += u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w; }
-    double v[1] = {acc};
-    grid_reduce<1>(v, row_scratch(rs, r), [=] __device__(double* t) { out[r] = t[0]; });
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, row_scratch(rs, r), [=] __device__(double* t) { out[r] = t[0]; });
 }
 
 // rout = rin - alpha w, rr2 = |rout|^2 per right-hand side (rout may be rin).
@@ -194,8 +194,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bres_update(const float2* rin, 
         o4[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
     }
-    double v[1] = {acc};
-    grid_reduce<1>(v, row_scratch(rs, r), [=] __device__(double* t) {
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, row_scratch(rs, r), [=] __device__(double* t) {
         g[r].rr2 = t[0];
         if (done) {
             iters[r] += 1;
@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmdot_rows(float2* const* __res
         cdot4(a0, b0, re, im); cdot4(a1, b1, re, im); cdot4(a2, b2, re, im); cdot4(a3, b3, re, im);
     }
     for (; i < n2; i += stride) cdot4(Wj[i], w4[i], re, im);
-    double v[2] = {re, im};
-    block_sum<2>(v);
+    const float vf[2] = {re, im};
+    double v[2];
+    block_sum_f<2>(vf, v);
     const size_t rowi = (size_t)r * BK_MAX + j;
     double* pr = part + rowi * 2 * BMDOT_BLOCKS;
     if (threadIdx.x == 0) {
@@ -234,12 +235,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmdot_rows(float2* const* __res
     }
     if (!grid_last_block(counters + rowi * CROW)) return;
     __threadfence();
-    double w2[2] = {0.0, 0.0};
-    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
-        w2[0] += __ldcg(pr + bb);
-        w2[1] += __ldcg(pr + BMDOT_BLOCKS + bb);
-    }
-    block_sum<2>(w2);
+    double w2[2];
+    grid_final_sum<2>(pr, BMDOT_BLOCKS, w2);
     if (threadIdx.x == 0) {
         const double nn = g[r].nrm[j];
         const double cr = nn > 0 ? w2[0] / nn : 0.0, ci = nn > 0 ? w2[1] / nn : 0.0;
@@ -281,10 +278,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmdot(float2* const* __restrict
 #pragma unroll
     for (int j0 = 0; j0 < KM; j0 += 4) {
         if (j0 >= k) break;                                       // block-uniform
-        double v[8];
+        float vf[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { v[2 * q] = re[j0 + q]; v[2 * q + 1] = im[j0 + q]; }
-        block_sum<8>(v);
+        for (int q = 0; q < 4; ++q) { vf[2 * q] = re[j0 + q]; vf[2 * q + 1] = im[j0 + q]; }
+        double v[8];
+        block_sum_f<8>(vf, v);
         if (threadIdx.x == 0)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -295,16 +293,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmdot(float2* const* __restrict
     }
     if (!grid_last_block(counters + (size_t)r * BK_MAX * CROW)) return;
     __threadfence();
-    for (int j = 0; j < k; ++j) {
-        double w2[2] = {0.0, 0.0};
-        for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
-            w2[0] += __ldcg(pr + (size_t)j * 2 * BMDOT_BLOCKS + bb);
-            w2[1] += __ldcg(pr + (size_t)j * 2 * BMDOT_BLOCKS + BMDOT_BLOCKS + bb);
+    // quantity q = 2 j + (0: Re, 1: Im) of block b at pr[q * BMDOT_BLOCKS + b]; warp w sums q = w, w + 8, ...
+    __shared__ double tot[2 * KM];
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int q = warp; q < 2 * k; q += RED_THREADS / 32) {
+            double sq = 0.0;
+            for (unsigned bb = lane; bb < gridDim.x; bb += 32) sq += __ldcg(pr + (size_t)q * BMDOT_BLOCKS + bb);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+            if (lane == 0) tot[q] = sq;
         }
-        block_sum<2>(w2);
+    }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
         if (threadIdx.x == 0) {
             const double nn = g[r].nrm[j];
-            const double cr = nn > 0 ? w2[0] / nn : 0.0, ci = nn > 0 ? w2[1] / nn : 0.0;
+            const double cr = nn > 0 ? tot[2 * j] / nn : 0.0, ci = nn > 0 ? tot[2 * j + 1] / nn : 0.0;
             g[r].coef[j][0] = cr;
             g[r].coef[j][1] = ci;
             g[r].C[k][j][0] = first ? cr : g[r].C[k][j][0] + cr;
@@ -354,8 +359,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bmaxpy(float2* __restrict__ w, 
         }
     }
     if (FINAL) {
-        double v[3] = {f0, f1, f2};
-        grid_reduce<3>(v, row_scratch(rs, r), [=] __device__(double* t) {
+        const float v[3] = {f0, f1, f2};
+        grid_reduce_f<3>(v, row_scratch(rs, r), [=] __device__(double* t) {
             const double ar = t[0] > 0 ? t[1] / t[0] : 0.0, ai = t[0] > 0 ? t[2] / t[0] : 0.0;
             g[r].nrm[k] = t[0];
             g[r].alpha[0] = ar; g[r].alpha[1] = ai;
@@ -411,7 +416,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bstep_dots(float2* const* __res
     }
     const int nq = 2 * k + 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double v[NQ];
+    // the tree over each warp in FP32, every sum across warps and blocks in FP64
+    float v[NQ];
     v[0] = ww; v[1] = wr; v[2] = wi; v[3] = rr;
 #pragma unroll
     for (int j = 0; j < KM; ++j) { v[4 + 2 * j] = re[j]; v[5 + 2 * j] = im[j]; }
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_bstep_dots(float2* const* __res
         if (q < nq) {                                             // block-uniform
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
-            if (lane == 0) sh[q][warp] = v[q];
+            if (lane == 0) sh[q][warp] = (double)v[q];
         }
     }
     __syncthreads();

@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_l3_mdot(Ptrs W, const float2* _
         re += u.x * v.x + u.y * v.y;
         im += u.x * v.y - u.y * v.x;
     }
-    double v2[2] = {re, im};
-    grid_reduce<2>(v2, row_rs(part, cnt, j), [=] __device__(double* t) { g->c[j][0] = t[0]; g->c[j][1] = t[1]; });
+    const float v2[2] = {re, im};
+    grid_reduce_f<2>(v2, row_rs(part, cnt, j), [=] __device__(double* t) { g->c[j][0] = t[0]; g->c[j][1] = t[1]; });
 }
 
 // w -= sum_{j<k} c_j W_j, z -= sum_{j<k} c_j Z_j; then inv = 1 / |w|, alpha = <w, r> / |w|^2
@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_l3_orth(Ptrs W, Ptrs Z, int k, 
         ar += a.x * ri.x + a.y * ri.y;
         ai += a.x * ri.y - a.y * ri.x;
     }
-    double v[3] = {nn, ar, ai};
-    grid_reduce<3>(v, rs, [=] __device__(double* t) {
+    const float v[3] = {nn, ar, ai};
+    grid_reduce_f<3>(v, rs, [=] __device__(double* t) {
         if (t[0] > 0.0) {
             g->inv = 1.0 / sqrt(t[0]);
             g->alpha[0] = t[1] / t[0];
@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_l3_upd(float2* __restrict__ w, 
         z[i] = make_float2(b.x * inv, b.y * inv);
         acc += ri.x * ri.x + ri.y * ri.y;
     }
-    double v[1] = {acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, rs, [=] __device__(double* t) {
         g->rr2 = t[0];
         g->steps += 1;
         if (t[0] <= g->ref2 || g->steps >= g->maxit) g->done = 1;
@@ -394,8 +394,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_l3_norm(const float2* __restric
                                                          double* out) {
     float acc = 0.f;
     L3_LOOP(i, n) { const float2 u = a[i]; acc += u.x * u.x + u.y * u.y; }
-    double v[1] = {acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) { *out = t[0]; });
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, rs, [=] __device__(double* t) { *out = t[0]; });
 }
 
 __global__ void k_l3_sub(float2* __restrict__ out, const float2* __restrict__ a, const float2* __restrict__ b,
@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg3_alpha(const float2* __restr
     if (S->done) return;
     float acc = 0.f;
     L3_LOOP(i, n) { const float2 u = q[i]; acc += u.x * u.x + u.y * u.y; }
-    double v[1] = {acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, rs, [=] __device__(double* t) {
         if (t[0] > 0.0) S->alpha = S->rn2 / t[0];
         else { S->alpha = 0.0; S->done = 1; }
     });
@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg3_upd1(float2* __restrict__ x
         x[i] = xi; rr[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y;
     }
-    double v[1] = {acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, rs, [=] __device__(double* t) {
         S->rr2 = t[0];
         S->iters += 1;
         if (t[0] <= S->tol2 * S->bn2 || S->iters >= S->maxit) S->done = 1;
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg3_upd2(float2* __restrict__ r
         r[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y;
     }
-    double v[1] = {acc};
-    grid_reduce<1>(v, rs, [=] __device__(double* t) {
+    const float v[1] = {acc};
+    grid_reduce_f<1>(v, rs, [=] __device__(double* t) {
         S->beta = S->rn2 > 0.0 ? t[0] / S->rn2 : 0.0;
         S->rn2 = t[0];
     });
@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg3_init(const float2* __restri
         a1 += v.x * v.x + v.y * v.y;
         a2 += w.x * w.x + w.y * w.y;
     }
-    double v[3] = {a0, a1, a2};
-    grid_reduce<3>(v, rs, [=] __device__(double* t) {
+    const float v[3] = {a0, a1, a2};
+    grid_reduce_f<3>(v, rs, [=] __device__(double* t) {
         S->rn2 = t[0]; S->rr2 = t[1]; S->bn2 = t[2]; S->tol2 = tol * tol;
         S->iters = 0; S->maxit = maxit;
         S->done = (t[2] == 0.0 || t[1] <= tol * tol * t[2] || maxit <= 0) ? 1 : 0;
