@@ -852,6 +852,52 @@ def time_coarse_multi(dw, dev, nrhs=64, reps=20):
             "per_vector_launches_ms": t_one * 1e3, "speedup": t_one / t_tc}
 
 
+def profile_solve(which):
+    """One MG solve inside the NVTX range "solve", for an ncu launch list (no JSON line): the
+    hierarchy is set up as in the timed legs, a warm call builds the workspaces and graphs, then
+    the solve runs.  which: "solve2d" (256^2 x 16), "solve4d" (16^3 x 32 x 16) or "batched256"
+    (the 21 sources of the 64-source batch's 256^2 class, one batched K-cycle)."""
+    import torch
+    import paper_2004_07732_gb300 as dw
+    dev = torch.device("cuda", 0)
+    if which == "solve4d":
+        wl = synth.SU3_16x32
+        U, srcs = wl.draw(1)
+        g = dw.make_geom(wl.dims, wl.Ls, group="su3")
+        nvec = 24
+        rng = synth.rng_for(wl.seed + 7000)
+        starts = np.stack([synth.gaussian_complex(rng, (wl.V * 12,)) for _ in range(nvec)])
+        params = {"nvec": nvec, "block": [2, 2, 2, 2], "setup_mass": SETUP_MASS_SU3, "post_smooth": 16,
+                  "coarse_tol": 0.4}
+        nrhs = 1
+    else:
+        if which == "batched256":
+            wl, nrhs = synth.batched_classes()[2]
+        else:
+            wl, nrhs = SOLVE_WL, 1
+        U, srcs = wl.draw(nrhs)
+        g = dw.make_geom(wl.dims, wl.Ls)
+        params = dw.mg_default_params()
+        params["setup_mass"] = SETUP_MASS[wl.sigma]
+        rng = synth.rng_for(wl.seed + 7000)
+        starts = np.stack([synth.gaussian_complex(rng, (wl.V * 2,)) for _ in range(params["nvec"])])
+    U64 = torch.from_numpy(U.reshape(-1)).to(dev)
+    b = torch.from_numpy(np.stack([x.reshape(-1) for x in srcs[:nrhs]]).reshape(-1)).to(dev)
+    mg = dw.mg_setup(g, U64, wl.M5, wl.mf, params, torch.from_numpy(starts.reshape(-1)).to(dev))
+    x = torch.empty_like(b)
+    dw.mg_solve_batched(mg, b, x, nrhs, tol=1e-10, maxiter=2, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push("solve")
+    t0 = time.perf_counter()
+    st, status = dw.mg_solve_batched(mg, b, x, nrhs, tol=1e-10, raise_noconv=False)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    dw.mg_destroy(mg)
+    print(json.dumps({"profile": which, "seconds": t, "status": status,
+                      "outer_iterations_max": max(s["iterations"] for s in st)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -865,7 +911,12 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-coarse", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--profile", choices=["solve2d", "solve4d", "batched256"], default=None,
+                    help="run one MG solve inside the NVTX range 'solve' for an ncu launch list, print no bench line")
     args = ap.parse_args()
+    if args.profile:
+        profile_solve(args.profile)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
