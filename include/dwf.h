@@ -462,12 +462,14 @@ DWF_API dwf_status mg_coarse_apply(const dwf_mg* h, const void* in, void* out, d
 /* The same coarse operator on nrhs right-hand sides at once, on the tensor
  * cores: in / out hold nrhs coarse vectors back to back ([rhs][s][site][dof],
  * complex64).  Per coarse site the stencil is a dense contraction over the
- * nrhs * Ls_c columns, evaluated with mma.sync TF32 products of FP32 data split
- * into high and low parts (FP32-level accuracy), FP32 accumulation.  The
- * blocks are the handle's coarse block storage (coarse_block_prec), as for
- * mg_coarse_apply.  With coarse_tc = 0 the first call for a new nrhs times the
- * candidate forms (using in and out as scratch, synchronising `stream`) and
- * keeps the fastest.  2-d, 16 coarse dof. */
+ * nrhs * Ls_c columns, evaluated on the tensor cores with TF32 products of
+ * FP32 data split into high and low parts (FP32-level accuracy) and FP32
+ * accumulation: tcgen05 (accumulator in tensor memory; the data operand in
+ * tensor memory or in shared memory) or mma.sync.  The blocks are the handle's
+ * coarse block storage (coarse_block_prec), as for mg_coarse_apply; the
+ * tcgen05 forms need FP16 blocks.  With coarse_tc = 0 the first call for a new
+ * nrhs times the candidate forms (using in and out as scratch, synchronising
+ * `stream`) and keeps the fastest.  2-d, 16 coarse dof. */
 DWF_API dwf_status mg_coarse_apply_multi(const dwf_mg* h, int nrhs, const void* in, void* out, double mf,
                                          int dagger, void* stream);
 

@@ -163,3 +163,17 @@ def test_coarse_48dof_fp16_matches_oracle_on_gpu_blocks(dw, Ls_c):
             dw.mg_coarse_apply(h, vd, out, m, dagger=dag)
             _check(out.cpu().numpy()[None, :], want[None, :], ("48dof", Ls_c, m, dag))
     h.close()
+
+
+def test_multi_rhs_contraction_rejects_unknown_layout(dw, case2d):
+    """mg_coarse_apply_multi_layout takes the two documented layouts only (DWF_ERR_ARG otherwise)."""
+    c = case2d
+    h = c.setup(dw, 0)
+    vd = _dev(c.v[:2], torch.complex64)
+    out = torch.empty_like(vd)
+    lib = dw.lib()
+    st = lib.mg_coarse_apply_multi_layout(h.ptr, 2, vd.data_ptr(), out.data_ptr(), 0.1, 0, 2, None)
+    assert st == 1                                    # DWF_ERR_ARG
+    st = lib.mg_coarse_apply_multi_layout(h.ptr, 2, vd.data_ptr(), vd.data_ptr(), 0.1, 0, 1, None)
+    assert st == 1                                    # in and out must be distinct
+    h.close()
