@@ -144,3 +144,47 @@ def test_autograd_rejects_a_hierarchy_of_other_links(dw):
     with pytest.raises(dw.DwfError, match="set up for"):
         dw.solve(th, b, g, M5, 2 * mf, tol=1e-10, mg=mg)
     mg.close()
+
+
+@pytest.mark.parametrize("checkpoint", ["host", "recompute"])
+def test_checkpoint_modes_give_the_same_gradients(dw, checkpoint):
+    """x kept on the host, or recomputed in backward, gives the gradients of the default (x on the
+    device): the solvers are deterministic, so the recomputed x is the forward's x."""
+    dims, Ls, M5, mf = (8, 8), 4, 1.0, 0.05
+    rng = synth.rng_for(41)
+    theta = synth.u1_angles(rng, dims, 0.5)
+    b = synth.gaussian_spinor(rng, dims, Ls).reshape(-1)
+    g = dw.make_geom(dims, Ls)
+    grads = {}
+    for mode in ("device", checkpoint):
+        th = _dev(theta, torch.float64).requires_grad_(True)
+        bd = _dev(b).requires_grad_(True)
+        x = dw.solve(th, bd, g, M5, mf, tol=1e-12, checkpoint=mode)
+        loss = (x.abs() ** 2).sum()
+        loss.backward()
+        grads[mode] = (loss.item(), th.grad.clone(), bd.grad.clone())
+    l0, t0, b0 = grads["device"]
+    l1, t1, b1 = grads[checkpoint]
+    assert l1 == l0
+    assert torch.equal(t1, t0) and torch.equal(b1, b0)
+    # 4-d SU(3) links
+    dims4, Ls4, M54 = (4, 4, 4, 4), 4, 1.8
+    U = synth.su3_links(rng, dims4, 0.3)
+    b4 = synth.gaussian_spinor(rng, dims4, Ls4, "su3").reshape(-1)
+    g4 = dw.make_geom(dims4, Ls4, group="su3")
+    out = {}
+    for mode in ("device", checkpoint):
+        Ud = _dev(U).requires_grad_(True)
+        bd = _dev(b4).requires_grad_(True)
+        x = dw.solve_links(Ud, bd, g4, M54, 0.05, tol=1e-12, checkpoint=mode)
+        (x.abs() ** 2).sum().backward()
+        out[mode] = (Ud.grad.clone(), bd.grad.clone())
+    assert torch.equal(out[checkpoint][0], out["device"][0]) and torch.equal(out[checkpoint][1], out["device"][1])
+
+
+def test_checkpoint_mode_is_checked(dw):
+    g = dw.make_geom((8, 8), 4)
+    th = torch.zeros(dw.link_size(g), dtype=torch.float64, device="cuda", requires_grad=True)
+    b = torch.ones(dw.spinor_size(g), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError):
+        dw.solve(th, b, g, 1.0, 0.05, checkpoint="disk")
