@@ -21,7 +21,7 @@ from oracle import dirac, mg as omg
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-NRHS = (1, 7, 32, 33, 34, 64)
+NRHS = (1, 7, 16, 32, 33, 34, 64)
 FORMS = {0: "autotuned", 1: "tcgen05 persistent", 2: "mma.sync x1", 3: "mma.sync x2", 4: "mma.sync x4",
          5: "tcgen05 per item", 6: "tcgen05, A in tensor memory"}
 
@@ -112,7 +112,7 @@ def _from_site_major(v, nrhs, Ls_c, Vc):
 @pytest.mark.parametrize("layout", ["slice_major", "site_major"])
 @pytest.mark.parametrize("tc", sorted(FORMS))
 def test_multi_rhs_contraction_forms_match_oracle(dw, case2d, tc, layout):
-    """Every form of the many-right-hand-side contraction at nrhs = 1, 7, 32, 33, 64, both
+    """Every form of the many-right-hand-side contraction at nrhs = 1, 7, 16, 32, 33, 34, 64, both
     operators (m_f and m = 1) and both daggers, on both vector layouts.  tcgen05 runs from 128
     columns (32 right-hand sides x 4 slices; 33 and 34 leave a partial tile); below 128 columns
     coarse_tc = 1 and 5 fall back to mma.sync; the tensor-memory-operand form (coarse_tc = 6) runs from 64 columns."""
