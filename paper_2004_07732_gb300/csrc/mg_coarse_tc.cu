@@ -14,9 +14,12 @@
 // layouts: slice-major [rhs][s][coarse site][16] (cs = Vc * 16, ss = 16; the
 // batched solver's) and site-major [coarse site][rhs][s][16] (cs = 16,
 // ss = ncols * 16), where the 128 columns of one site are one contiguous
-// 16 KB run.  Blocks: the FP32 column-major Galerkin blocks.  With FP16
-// blocks, at least 128 columns and coarse_tc = 1 the contraction runs on
-// tcgen05 instead (k_coarse_umma below).
+// 16 KB run.  Blocks: the FP32 column-major Galerkin blocks, or the FP16 copy.
+// With FP16 blocks the contraction also has tcgen05 forms (accumulators in
+// tensor memory): k_coarse_umma and k_coarse_umma_p keep both operands in
+// shared memory (from 128 columns), k_coarse_umma_t keeps the data operand in
+// tensor memory (from 64 columns).  The autotuner (coarse_tc = 0) times the
+// eligible forms on first use and keeps the fastest; coarse_tc 1-6 fix one.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
