@@ -392,3 +392,89 @@ def test_transfer_diagnostics_limits():
     kept = np.sum(np.abs(vv[0, :, 1]) ** 2) + np.sum(np.abs(vv[Ls - 1, :, 0]) ** 2)
     want = np.sqrt(1 - kept / np.sum(np.abs(v) ** 2))
     assert abs(mg.colinearity(v, Rw, Pw) - want) < 1e-13
+
+
+def test_wall_transfers_between_coarse_levels():
+    """restrict_walls / prolong_walls with the sigma_3 projectors of a coarse level on both sides
+    (the level-2 -> level-3 transfer): adjoint to each other, supported on the walls only, and,
+    for a unitary prolongator that commutes with sigma_3, R P is the identity on vectors whose
+    coarse slice 1 is chirality - and slice Ls_c chirality + (the wall field of Eq.
+    TruncProjectInterpolate in the permuted basis)."""
+    rng = np.random.default_rng(12)
+    V2, nv1, Ls2, Ls3 = 6, 3, 5, 3               # level-2 sites and vectors; 2 nv1 dof per site
+    n2 = V2 * 2 * nv1
+    # a unitary prolongator commuting with sigma_3: one unitary per chirality sector, per site
+    blocks = []
+    for _ in range(V2):
+        Q = [np.linalg.qr(rng.standard_normal((nv1, nv1)) + 1j * rng.standard_normal((nv1, nv1)))[0]
+             for _ in range(2)]
+        B = np.zeros((2 * nv1, 2 * nv1), dtype=complex)
+        B[:nv1, :nv1], B[nv1:, nv1:] = Q
+        blocks.append(B)
+    P = np.zeros((n2, n2), dtype=complex)
+    for i, B in enumerate(blocks):
+        P[i * 2 * nv1:(i + 1) * 2 * nv1, i * 2 * nv1:(i + 1) * 2 * nv1] = B
+    Fp, Fm = mg.coarse_projectors(V2, nv1)        # finer side: the level-2 chirality
+    Cp, Cm = mg.coarse_projectors(V2, nv1)        # coarser side: the same sigma_3 split
+    s3 = (Fp - Fm).toarray()
+    assert np.abs(s3 @ P - P @ s3).max() < 1e-14
+    x = rng.standard_normal(Ls2 * n2) + 1j * rng.standard_normal(Ls2 * n2)
+    y = rng.standard_normal(Ls3 * n2) + 1j * rng.standard_normal(Ls3 * n2)
+    Rx = mg.restrict_walls(x, P, Ls2, Ls3, Fp, Fm, Cp, Cm)
+    Py = mg.prolong_walls(y, P, Ls2, Ls3, Fp, Fm, Cp, Cm)
+    assert abs(np.vdot(Rx, y) - np.vdot(x, Py)) < 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
+    assert np.abs(Rx.reshape(Ls3, n2)[1:Ls3 - 1]).max() == 0.0
+    assert np.abs(Py.reshape(Ls2, n2)[1:Ls2 - 1]).max() == 0.0
+    e = np.zeros((Ls3, n2), dtype=complex)
+    e[0] = Cm @ (rng.standard_normal(n2) + 1j * rng.standard_normal(n2))
+    e[Ls3 - 1] = Cp @ (rng.standard_normal(n2) + 1j * rng.standard_normal(n2))
+    back = mg.restrict_walls(mg.prolong_walls(e.reshape(-1), P, Ls2, Ls3, Fp, Fm, Cp, Cm), P, Ls2, Ls3,
+                             Fp, Fm, Cp, Cm)
+    assert np.abs(back - e.reshape(-1)).max() < 1e-13
+    # the opposite chiralities on the walls are dropped
+    e2 = np.zeros((Ls3, n2), dtype=complex)
+    e2[0] = Cp @ rng.standard_normal(n2)
+    e2[Ls3 - 1] = Cm @ rng.standard_normal(n2)
+    assert np.abs(mg.prolong_walls(e2.reshape(-1), P, Ls2, Ls3, Fp, Fm, Cp, Cm)).max() < 1e-14
+
+
+def test_su3_generators_are_the_gell_mann_basis():
+    """Traceless Hermitian, tr(T_a T_b) = delta_ab / 2, and the su(3) structure constants
+    [T_1, T_2] = i T_3, [T_4, T_5] = i (T_3 + sqrt(3) T_8) / 2 of the Gell-Mann convention."""
+    T = force.su3_generators()
+    for a in range(8):
+        assert abs(np.trace(T[a])) < 1e-15
+        assert np.abs(T[a] - T[a].conj().T).max() < 1e-15
+        for b in range(8):
+            assert abs(np.trace(T[a] @ T[b]) - 0.5 * (a == b)) < 1e-15
+    comm = lambda A, B: A @ B - B @ A
+    assert np.abs(comm(T[0], T[1]) - 1j * T[2]).max() < 1e-15
+    assert np.abs(comm(T[3], T[4]) - 0.5j * (T[2] + np.sqrt(3) * T[7])).max() < 1e-14
+
+
+def test_directional_derivative_is_the_operator_difference():
+    """D_DW is real-linear in the links (the backward hop reads U^dag), so the central difference
+    of Re(lambda^dag D_DW(U + h dU e_link) x) in h equals the directional derivative exactly (up to
+    rounding), for SU(3) in 4-d and U(1) in 2-d."""
+    rng = synth.rng_for(13)
+    for dims, Ls, group in (((2, 2, 2, 4), 2, "su3"), ((4, 6), 3, "u1")):
+        nd = len(dims)
+        if group == "su3":
+            U = synth.su3_links(rng, dims, 0.3)
+            dU = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        else:
+            U = synth.u1_links(synth.u1_angles(rng, dims, 0.5))
+            dU = complex(rng.standard_normal(), rng.standard_normal())
+        lam = synth.gaussian_spinor(rng, dims, Ls, group).reshape(-1)
+        x = synth.gaussian_spinor(rng, dims, Ls, group).reshape(-1)
+        for mu, site in ((0, 1), (nd - 1, 3)):
+            got = force.directional_derivative(U, dims, Ls, lam, x, mu, site, dU, group)
+            h = 1e-3
+            vals = []
+            for sgn in (1, -1):
+                Uh = np.array(U, dtype=complex, copy=True)
+                Uh[mu, site] = Uh[mu, site] + sgn * h * dU
+                D = dirac.dwf_matrix(Uh, dims, Ls, 1.3, 0.07, group)
+                vals.append(np.vdot(lam, D @ x).real)
+            want = (vals[0] - vals[1]) / (2 * h)
+            assert abs(got - want) < 1e-9 * max(1.0, abs(want)), (group, mu, site, got, want)
