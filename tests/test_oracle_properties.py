@@ -6,8 +6,9 @@ directions).  Each property here is fixed by the definitions of Sec. 2 and 2.3
 for every shape:
   * Gamma_5-hermiticity of D_DW: D_DW^dag = Gamma_5 D_DW Gamma_5 with
     Gamma_5 = gamma_5 R_5 (Sec. 2.1);
-  * D_PV - D_DW(m) lives only on the two wall corners, as (1 - m) P_+ and
-    (1 - m) P_- (Eq. DWoperator with m -> 1);
+  * D_PV - D_DW(m) lives only on the two wall corners, as -(1 - m) P_+ on
+    (1, Ls) and -(1 - m) P_- on (Ls, 1) (Eq. DWoperator with m -> 1: its
+    literal corner terms are -m P_+ and -m P_-);
   * the sparse operator agrees with its point evaluator at every site;
   * the prolongator: P^dag P = 1 and gamma_5 P = P sigma_3 (Sec. 2.3);
   * the truncated transfers are adjoint and supported on the walls only
@@ -58,10 +59,10 @@ def test_pv_differs_only_on_the_wall_corners(g, M5, mf, seed):
     Pp, Pm = dirac.site_projectors(V, 2, 1)
     want = np.zeros_like(diff)
     if Ls == 1:
-        # both corners fall on the one slice: -m (P_+ + P_-) becomes -(1) (...), a difference of (m - 1) 1
+        # both corners fall on the one slice: -m (P_+ + P_-) = -m for D_DW(m), -1 for D_PV
         want[:n, :n] = (mf - 1.0) * (Pp + Pm).toarray()
     else:
-        # with the literal signs (-m P_+ on (1, Ls), -m P_- on (Ls, 1)) the PV - DW difference is -(1 - m)
+        # the corner terms -m P_+ on (1, Ls) and -m P_- on (Ls, 1) become -P_+ and -P_- for D_PV
         want[:n, (Ls - 1) * n:] = -(1.0 - mf) * Pp.toarray()
         want[(Ls - 1) * n:, :n] = -(1.0 - mf) * Pm.toarray()
     assert np.abs(diff - want).max() < 1e-14
@@ -119,3 +120,25 @@ def test_truncated_transfers_adjoint_and_on_the_walls(Ls, Ls_c, seed):
         assert np.abs(Rx.reshape(Ls_c, nc)[1:Ls_c - 1]).max() == 0.0
     if Ls > 2:
         assert np.abs(Py.reshape(Ls, nf)[1:Ls - 1]).max() == 0.0
+
+
+@settings(max_examples=12, deadline=None, derandomize=True)
+@given(st.tuples(st.integers(2, 3), st.integers(2, 3), st.integers(2, 3), st.integers(2, 4)), st.integers(1, 3),
+       st.lists(st.booleans(), min_size=4, max_size=4), st.integers(0, 10_000))
+def test_su3_gamma5_hermiticity_and_point_evaluator_any_shape(dims, Ls, anti, seed):
+    """4-d SU(3): Gamma_5-hermiticity and the point evaluator, on random small shapes."""
+    if int(np.prod(dims)) > 36:
+        dims = (2, 2, 2, dims[3])
+    V = int(np.prod(dims))
+    rng = synth.rng_for(seed)
+    U = synth.su3_links(rng, dims, 0.3)
+    an = [int(a) for a in anti]
+    D = dirac.dwf_matrix(U, dims, Ls, 1.8, 0.05, "su3", an)
+    Dd = D.toarray()
+    G5 = dirac.reflection_gamma5(V, Ls, 4, 3).toarray()
+    assert np.abs(Dd.conj().T - G5 @ Dd @ G5).max() < 1e-13
+    psi = synth.gaussian_spinor(rng, dims, Ls, "su3").reshape(-1)
+    points = [(s, x) for s in range(Ls) for x in range(V)]
+    got = np.asarray(dirac.dwf_apply_points(U, psi, dims, Ls, 1.8, 0.05, points, "su3", antiperiodic=an)).reshape(-1)
+    want = D @ psi
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
