@@ -23,6 +23,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <mutex>
+
 #include "mg.cuh"
 #include "async_copy.cuh"
 #include "mma_tf32.cuh"
@@ -1110,24 +1112,37 @@ static dwf_status input_tensor_map(CUtensorMap* tm, const float2* in, const TcPa
     return DWF_OK;
 }
 
+// Once per device (the current one): the dynamic shared-memory limit of the three tcgen05 forms,
+// and the device's SM count (the persistent forms launch one CTA per SM).  Guarded by a mutex:
+// mg_solve_groups runs hierarchies from several host threads.
+static dwf_status tc_device_init(int* sms_out) {
+    static std::mutex mu;
+    static int sms_of[64] = {0};                 // 0: this device is not set up yet
+    int dev = 0;
+    DWF_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device ordinal %d out of range", dev); return DWF_ERR_UNSUPPORTED; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (sms_of[dev] == 0) {
+        DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(UmSmem)));
+        DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma_p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(UpSmem)));
+        DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma_t<UT_NG, UT_NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(UtSmem<UT_NG, UT_NR>)));
+        int sms = 0;
+        DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (sms <= 0) { set_error("no multiprocessors reported"); return DWF_ERR_CUDA; }
+        sms_of[dev] = sms;
+    }
+    *sms_out = sms_of[dev];
+    return DWF_OK;
+}
+
 static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, const float2* in, float2* out,
                               const int* skip_rhs, cudaStream_t st) {
     if (form == TC_UMMA_T) {
-        static unsigned long long attr_set = 0;      // per device
-        static int sms_of[64] = {0};
-        int dev = 0;
-        DWF_CHECK_CUDA(cudaGetDevice(&dev));
-        if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
-            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma_t<UT_NG, UT_NR>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)sizeof(UtSmem<UT_NG, UT_NR>)));
-            if (dev < 64) {
-                DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev));
-                attr_set |= 1ull << dev;
-            }
-        }
-        int sms = dev < 64 ? sms_of[dev] : 0;
-        if (sms <= 0) DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int sms = 0;
+        DWF_TRY(tc_device_init(&sms));
         const long long nitems = p.Vc * ((p.ncols + UM_M - 1) / UM_M);
         if (nitems > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
         const long long grid = nitems < sms ? nitems : sms;
@@ -1140,20 +1155,8 @@ static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, cons
         return DWF_OK;
     }
     if (form == TC_UMMA_P) {
-        static unsigned long long attr_set = 0;      // per device
-        static int sms_of[64] = {0};
-        int dev = 0;
-        DWF_CHECK_CUDA(cudaGetDevice(&dev));
-        if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
-            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma_p, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)sizeof(UpSmem)));
-            if (dev < 64) {
-                DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev));
-                attr_set |= 1ull << dev;
-            }
-        }
-        int sms = dev < 64 ? sms_of[dev] : 0;
-        if (sms <= 0) DWF_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int sms = 0;
+        DWF_TRY(tc_device_init(&sms));
         const long long nitems = p.Vc * ((p.ncols + UM_M - 1) / UM_M);
         const long long grid = nitems < sms ? nitems : sms;
         if (grid < 1) return DWF_OK;
@@ -1165,12 +1168,8 @@ static dwf_status launch_form(const dwf_mg* h, int form, const TcParams& p, cons
         return DWF_OK;
     }
     if (form == TC_UMMA) {
-        static bool attr = false;
-        if (!attr) {
-            DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)sizeof(UmSmem)));
-            attr = true;
-        }
+        int sms = 0;
+        DWF_TRY(tc_device_init(&sms));
         const long long ctas = p.Vc * ((p.ncols + UM_M - 1) / UM_M);
         if (ctas > 0x7fffffffLL) { set_error("coarse batch too large for one launch"); return DWF_ERR_ARG; }
         k_coarse_umma<<<(unsigned)ctas, UM_THREADS, sizeof(UmSmem), st>>>((const __half2*)h->Ytile, in, out, p,
