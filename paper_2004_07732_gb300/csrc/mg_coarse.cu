@@ -6,6 +6,8 @@
 //     exact adjoint of the stored operator;
 //   * truncated wall restriction / prolongation (Eq. TruncProjectInterpolate).
 // Coarse vectors are [s][coarse site][chirality][vec], complex64.
+#include <mutex>
+
 #include "mg.cuh"
 #include "async_copy.cuh"
 #include "mma_tf32.cuh"
@@ -1560,22 +1562,37 @@ __global__ void __launch_bounds__(TILE_THREADS, 2) k_coarse_gcr_persistent(PgcrA
     }
 }
 
+// resident blocks per SM of the persistent coarse GCR, set up once per (device, block storage)
+// under a mutex (the kernel's shared-memory limit is a per-device attribute)
 template <class BT>
-static dwf_status launch_pgcr(PgcrArgs& a, int nsm, cudaStream_t st) {
-    static int per_sm[2] = {0, 0};
-    const int which = sizeof(BT) == sizeof(float2) ? 0 : 1;
-    const size_t smem = sizeof(TileSmemT<BT>);
-    if (per_sm[which] == 0) {
+static dwf_status pgcr_blocks_per_sm(int* out) {
+    static std::mutex mu;
+    static int per_sm[64] = {0};
+    int dev = 0;
+    DWF_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device ordinal %d out of range", dev); return DWF_ERR_UNSUPPORTED; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (per_sm[dev] == 0) {
+        const size_t smem = sizeof(TileSmemT<BT>);
         int per = 0;
         DWF_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_gcr_persistent<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         DWF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_gcr_persistent<BT>, TILE_THREADS,
                                                                      smem));
         if (per < 1) { set_error("persistent coarse GCR cannot be resident"); return DWF_ERR_UNSUPPORTED; }
-        per_sm[which] = per < PGCR_BLOCKS_PER_SM ? per : PGCR_BLOCKS_PER_SM;
+        per_sm[dev] = per < PGCR_BLOCKS_PER_SM ? per : PGCR_BLOCKS_PER_SM;
     }
+    *out = per_sm[dev];
+    return DWF_OK;
+}
+
+template <class BT>
+static dwf_status launch_pgcr(PgcrArgs& a, int nsm, cudaStream_t st) {
+    const size_t smem = sizeof(TileSmemT<BT>);
+    int per = 0;
+    DWF_TRY(pgcr_blocks_per_sm<BT>(&per));
     const int ntiles = ((a.cp.Lc[0] + TILE_X - 1) / TILE_X) * ((a.cp.Lc[1] + TILE_Y - 1) / TILE_Y);
-    int grid = nsm * per_sm[which];
+    int grid = nsm * per;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     void* args[] = {&a};
