@@ -179,19 +179,22 @@ __device__ __forceinline__ int pair_nb(const Fine4dParams& p, int site, int d, b
     return cross ? site + (L - 1) * st : site - st;
 }
 
-constexpr int PAIR_THREADS = 128;           // 32 sites x 4 slice pairs
+constexpr int PAIR_PY = 2;                    // slice pairs per block
+constexpr int PAIR_THREADS = 32 * PAIR_PY;
 
-// Block: 32 sites x 4 slice pairs; blocks numbered pair group fastest, so the blocks running at
+// Block: 32 sites x 2 slice pairs; blocks numbered pair group fastest, so the blocks running at
 // one time cover a compact stretch of the lattice and the neighbour loads of one block find the
-// other blocks' spinors in L2.  128 registers give four blocks (16 warps) per SM; the neighbour
+// other blocks' spinors in L2.  128 registers give eight blocks (16 warps) per SM; the neighbour
 // spinors of one direction are loaded together, and their latency is hidden across warps.
+// Measured at 16^3 x 32 x 16: 119 us with 2 pairs per block, 119 us with 1, 122.5 us with 4,
+// 137 us with 8.
 template <class LT, bool DAG>
-__global__ void __launch_bounds__(PAIR_THREADS, 4) k_dwf4d_pair(const typename LT::store* __restrict__ U,
+__global__ void __launch_bounds__(PAIR_THREADS, 8) k_dwf4d_pair(const typename LT::store* __restrict__ U,
                                                        const float4* __restrict__ psi, float4* __restrict__ out,
                                                        Fine4dParams p, LayP2 lay, int ngroups, const int* skip) {
     if (skip && *skip) return;
     const int site = (int)(blockIdx.x / ngroups) * 32 + threadIdx.x;
-    const int j = (int)(blockIdx.x % ngroups) * 4 + threadIdx.y;
+    const int j = (int)(blockIdx.x % ngroups) * PAIR_PY + threadIdx.y;
     if (site >= p.V || j >= lay.NP) return;
     const int jb = j > 0 ? j - 1 : lay.NP - 1;        // pair holding slice 2j - 1 (or the wall Ls - 1)
     const int ja = j + 1 < lay.NP ? j + 1 : 0;        // pair holding slice 2j + 2 (or the wall 0)
@@ -234,10 +237,10 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4) k_dwf4d_pair(const typename L
 template <class LT>
 dwf_status launch_pair(const void* U, const void* psi, void* out, const Fine4dParams& p, const LayP2& lay, bool dagger,
                        cudaStream_t st, const int* skip) {
-    const long long ng = (lay.NP + 3) / 4;
+    const long long ng = (lay.NP + PAIR_PY - 1) / PAIR_PY;
     const long long blocks = lay.NB * ng;
     if (blocks > 0x7fffffffLL) { set_error("4-d lattice too large for one launch"); return DWF_ERR_ARG; }
-    dim3 block(32, 4);
+    dim3 block(32, PAIR_PY);
     auto Ut = reinterpret_cast<const typename LT::store*>(U);
     if (dagger) k_dwf4d_pair<LT, true><<<(unsigned)blocks, block, 0, st>>>(Ut, (const float4*)psi, (float4*)out, p, lay, (int)ng, skip);
     else        k_dwf4d_pair<LT, false><<<(unsigned)blocks, block, 0, st>>>(Ut, (const float4*)psi, (float4*)out, p, lay, (int)ng, skip);
