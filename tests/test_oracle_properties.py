@@ -12,7 +12,9 @@ for every shape:
   * the sparse operator agrees with its point evaluator at every site;
   * the prolongator: P^dag P = 1 and gamma_5 P = P sigma_3 (Sec. 2.3);
   * the truncated transfers are adjoint and supported on the walls only
-    (Eq. TruncProjectInterpolate).
+    (Eq. TruncProjectInterpolate);
+  * the Mobius operator at b5 = 1, c5 = 0 is the Shamir operator;
+  * the Galerkin kernel is sigma_3-hermitian (Sec. 2.3).
 """
 import numpy as np
 import pytest
@@ -142,3 +144,34 @@ def test_su3_gamma5_hermiticity_and_point_evaluator_any_shape(dims, Ls, anti, se
     got = np.asarray(dirac.dwf_apply_points(U, psi, dims, Ls, 1.8, 0.05, points, "su3", antiperiodic=an)).reshape(-1)
     want = D @ psi
     assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+@settings(**SETTINGS)
+@given(geoms_2d, st.floats(0.2, 1.9), st.floats(0.0, 0.5), st.integers(0, 10_000))
+def test_mobius_at_b5_1_c5_0_is_the_shamir_operator(g, M5, mf, seed):
+    """D_M = (1_s x D_W)(b5 - c5 H_s) + 1 + H_s reduces to D_DW at b5 = 1, c5 = 0, for every shape."""
+    L0, L1, Ls, anti = g
+    dims = (L0, L1)
+    an = [int(a) for a in anti]
+    U = _u1(dims, seed)
+    Dm = dirac.mobius_matrix(U, dims, Ls, M5, mf, 1.0, 0.0, antiperiodic=an)
+    Dd = dirac.dwf_matrix(U, dims, Ls, M5, mf, antiperiodic=an)
+    assert abs(Dm - Dd).max() < 1e-14
+
+
+@settings(**SETTINGS)
+@given(st.sampled_from([((4, 4), (2, 2)), ((6, 4), (3, 2)), ((8, 4), (4, 2))]), st.integers(1, 3),
+       st.integers(0, 10_000))
+def test_galerkin_kernel_is_sigma3_hermitian(geom, nvec, seed):
+    """With a chirality-preserving prolongator the Galerkin kernel inherits gamma_5-hermiticity:
+    Dhat_W^dag = sigma_3 Dhat_W sigma_3 (the adjoint coarse stencil reads the same blocks)."""
+    dims, block = geom
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(seed)
+    U = _u1(dims, seed + 3)
+    vecs = [rng.standard_normal(V * 2) + 1j * rng.standard_normal(V * 2) for _ in range(nvec)]
+    P, cdims = mg.build_prolongator(vecs, dims, block, 2, 1)
+    K = mg.galerkin_kernel(P, dirac.wilson_matrix(U, dims, -1.0)).toarray()
+    Vc = int(np.prod(cdims))
+    s3 = np.kron(np.eye(Vc), np.diag([1.0] * nvec + [-1.0] * nvec))
+    assert np.abs(K.conj().T - s3 @ K @ s3).max() < 1e-12 * max(1.0, np.abs(K).max())
